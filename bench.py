@@ -1,0 +1,367 @@
+"""Benchmark: Levenberg-Marquardt PGET reconstructions per second on GB300.
+
+Workload (one "step" = one full reconstruction through the C ABI):
+  128 x 128 grid, 9 x 9 rod lattice (pitch 14, r = 5 px), lambda ~ U(0.5, 1.5) per rod with
+  10% of rods non-emitting, mu = 0.08 px^-1 in rods / 0.01 elsewhere; 360 angles over
+  360 degrees x 182 detectors (two opposed banks of 91) x 5 triangular sub-rays; Poisson
+  noise at 1e5 counts in the brightest bin; initial guess + 20 LM iterations with CG
+  capped at 30 steps; FP32 ray sums with Kahan compensation, FP64 CG scalars.
+Every step reconstructs a different seeded phantom; data are generated before timing and
+stay resident in HBM.  L2 is flushed (256 MB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pget|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank reconstructs its own
+requests (weak scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=128, n_lat=9, radius=5.0, n_angles=360, n_det=182, n_sub=5, collimator=1,
+                counts=1e5, max_iters=20, cg_max_iters=30)
+WORKLOAD_NAME = ("single-request LM: 128x128 grid, 9x9 rods r=5, 360 angles x 182 det (2 banks) "
+                 "x 5 triangular sub-rays, Poisson 1e5, 20 LM x 30 CG, FP32-Kahan rays / FP64 scalars")
+METRIC = "recon/s"
+SUB = (16, 16)
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pget", choices=["pget", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_problem(P, ctx, torch, seed: int, device: str):
+    from paper_2604_26745_gb300 import synth
+    W = WORKLOAD
+    ph = synth.lattice_phantom(W["n"], W["n_lat"], radius=W["radius"], seed=1100 + seed)
+    g = P.geometry(W["n"], W["n_angles"], W["n_det"], n_sub=W["n_sub"], collimator=W["collimator"])
+    lam = torch.tensor(ph.lam, dtype=torch.float64, device=device)
+    mu = torch.tensor(ph.mu, dtype=torch.float64, device=device)
+    y_clean = P.pget_forward(ctx, g, P.PGET_F64, lam, mu)
+    y = synth.poisson_noise(y_clean.cpu().numpy(), W["counts"], 2100 + seed)
+    return g, ph, y
+
+
+def samples_per_launch(g_np) -> dict:
+    """Ray samples one walk launch processes (distinct rays x in-grid samples), counted on
+    the host from the geometry (bilinear base pixel inside [-1, n-1]^2)."""
+    import numpy as np
+    n, na, nd, S = g_np["n"], g_np["n_angles"], g_np["n_det"], g_np["n_sub"]
+    nbk = 2 if nd == 182 else 1
+    nb = nd // nbk
+    r = n / math.sqrt(2.0)
+    p = 2 * r / nb
+    T = math.ceil(2 * r)
+    c = 0.5 * (n - 1)
+    t = -r + (np.arange(T) + 0.5)
+    u = np.array([(k - (S - 1) / 2) * 2 * p / (S + 1) for k in range(S)])
+    total_sub, total_distinct = 0, 0
+    for a in range(na):
+        for b in range(nbk):
+            psi = 2 * math.pi * a / na + b * math.pi
+            ct, st = math.cos(psi), math.sin(psi)
+            s = ((np.arange(nb) - 0.5 * (nb - 1) + 0.5 * b) * p)[:, None] + u[None, :]
+            s_all = s.ravel()
+            for arr, acc in ((s_all, "sub"), (np.unique(np.round(s_all / p * 2 * (S + 1)) * p / (2 * (S + 1))), "dist")):
+                fx = -arr[:, None] * st + t[None, :] * ct + c
+                fy = arr[:, None] * ct + t[None, :] * st + c
+                ok = (np.floor(fx) >= -1) & (np.floor(fx) <= n - 1) & (np.floor(fy) >= -1) & (np.floor(fy) <= n - 1)
+                if acc == "sub":
+                    total_sub += int(ok.sum())
+                else:
+                    total_distinct += int(ok.sum())
+    return {"sub_ray_samples": total_sub, "distinct_ray_samples": total_distinct}
+
+
+def cpu_baseline(y, g_dims) -> dict:
+    """The FP64 oracle as it stands, on this host's cores: one LM iteration (of 20) of one
+    reconstruction of the same workload; recon/s scaled by 20 iterations."""
+    from oracle import oracle as O
+    W = WORKLOAD
+    go = O.geom(W["n"], W["n_angles"], W["n_det"], n_sub=W["n_sub"], collimator=W["collimator"])
+    pr = O.default_params(max_iters=1, cg_max_iters=W["cg_max_iters"], cg_rel_tol=1e-6)
+    t0 = time.perf_counter()
+    l0, m0 = O.initial_guess(go, y)
+    O.lm(go, pr, y, l0, m0)
+    dt = time.perf_counter() - t0
+    per_recon = dt * W["max_iters"]
+    return {"value": 1.0 / per_recon, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"initial guess + 1 of {W['max_iters']} LM iterations (30 CG steps) of one "
+                      f"reconstruction, {dt:.2f} s, scaled x{W['max_iters']}"}
+
+
+# ------------------------------------------------------------------ reference
+def run_reference(args, rank: int):
+    """The CPU oracle timed as the reference arm: every step is one LM iteration of one
+    reconstruction of the same workload (bounded sample), reported as recon/s."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2604_26745_gb300 import synth
+    W = WORKLOAD
+    go = O.geom(W["n"], W["n_angles"], W["n_det"], n_sub=W["n_sub"], collimator=W["collimator"])
+    ph = synth.lattice_phantom(W["n"], W["n_lat"], radius=W["radius"], seed=1100)
+    y = synth.poisson_noise(O.forward(go, ph.lam, ph.mu), W["counts"], 2100)
+    pr = O.default_params(max_iters=1, cg_max_iters=W["cg_max_iters"], cg_rel_tol=1e-6)
+    l0, m0 = O.initial_guess(go, y)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.lm(go, pr, y, l0, m0)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    per_iter = sum(times) / len(times)
+    value = 1.0 / (per_iter * W["max_iters"])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"each step = 1 of {W['max_iters']} LM iterations of one reconstruction; "
+                                       f"recon/s = 1 / ({W['max_iters']} x mean step time)"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- product
+def main():
+    args = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    import numpy as np
+    import torch
+    from paper_2604_26745_gb300 import build, pget as P
+    build.build()
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = dist_
+    W = WORKLOAD
+    ctx = P.Context(local)
+    prec = P.PGET_F32_KAHAN
+    p = P.default_params(max_iters=W["max_iters"], cg_max_iters=W["cg_max_iters"], cg_rel_tol=1e-6,
+                         precision=prec)
+    nsteps = args.warmup + args.steps
+    probs = []
+    for k in range(nsteps):
+        g, ph, y = make_problem(P, ctx, torch, 97 * rank + k, dev)
+        probs.append((g, ph, torch.tensor(y, dtype=torch.float32, device=dev)))
+    lam = torch.empty((W["n"], W["n"]), dtype=torch.float32, device=dev)
+    mu = torch.empty_like(lam)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    reps = []
+    # warm-up (untimed)
+    for k in range(args.warmup):
+        g, ph, yd = probs[k]
+        l0, m0 = P.pget_initial_guess(ctx, g, p, yd)
+        P.pget_lm_solve(ctx, g, p, yd, l0, m0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    P.pget_profile_enable(ctx, True)
+    launches0 = P.pget_launch_count()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        g, ph, yd = probs[args.warmup + i]
+        flush.fill_(float(i))  # between timed steps, outside the events
+        ev[i][0].record(stream)
+        l0, m0 = P.pget_initial_guess(ctx, g, p, yd)
+        reps.append(P.pget_lm_solve(ctx, g, p, yd, l0, m0))
+        ev[i][1].record(stream)
+        lam, mu = l0, m0
+        if i == 0:
+            first = (lam.clone(), mu.clone())
+    torch.cuda.synchronize()
+    launches = P.pget_launch_count() - launches0
+    prof = P.pget_profile_read(ctx)
+    P.pget_profile_enable(ctx, False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # end to end through the host-buffer entry point (pinned buffers, copies inside)
+    e2e = None
+    if not args.no_e2e:
+        yh = [probs[args.warmup + i][2].cpu().pin_memory() for i in range(args.steps)]
+        lh = torch.empty((W["n"], W["n"]), dtype=torch.float32).pin_memory()
+        mh = torch.empty_like(lh).pin_memory()
+        g = probs[0][0]
+        P.pget_lm_solve_host(ctx, g, p, yh[0], lh, mh, True)  # warm
+        torch.cuda.synchronize()
+        ee = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P.pget_lm_solve_host(ctx, g, p, yh[i], lh, mh, True)
+            ee.append(time.perf_counter() - t0)
+        e_total = sum(ee)
+        if dist:
+            t = torch.tensor([e_total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_total = float(t.item())
+        e2e = {"value": world * args.steps / e_total, "unit": METRIC,
+               "h2d_bytes_per_step": int(yh[0].numel() * 4), "d2h_bytes_per_step": int(2 * lh.numel() * 4),
+               "timing": "host wall clock around pget_lm_solve_host (which synchronises)"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # accuracy of the first timed reconstruction: vs truth, and FP32-Kahan vs FP64 GPU path
+    g, ph, yd = probs[args.warmup]
+    p64 = P.default_params(max_iters=W["max_iters"], cg_max_iters=W["cg_max_iters"], cg_rel_tol=1e-6,
+                           precision=P.PGET_F64)
+    yd64 = yd.double()
+    l64, m64 = P.pget_initial_guess(ctx, g, p64, yd64)
+    P.pget_lm_solve(ctx, g, p64, yd64, l64, m64)
+    l32, m32 = first
+    u32 = torch.cat([l32.double().ravel(), m32.double().ravel()])
+    u64 = torch.cat([l64.ravel(), m64.ravel()])
+    f32_vs_f64 = float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64))
+    err_l = float(np.linalg.norm(l32.cpu().numpy() - ph.lam) / np.linalg.norm(ph.lam))
+    err_m = float(np.linalg.norm(m32.cpu().numpy() - ph.mu) / np.linalg.norm(ph.mu))
+
+    # roofline of the dominant kernel: algorithmic on-chip bytes per launch / measured time
+    counts = samples_per_launch(dict(n=W["n"], n_angles=W["n_angles"], n_det=W["n_det"], n_sub=W["n_sub"]))
+    bytes_per_sample = {"walk_forward": 32, "walk_jvp": 64, "walk_vjp": 64}
+    dom = max(prof, key=lambda k: prof[k]["total_ms"])
+    kern = {}
+    sm_mhz = clk.get("sm_mhz") or 1432.0
+    smem_peak = 152 * 128 * sm_mhz * 1e6 / 1e9  # GB/s: 152 SMs x 128 B/clk at the sampled clock
+    for k, v in prof.items():
+        if v["launches"] == 0:
+            continue
+        avg_ms = v["total_ms"] / v["launches"]
+        d = {"launches": v["launches"], "total_ms": round(v["total_ms"], 3), "avg_us": round(avg_ms * 1e3, 2),
+             "share_of_timed": round(v["total_ms"] / (sum(step_ms)), 4)}
+        if k in bytes_per_sample:
+            d["achieved_gbs"] = bytes_per_sample[k] * counts["distinct_ray_samples"] / (avg_ms * 1e-3) / 1e9
+        kern[k] = d
+    dk = dom if dom in bytes_per_sample else max((k for k in kern if k in bytes_per_sample),
+                                                 key=lambda k: kern[k]["total_ms"])
+    achieved = kern[dk]["achieved_gbs"]
+    roof = {"kernel": dk, "bound": "smem", "achieved": round(achieved, 1), "peak": round(smem_peak, 1),
+            "unit": "GB/s", "frac": round(achieved / smem_peak, 4), "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 B/clk shared-memory bandwidth x median sampled SM clock",
+            "algorithmic_bytes_per_launch": bytes_per_sample[dk] * counts["distinct_ray_samples"],
+            "units_per_launch": counts["distinct_ray_samples"],
+            "unit_desc": "in-grid samples of distinct rays (sub-rays sharing a line are one ray)"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(sum(step_ms) / len(step_ms), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MB write)", **{k: v for k, v in W.items()}},
+        "latency_ms": {"p50": round(statistics.median(step_ms), 3),
+                       "p99": round(sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)], 3)},
+        "accuracy": {"f32_kahan_vs_f64_gpu_rel_l2": f32_vs_f64, "rel_err_vs_truth_lambda": err_l,
+                     "rel_err_vs_truth_mu": err_m, "f_final": reps[0]["f_final"], "f0": reps[0]["f0"],
+                     "accepted": reps[0]["accepted"]},
+        "roofline": roof, "kernels": kern, "gpu_launches": int(launches),
+        "clocks": clk, "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(probs[args.warmup][2].cpu().double().numpy(), None)
+        except Exception as ex:  # reported, never fatal
+            line["cpu_baseline"] = {"error": str(ex)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

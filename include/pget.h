@@ -1,0 +1,208 @@
+/*
+ * pget.h -- C ABI of libpget.so, the GB300 (sm_103a) hot path of the Levenberg-Marquardt
+ * reconstruction for passive gamma emission tomography (PGET).
+ *
+ * Paper: "Robust Model-Based Iteration for Passive Gamma Emission Tomography",
+ * Heikkila, Heikkinen, Rimppi, Helin (arXiv 2604.26745).
+ *
+ * Unknowns: emission lambda and attenuation mu on an n x n pixel grid (pixel size 1,
+ * row-major img[iy * n + ix], pixel centre at (ix - (n-1)/2, iy - (n-1)/2)).
+ * Data: y[a * n_det + d], a = 0..n_angles-1 (phi_a = 2 pi a / n_angles), d = detector.
+ *
+ * Conventions shared by every call
+ *   - Arrays are caller-owned, contiguous DEVICE pointers unless a name ends in _host.
+ *     Element type: double for PGET_F64, float for PGET_F32 and PGET_F32_KAHAN.
+ *     The library never frees caller memory and never keeps a caller pointer after a
+ *     call returns.
+ *   - stream is a cudaStream_t passed as void* (NULL: the legacy default stream).
+ *     forward / jvp / vjp / reg_apply only enqueue work and return; they may reuse
+ *     context workspace, so calls on one context must not overlap on different streams.
+ *   - Every call returns a pget_status and never aborts, traps or prints.  On an error
+ *     pget_last_error(ctx) gives a one-line message (thread-local, valid until the next
+ *     call on that thread).
+ *   - A context serves one device; it owns all workspace (allocated on first use for a
+ *     geometry, freed by pget_destroy) and counts it against mem_budget_bytes.
+ */
+#ifndef PGET_H
+#define PGET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PGET_OK = 0,
+    PGET_EINVAL = 1,      /* bad argument: geometry, size, null pointer, precision      */
+    PGET_ENOMEM = 2,      /* workspace would exceed the context's memory budget         */
+    PGET_EAGAIN = 3,      /* serving: no free slot or memory right now, retry later     */
+    PGET_ECUDA = 4,       /* a CUDA runtime call failed (message has the CUDA error)    */
+    PGET_ETIMEOUT = 5,    /* a bounded device-side wait ran out                         */
+    PGET_ENUMERIC = 6,    /* NaN or Inf met in a result that must be finite             */
+    PGET_ENOTFOUND = 7    /* serving: unknown ticket                                     */
+} pget_status;
+
+typedef enum {
+    PGET_F64 = 0,         /* everything in double                                        */
+    PGET_F32 = 1,         /* float ray sums and vectors; double dot products and scalars */
+    PGET_F32_KAHAN = 2    /* as PGET_F32 with Kahan-compensated sums along every ray     */
+} pget_precision;
+
+/* Measurement geometry (Sec. 2 and Sec. 2.1 of the paper: two opposed detector banks
+ * with a half-pitch offset, a full rotation, collimated detectors).
+ *   Detector d of bank b (b = 0: looks along theta = (cos phi, sin phi); b = 1: along
+ *   theta + pi) sits at offset s_d = (d - (nb-1)/2 + b/2) * det_pitch in its bank's own
+ *   frame, nb = n_det / n_banks.  Its collimator response is n_sub parallel sub-rays at
+ *   offsets u_k with weights w_k (sum w = 1): triangular u_k = (k - (S-1)/2) 2p/(S+1),
+ *   w_k ~ 1 - |u_k|/p; box u_k = (k - (S-1)/2) p/S, w_k = 1/S.
+ *   A ray at offset s is sampled at x_j = s theta_perp + t_j theta, t_j = -r + (j+1/2) h,
+ *   j = 0..T-1, T = ceil(2 r / h), theta_perp = (-sin, cos); the detector is at +theta. */
+typedef struct {
+    int32_t n;            /* grid size n >= 2                                             */
+    int32_t n_angles;     /* >= 1, phi_a = 2 pi a / n_angles                              */
+    int32_t n_det;        /* detectors in total, all banks                                */
+    int32_t n_banks;      /* 1 or 2; 0 selects 2 when n_det == 182, else 1                */
+    int32_t n_sub;        /* sub-rays per detector, 1..64                                 */
+    int32_t collimator;   /* 0 box, 1 triangular                                          */
+    double step;          /* ray sample spacing h in pixels (<= 0: 1)                     */
+    double fov_radius;    /* r (<= 0: n / sqrt 2, the circumscribed disk of the grid)     */
+    double det_pitch;     /* p (<= 0: 2 r / nb)                                           */
+} pget_geometry;
+
+/* Levenberg-Marquardt parameters (Sec. 2.2, Eq. (6)-(9), Sec. 3.1).
+ * Objective f(u) = 1/2 |A(u) - y|^2 + R(lambda) + R(mu) with the smoothed total variation
+ * R(v) = alpha sum_px sqrt(|grad v|^2 + tv_eps^2) (forward differences, zero-flux border);
+ * tv_eps <= 0 selects the quadratic R(v) = alpha/2 |grad v|^2. */
+typedef struct {
+    double alpha_lambda, alpha_mu;   /* prior weights (1e-2)                                     */
+    double tv_eps;                   /* smoothing of the TV prior (1e-3); <= 0: quadratic prior  */
+    double lambda_max, mu_max;       /* box [0, lambda_max] x [0, mu_max] (2.0, 0.2)             */
+    int32_t max_iters;               /* LM iterations; a rejected trial counts as one (20)       */
+    int32_t cg_max_iters;            /* CG iterations per LM step (30)                           */
+    double cg_rel_tol;               /* CG stops when |res| <= tol |rhs| (1e-6)                  */
+    double nu0_scale;                /* nu_0 = nu0_scale |J g|^2 / |g|^2, g = grad f(u_0) (1e-3) */
+    double nu_up, nu_down;           /* nu *= nu_up if rho < rho_lo, *= nu_down if rho > rho_hi  */
+    double eta;                      /* accept iff rho > eta, eta in (0, 1/4) (1e-3)             */
+    double rho_lo, rho_hi;           /* (0.25, 0.75)                                              */
+    double nu_min, nu_max;           /* nu clamped to [nu_min nu_0, nu_max nu_0] (1e-12, 1e12)   */
+    int32_t precision;               /* pget_precision                                           */
+} pget_lm_params;
+
+#define PGET_TRACE 256
+
+typedef struct {
+    int32_t iters_run, accepted, cg_iters_total;
+    int32_t status;                  /* pget_status of the solve                             */
+    double f0, f_final, nu0, nu_final;
+    /* per iteration k < min(iters_run, PGET_TRACE): objective after the iteration, rho,
+     * nu after its update, model decrease m(0) - m(s), actual decrease, accepted flag,
+     * CG iterations run */
+    double f[PGET_TRACE], rho[PGET_TRACE], nu[PGET_TRACE], pred[PGET_TRACE], ared[PGET_TRACE];
+    int32_t acc[PGET_TRACE], cg_iters[PGET_TRACE];
+    double device_ms;                /* device time of the solve (CUDA events)               */
+} pget_lm_report;
+
+typedef struct pget_ctx pget_ctx;
+
+/* Create a context on `device` whose workspace may use at most mem_budget_bytes
+ * (0: no limit).  *ctx is set to NULL on failure. */
+pget_status pget_create(pget_ctx** ctx, int device, size_t mem_budget_bytes);
+
+/* Free the context and all of its workspace (waits for its work to finish). */
+pget_status pget_destroy(pget_ctx* ctx);
+
+/* Fill *out with the defaults listed above (precision PGET_F32_KAHAN). */
+void pget_default_params(pget_lm_params* out);
+
+/* Forward model y = A(lambda, mu): the attenuated ray transform of Eq. (1) in its
+ * sampled form (Eq. (5)): per ray q = h sum_j lambda_j exp(-E_j),
+ * E_j = h (mu_j / 2 + sum_{i > j} mu_i) (i > j: nearer the detector), lambda_j, mu_j
+ * bilinear samples (zero outside the grid), y = sum_k w_k q_k.
+ * lam, mu: [n][n] in; y: [n_angles][n_det] out. */
+pget_status pget_forward(pget_ctx* ctx, const pget_geometry* g, int32_t precision,
+                         const void* lam, const void* mu, void* y, void* stream);
+
+/* Jacobian-vector product dy = J (dlam, dmu), the Frechet derivative of Eq. (2):
+ * per ray q' = h sum_j exp(-E_j) (dlam_j - lambda_j dE_j), dE_j = h (dmu_j/2 + sum_{i>j} dmu_i).
+ * lam, mu, dlam, dmu: [n][n] in; dy: [n_angles][n_det] out. */
+pget_status pget_jvp(pget_ctx* ctx, const pget_geometry* g, int32_t precision,
+                     const void* lam, const void* mu, const void* dlam, const void* dmu,
+                     void* dy, void* stream);
+
+/* Adjoint product (glam, gmu) = J^T r (the F'* of Thm. 3.1 and the convergence proof in
+ * Sec. 3.1), computed as a gather: every output pixel sums the contributions of the ray
+ * samples whose bilinear footprint covers it; no atomics, deterministic.
+ * lam, mu: [n][n] in; r: [n_angles][n_det] in; glam, gmu: [n][n] out. */
+pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t precision,
+                     const void* lam, const void* mu, const void* r, void* glam, void* gmu,
+                     void* stream);
+
+/* Prior of the objective above (it stands in for the P1/P2 terms of Eq. (6)):
+ * out = alpha grad^T W(u) grad v with the lagged-diffusivity weights
+ * W(u) = 1 / sqrt(|grad u|^2 + eps^2) (eps <= 0: W = 1), and, when value_host is not
+ * NULL, *value_host = R(u) (synchronises the stream).  With v = u, out is grad R(u).
+ * u, v, out: [n][n]. */
+pget_status pget_reg_apply(pget_ctx* ctx, int32_t n, int32_t precision, double alpha,
+                           double eps, const void* u, const void* v, void* out,
+                           double* value_host, void* stream);
+
+/* Conjugate gradients from x = 0 on the damped normal equations of Eq. (9):
+ * (J^T J + alpha grad^T W grad + nu I) x = rhs at u = (lam, mu), W frozen at u,
+ * stopping after p->cg_max_iters iterations or when |res| <= p->cg_rel_tol |rhs|.
+ * rhs, x: [2][n][n] (lambda block, then mu block).  *iters_host (optional) gets the
+ * iterations run (synchronises the stream). */
+pget_status pget_cg_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
+                          const void* lam, const void* mu, double nu, const void* rhs,
+                          void* x, int32_t* iters_host, void* stream);
+
+/* Initial guess (the paper states none): mu = mu_init, lambda = c with
+ * c = sum y / sum A(1, mu_init), both projected onto the box. */
+pget_status pget_initial_guess(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
+                               double mu_init, const void* y, void* lam, void* mu, void* stream);
+
+/* Levenberg-Marquardt trust-region solve (Sec. 2.2 and 3.1): each iteration runs CG on
+ * Eq. (9), projects u + delta onto the box, takes s = P(u + delta) - u, evaluates the
+ * model decrease of Eq. (8) and rho of Eq. (12), accepts iff rho > eta and updates nu.
+ * All state stays on the device; one host synchronisation per iteration reads the
+ * FP64 scalars into the report.  lam_io, mu_io: initial guess in, result out.
+ * rep: host memory.  Blocks until done. */
+pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
+                          const void* y, void* lam_io, void* mu_io, pget_lm_report* rep,
+                          void* stream);
+
+/* As pget_lm_solve with HOST buffers (pinned or pageable): copies y_host to the device,
+ * computes the initial guess (mu_init 0.01) when init_guess != 0 (else takes
+ * lam_host / mu_host as the initial guess), solves, and copies the result back. */
+pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
+                               const void* y_host, void* lam_host, void* mu_host,
+                               int32_t init_guess, pget_lm_report* rep, void* stream);
+
+/* ------------------------------------------------------------- diagnostics
+ * Device time of the hot kernels, measured with CUDA events recorded on the stream each
+ * kernel is launched on (no effect on results).  pget_profile_enable resets the counters;
+ * pget_profile_read synchronises on the recorded events and fills up to max entries
+ * (walk_forward, walk_jvp, walk_vjp, reduce_views), returning how many were written. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} pget_kernel_stat;
+
+pget_status pget_profile_enable(pget_ctx* ctx, int32_t enable);
+int32_t pget_profile_read(pget_ctx* ctx, pget_kernel_stat* out, int32_t max);
+
+/* Kernel launches issued by this library since it was loaded (all contexts). */
+long long pget_launch_count(void);
+
+/* Message of the last error on this thread ("" if none). */
+const char* pget_last_error(pget_ctx* ctx);
+
+/* Library version string. */
+const char* pget_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGET_H */

@@ -1,0 +1,885 @@
+// api.cu -- the C ABI of libpget.so: context, workspace, and the drivers of the
+// forward / JVP / VJP operators, the CG solve of Eq. (9) and the LM iteration (Sec. 2.2).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pget_internal.cuh"
+#include "vec.cuh"
+
+using namespace pget;
+
+static thread_local std::string g_last_error;
+
+static pget_status fail(pget_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return fail(PGET_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+namespace pget {
+
+// -------------------------------------------------------------------- profiling
+// CUDA events around the hot kernels, recorded on the stream the kernels run on;
+// elapsed times are collected once the stream has been synchronised.
+enum ProfKind { kPFwd = 0, kPJvp = 1, kPVjp = 2, kPRed = 3, kPKinds = 4 };
+static const char* kProfNames[kPKinds] = {"walk_forward", "walk_jvp", "walk_vjp", "reduce_views"};
+
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double total_ms[kPKinds] = {0, 0, 0, 0};
+    long long count[kPKinds] = {0, 0, 0, 0};
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void begin(int kind, cudaStream_t st) {
+        if (!on) return;
+        Rec r{kind, get(), get()};
+        cudaEventRecord(r.a, st);
+        pending.push_back(r);
+    }
+    void end(cudaStream_t st) {
+        if (!on || pending.empty()) return;
+        cudaEventRecord(pending.back().b, st);
+    }
+    void collect() {
+        for (auto& r : pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                total_ms[r.kind] += ms;
+                count[r.kind] += 1;
+            }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        pending.clear();
+    }
+    void reset() {
+        collect();
+        for (int k = 0; k < kPKinds; ++k) {
+            total_ms[k] = 0;
+            count[k] = 0;
+        }
+    }
+    ~Profiler() {
+        for (auto& r : pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// --------------------------------------------------------------------- workspace
+struct Workspace {
+    Profiler* prof = nullptr;
+    Geometry g;
+    int prec = 0;
+    bool f64 = false;
+    size_t elt = 4;
+    int P = 0, groups = 1, n_views = 0;
+    size_t nn = 0, M = 0, nslots = 0, img_elems = 0;
+    WalkPlan pf, pj, pv;
+    ViewDev* d_views = nullptr;
+    int* d_vtrans = nullptr;
+    int* d_det_slot = nullptr;
+    double* d_w = nullptr;
+    int* d_src_off = nullptr;
+    int* d_src_det = nullptr;
+    double* d_src_w = nullptr;
+    void* pk_u[2] = {nullptr, nullptr};
+    void* pk_ut[2] = {nullptr, nullptr};
+    void* pk_p[2] = {nullptr, nullptr};
+    void *u = nullptr, *ut = nullptr, *x = nullptr, *res = nullptr, *p = nullptr, *q = nullptr,
+         *s = nullptr, *gr = nullptr, *Wl = nullptr, *Wm = nullptr;
+    void *yb = nullptr, *r = nullptr, *rt = nullptr, *Jp = nullptr;
+    void *U = nullptr, *Ut = nullptr;
+    void *gpart = nullptr, *part2 = nullptr;
+    double* dpart[4] = {nullptr, nullptr, nullptr, nullptr};
+    LmState* lm = nullptr;
+    int* err = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+
+    ~Workspace() {
+        for (void* a : allocs) cudaFree(a);
+    }
+    template <typename X>
+    cudaError_t alloc(X** ptr, size_t bytes_) {
+        void* a = nullptr;
+        size_t b = bytes_ ? bytes_ : 16;
+        cudaError_t e = cudaMalloc(&a, b);
+        if (e != cudaSuccess) return e;
+        allocs.push_back(a);
+        bytes += b;
+        *ptr = (X*)a;
+        return cudaMemset(a, 0, b);
+    }
+};
+
+// bytes a workspace for this geometry and precision will take
+static size_t workspace_bytes(const Geometry& g, int prec, int groups) {
+    size_t elt = prec == PGET_F64 ? 8 : 4;
+    size_t nn = (size_t)g.n * g.n, M = (size_t)g.n_angles * g.n_det;
+    size_t V = (size_t)g.n_angles * g.n_banks;
+    size_t P = (size_t)((g.n + 2 + 1) / 2) * 2;
+    size_t img = (size_t)(g.n + 2) * P * 2 * elt;
+    size_t b = 0;
+    b += 6 * img;                       // three packed pairs, two layouts each
+    b += 8 * 2 * nn * elt + 2 * nn * elt;  // vectors + weights
+    b += 4 * M * elt;                   // sinograms
+    b += 2 * V * g.max_slots * elt;     // slot totals
+    b += V * 2 * nn * elt;              // per-view partial gradients
+    b += (size_t)groups * 2 * nn * elt;
+    b += 4 * kRedBlocks * 8 + sizeof(LmState) + 64;
+    b += V * sizeof(ViewDev) + V * 4 + (size_t)g.n_det * g.n_sub * 4 + g.n_sub * 8;
+    b += g.src_off.size() * 4 + g.src_det.size() * 12;
+    return b;
+}
+
+}  // namespace pget
+
+struct pget_ctx {
+    Profiler prof;
+    int device = 0;
+    size_t budget = 0;
+    std::mutex mu;
+    std::unique_ptr<Workspace> ws;
+    std::string ws_key;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+pget_status get_workspace(pget_ctx* ctx, const pget_geometry* gin, int prec, Workspace** out) {
+    if (!gin) return fail(PGET_EINVAL, "null geometry");
+    if (prec != PGET_F64 && prec != PGET_F32 && prec != PGET_F32_KAHAN)
+        return fail(PGET_EINVAL, "unknown precision %d", prec);
+    Geometry g;
+    std::string msg;
+    pget_status s = build_geometry(*gin, &g, &msg);
+    if (s != PGET_OK) return fail(s, "%s", msg.c_str());
+    std::string key = g.key + "#" + std::to_string(prec);
+    if (ctx->ws && ctx->ws_key == key) {
+        *out = ctx->ws.get();
+        return PGET_OK;
+    }
+    const int V = g.n_angles * g.n_banks;
+    const int tiles = ((g.n + 31) / 32) * ((g.n + 31) / 32);
+    int groups = std::max(1, std::min(V, (2 * kRedBlocks + tiles - 1) / tiles));
+    size_t need = workspace_bytes(g, prec, groups);
+    size_t held = ctx->ws ? ctx->ws->bytes : 0;
+    if (ctx->budget && need > ctx->budget)
+        return fail(PGET_ENOMEM, "workspace needs %zu bytes, budget %zu", need, ctx->budget);
+    (void)held;
+    ctx->ws.reset();
+    ctx->ws_key.clear();
+    auto w = std::make_unique<Workspace>();
+    w->g = std::move(g);
+    Geometry& G = w->g;
+    w->prec = prec;
+    w->f64 = prec == PGET_F64;
+    w->elt = w->f64 ? 8 : 4;
+    w->P = ((G.n + 2 + 1) / 2) * 2;
+    w->groups = groups;
+    w->n_views = V;
+    w->nn = (size_t)G.n * G.n;
+    w->M = (size_t)G.n_angles * G.n_det;
+    w->nslots = (size_t)V * G.max_slots;
+    w->img_elems = (size_t)(G.n + 2) * w->P;
+    const size_t budget_smem = 100 * 1024;
+    w->pf = plan_walk(G, w->P, kFwd, w->f64, budget_smem);
+    w->pj = plan_walk(G, w->P, kJvp, w->f64, budget_smem);
+    w->pv = plan_walk(G, w->P, kVjp, w->f64, budget_smem);
+    const size_t e = w->elt, e2 = 2 * e;
+    CK(w->alloc(&w->d_views, sizeof(ViewDev) * V));
+    CK(cudaMemcpy(w->d_views, G.views.data(), sizeof(ViewDev) * V, cudaMemcpyHostToDevice));
+    std::vector<int> vt(V);
+    for (int v = 0; v < V; ++v) vt[v] = G.views[v].transposed;
+    CK(w->alloc(&w->d_vtrans, sizeof(int) * V));
+    CK(cudaMemcpy(w->d_vtrans, vt.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_det_slot, sizeof(int) * G.det_slot.size()));
+    CK(cudaMemcpy(w->d_det_slot, G.det_slot.data(), sizeof(int) * G.det_slot.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_w, sizeof(double) * G.w.size()));
+    CK(cudaMemcpy(w->d_w, G.w.data(), sizeof(double) * G.w.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_src_off, sizeof(int) * G.src_off.size()));
+    CK(cudaMemcpy(w->d_src_off, G.src_off.data(), sizeof(int) * G.src_off.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_src_det, sizeof(int) * G.src_det.size()));
+    CK(cudaMemcpy(w->d_src_det, G.src_det.data(), sizeof(int) * G.src_det.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_src_w, sizeof(double) * G.src_w.size()));
+    CK(cudaMemcpy(w->d_src_w, G.src_w.data(), sizeof(double) * G.src_w.size(), cudaMemcpyHostToDevice));
+    for (int l = 0; l < 2; ++l) {
+        CK(w->alloc(&w->pk_u[l], e2 * w->img_elems));
+        CK(w->alloc(&w->pk_ut[l], e2 * w->img_elems));
+        CK(w->alloc(&w->pk_p[l], e2 * w->img_elems));
+    }
+    void** vecs[] = {&w->u, &w->ut, &w->x, &w->res, &w->p, &w->q, &w->s, &w->gr};
+    for (void** vp : vecs) CK(w->alloc(vp, e * 2 * w->nn));
+    CK(w->alloc(&w->Wl, e * w->nn));
+    CK(w->alloc(&w->Wm, e * w->nn));
+    CK(w->alloc(&w->yb, e * w->M));
+    CK(w->alloc(&w->r, e * w->M));
+    CK(w->alloc(&w->rt, e * w->M));
+    CK(w->alloc(&w->Jp, e * w->M));
+    CK(w->alloc(&w->U, e * w->nslots));
+    CK(w->alloc(&w->Ut, e * w->nslots));
+    CK(w->alloc(&w->gpart, e * (size_t)V * 2 * w->nn));
+    CK(w->alloc(&w->part2, e * (size_t)groups * 2 * w->nn));
+    for (int k = 0; k < 4; ++k) CK(w->alloc(&w->dpart[k], sizeof(double) * kRedBlocks));
+    CK(w->alloc(&w->lm, sizeof(LmState)));
+    CK(w->alloc(&w->err, sizeof(int) * 4));
+    w->prof = &ctx->prof;
+    ctx->ws = std::move(w);
+    ctx->ws_key = key;
+    *out = ctx->ws.get();
+    return PGET_OK;
+}
+
+// ------------------------------------------------------------------ operators
+WalkArgs base_args(const Workspace& w) {
+    WalkArgs a{};
+    const Geometry& G = w.g;
+    a.views = w.d_views;
+    a.n = G.n;
+    a.T = G.T;
+    a.P = w.P;
+    a.h = G.h;
+    a.max_slots = G.max_slots;
+    a.n_det = G.n_det;
+    a.n_banks = G.n_banks;
+    a.nb = G.nb;
+    a.n_sub = G.n_sub;
+    a.det_slot = w.d_det_slot;
+    a.w = w.d_w;
+    a.src_off = w.d_src_off;
+    a.src_det = w.d_src_det;
+    a.src_w = w.d_src_w;
+    a.err = w.err;
+    return a;
+}
+
+cudaError_t op_forward(const Workspace& w, void* const pk[2], void* U_out, void* y_out, const int* stop, cudaStream_t st) {
+    WalkArgs a = base_args(w);
+    a.Yc = w.pf.Yc;
+    a.nchunks = w.pf.nchunks;
+    a.u_img[0] = pk[0];
+    a.u_img[1] = pk[1];
+    a.slot_val = U_out;
+    a.y_out = y_out;
+    a.stop = stop;
+    w.prof->begin(kPFwd, st);
+    cudaError_t e = launch_walk(kFwd, w.prec, w.pf, a, w.n_views, st);
+    w.prof->end(st);
+    return e;
+}
+
+cudaError_t op_jvp(const Workspace& w, void* const pku[2], void* const pkp[2], void* dy, const int* stop, cudaStream_t st) {
+    WalkArgs a = base_args(w);
+    a.Yc = w.pj.Yc;
+    a.nchunks = w.pj.nchunks;
+    a.u_img[0] = pku[0];
+    a.u_img[1] = pku[1];
+    a.p_img[0] = pkp[0];
+    a.p_img[1] = pkp[1];
+    a.y_out = dy;
+    a.stop = stop;
+    w.prof->begin(kPJvp, st);
+    cudaError_t e = launch_walk(kJvp, w.prec, w.pj, a, w.n_views, st);
+    w.prof->end(st);
+    return e;
+}
+
+// J^T r (+ optional prior / damping / dot through ra)
+template <typename T>
+cudaError_t op_vjp(Workspace& w, void* const pku[2], const void* U, const void* r, RedArgs<T> ra,
+                   const int* stop, cudaStream_t st) {
+    WalkArgs a = base_args(w);
+    a.Yc = w.pv.Yc;
+    a.nchunks = w.pv.nchunks;
+    a.sb_cap = w.pv.sb_cap;
+    a.u_img[0] = pku[0];
+    a.u_img[1] = pku[1];
+    a.slot_val = (void*)U;
+    a.r_in = r;
+    a.gpart = w.gpart;
+    a.stop = stop;
+    w.prof->begin(kPVjp, st);
+    cudaError_t e = launch_walk(kVjp, w.prec, w.pv, a, w.n_views, st);
+    w.prof->end(st);
+    if (e != cudaSuccess) return e;
+    ra.n = w.g.n;
+    ra.skip = stop;
+    w.prof->begin(kPRed, st);
+    reduce_views<T>((const T*)w.gpart, w.d_vtrans, w.g.n, w.n_views, w.groups, (T*)w.part2, ra,
+                    w.prec == PGET_F32_KAHAN, st);
+    w.prof->end(st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+void pack_vec(const Workspace& w, const void* vec, void* const pk[2], const int* skip, cudaStream_t st) {
+    const T* a = (const T*)vec;
+    pack<T>(a, a + w.nn, w.g.n, w.P, pk[0], pk[1], skip, st);
+}
+
+template <typename T>
+void pack_pair(const Workspace& w, const void* lam, const void* mu, void* const pk[2], cudaStream_t st) {
+    pack<T>((const T*)lam, (const T*)mu, w.g.n, w.P, pk[0], pk[1], nullptr, st);
+}
+
+// CG on (J^T J + H + nu I) x = scale_b * b, H and U at the packed iterate pk_u
+template <typename T>
+pget_status run_cg(Workspace& w, const void* b, double scale_b, double nu, const double* nu_dev,
+                   const pget_lm_params& p, cudaStream_t st) {
+    const size_t m = 2 * w.nn;
+    CgState* cg = &w.lm->cg;
+    cg_init<T>((const T*)b, (T*)w.x, (T*)w.res, (T*)w.p, m, scale_b, p.cg_rel_tol, w.dpart[0], cg, st);
+    const int* stop = &cg->stop;
+    for (int it = 0; it < p.cg_max_iters; ++it) {
+        pack_vec<T>(w, w.p, w.pk_p, stop, st);
+        cudaError_t e = op_jvp(w, w.pk_u, w.pk_p, w.Jp, stop, st);
+        if (e != cudaSuccess) return fail(PGET_ECUDA, "jvp launch: %s", cudaGetErrorString(e));
+        RedArgs<T> ra;
+        ra.out = (T*)w.q;
+        ra.v = (const T*)w.p;
+        ra.Wl = (const T*)w.Wl;
+        ra.Wm = (const T*)w.Wm;
+        ra.alpha_l = p.alpha_lambda;
+        ra.alpha_m = p.alpha_mu;
+        ra.nu = nu;
+        ra.nu_dev = nu_dev;
+        ra.dotv = (const T*)w.p;
+        ra.part = w.dpart[0];
+        e = op_vjp<T>(w, w.pk_u, w.U, w.Jp, ra, stop, st);
+        if (e != cudaSuccess) return fail(PGET_ECUDA, "vjp launch: %s", cudaGetErrorString(e));
+        cg_finish_pq(w.dpart[0], cg, st);
+        cg_update<T>((T*)w.x, (T*)w.res, (const T*)w.p, (const T*)w.q, m, w.dpart[0], cg, st);
+        cg_pupdate<T>((T*)w.p, (const T*)w.res, m, cg, st);
+    }
+    CK(cudaGetLastError());
+    return PGET_OK;
+}
+
+pget_status check_err(Workspace& w, cudaStream_t st) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (e) return fail(PGET_ECUDA, "device error flags 0x%x (sample buffer overflow)", e);
+    return PGET_OK;
+}
+
+void params_dev(const pget_lm_params& p, LmParamsDev* d) {
+    d->eta = p.eta;
+    d->rho_lo = p.rho_lo;
+    d->rho_hi = p.rho_hi;
+    d->nu_up = p.nu_up;
+    d->nu_down = p.nu_down;
+    d->nu_min = p.nu_min;
+    d->nu_max = p.nu_max;
+}
+
+pget_status check_params(const pget_lm_params* p) {
+    if (!p) return fail(PGET_EINVAL, "null params");
+    if (p->max_iters < 0 || p->cg_max_iters < 0) return fail(PGET_EINVAL, "negative iteration count");
+    if (!(p->lambda_max > 0) || !(p->mu_max > 0)) return fail(PGET_EINVAL, "box bounds must be positive");
+    if (!(p->alpha_lambda >= 0) || !(p->alpha_mu >= 0)) return fail(PGET_EINVAL, "prior weights must be >= 0");
+    if (!(p->nu_up >= 1) || !(p->nu_down > 0 && p->nu_down <= 1)) return fail(PGET_EINVAL, "bad nu_up / nu_down");
+    if (p->precision != PGET_F64 && p->precision != PGET_F32 && p->precision != PGET_F32_KAHAN)
+        return fail(PGET_EINVAL, "unknown precision %d", p->precision);
+    return PGET_OK;
+}
+
+// LM solve on device pointers (y, u0 planar inputs copied into the workspace)
+template <typename T>
+pget_status lm_solve_impl(Workspace& w, const pget_lm_params& p, const void* y, const void* lam,
+                          const void* mu, void* lam_out, void* mu_out, pget_lm_report* rep, cudaStream_t st) {
+    const size_t nn = w.nn, M = w.M;
+    const int n = w.g.n;
+    LmState* L = w.lm;
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    CK(cudaEventRecord(ev0, st));
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    if (y != w.yb) CK(cudaMemcpyAsync(w.yb, y, w.elt * M, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(w.u, lam, w.elt * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync((char*)w.u + w.elt * nn, mu, w.elt * nn, cudaMemcpyDeviceToDevice, st));
+    clamp_box<T>((T*)w.u, nn, p.lambda_max, p.mu_max, st);
+    pack_vec<T>(w, w.u, w.pk_u, nullptr, st);
+    T* u = (T*)w.u;
+    // objective and gradient at u_0
+    CK(op_forward(w, w.pk_u, w.U, w.Jp, nullptr, st));
+    sub_dot<T>((const T*)w.Jp, (const T*)w.yb, (T*)w.r, M, w.dpart[0], nullptr, st);
+    finish_sum(w.dpart[0], &L->rtrt, nullptr, st);
+    reg_value<T>(u, n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st);
+    finish_sum(w.dpart[1], &L->Rl, nullptr, st);
+    reg_value<T>(u + nn, n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st);
+    finish_sum(w.dpart[2], &L->Rm, nullptr, st);
+    reg_weights<T>(u, n, p.tv_eps, (T*)w.Wl, nullptr, st);
+    reg_weights<T>(u + nn, n, p.tv_eps, (T*)w.Wm, nullptr, st);
+    RedArgs<T> ga;
+    ga.out = (T*)w.gr;
+    ga.v = u;
+    ga.Wl = (const T*)w.Wl;
+    ga.Wm = (const T*)w.Wm;
+    ga.alpha_l = p.alpha_lambda;
+    ga.alpha_m = p.alpha_mu;
+    ga.nu = 0.0;
+    CK(op_vjp<T>(w, w.pk_u, w.U, w.r, ga, nullptr, st));
+    dot<T>((const T*)w.gr, (const T*)w.gr, 2 * nn, w.dpart[0], nullptr, st);
+    finish_sum(w.dpart[0], &L->gg, nullptr, st);
+    pack_vec<T>(w, w.gr, w.pk_p, nullptr, st);
+    CK(op_jvp(w, w.pk_u, w.pk_p, w.Jp, nullptr, st));
+    dot<T>((const T*)w.Jp, (const T*)w.Jp, M, w.dpart[0], nullptr, st);
+    finish_sum(w.dpart[0], &L->JsJs, nullptr, st);
+    lm_init_f(L, p.nu0_scale, st);
+    LmParamsDev pd;
+    params_dev(p, &pd);
+    const int* no_grad = &L->no_grad;
+    for (int k = 0; k < p.max_iters; ++k) {
+        // gradient and prior weights at a newly accepted iterate
+        reg_weights<T>(u, n, p.tv_eps, (T*)w.Wl, no_grad, st);
+        reg_weights<T>(u + nn, n, p.tv_eps, (T*)w.Wm, no_grad, st);
+        CK(op_vjp<T>(w, w.pk_u, w.U, w.r, ga, no_grad, st));
+        // step from the damped normal equations, rhs = -grad
+        pget_status s = run_cg<T>(w, w.gr, -1.0, 0.0, &L->nu, p, st);
+        if (s != PGET_OK) return s;
+        lm_step<T>(u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, p.lambda_max, p.mu_max, st);
+        pack_vec<T>(w, w.ut, w.pk_ut, nullptr, st);
+        pack_vec<T>(w, w.s, w.pk_p, nullptr, st);
+        lm_model<T>((const T*)w.s, (const T*)w.gr, (const T*)w.Wl, (const T*)w.Wm, n, p.alpha_lambda,
+                    p.alpha_mu, w.dpart[0], w.dpart[1], st);
+        finish_sum(w.dpart[0], &L->sg, nullptr, st);
+        finish_sum(w.dpart[1], &L->sHs, nullptr, st);
+        CK(op_jvp(w, w.pk_u, w.pk_p, w.Jp, nullptr, st));
+        dot<T>((const T*)w.Jp, (const T*)w.Jp, M, w.dpart[2], nullptr, st);
+        finish_sum(w.dpart[2], &L->JsJs, nullptr, st);
+        CK(op_forward(w, w.pk_ut, w.Ut, w.rt, nullptr, st));
+        sub_dot<T>((const T*)w.rt, (const T*)w.yb, (T*)w.rt, M, w.dpart[3], nullptr, st);
+        finish_sum(w.dpart[3], &L->rtrt, nullptr, st);
+        const T* ut = (const T*)w.ut;
+        reg_value<T>(ut, n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st);
+        finish_sum(w.dpart[1], &L->Rl, nullptr, st);
+        reg_value<T>(ut + nn, n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st);
+        finish_sum(w.dpart[2], &L->Rm, nullptr, st);
+        lm_decide(L, pd, st);
+        const int* acc = &L->accept;
+        copy_if<T>((T*)w.u, ut, 2 * nn, acc, st);
+        copy_if<T>((T*)w.r, (const T*)w.rt, M, acc, st);
+        copy_if<T>((T*)w.U, (const T*)w.Ut, w.nslots, acc, st);
+        if (w.f64) {
+            copy_if<double2>((double2*)w.pk_u[0], (const double2*)w.pk_ut[0], w.img_elems, acc, st);
+            copy_if<double2>((double2*)w.pk_u[1], (const double2*)w.pk_ut[1], w.img_elems, acc, st);
+        } else {
+            copy_if<float2>((float2*)w.pk_u[0], (const float2*)w.pk_ut[0], w.img_elems, acc, st);
+            copy_if<float2>((float2*)w.pk_u[1], (const float2*)w.pk_ut[1], w.img_elems, acc, st);
+        }
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemcpyAsync(lam_out, w.u, w.elt * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(mu_out, (char*)w.u + w.elt * nn, w.elt * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(ev1, st));
+    std::unique_ptr<LmState> hl(new LmState);
+    CK(cudaMemcpyAsync(hl.get(), L, sizeof(LmState), cudaMemcpyDeviceToHost, st));
+    pget_status es = check_err(w, st);
+    w.prof->collect();
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (es != PGET_OK) return es;
+    if (rep) {
+        memset(rep, 0, sizeof *rep);
+        rep->iters_run = hl->iter;
+        rep->accepted = hl->accepted;
+        rep->cg_iters_total = hl->cg_total;
+        rep->f0 = hl->f0;
+        rep->f_final = hl->f;
+        rep->nu0 = hl->nu0;
+        rep->nu_final = hl->nu;
+        int kk = std::min(hl->iter, PGET_TRACE);
+        for (int k = 0; k < kk; ++k) {
+            rep->f[k] = hl->tr_f[k];
+            rep->rho[k] = hl->tr_rho[k];
+            rep->nu[k] = hl->tr_nu[k];
+            rep->pred[k] = hl->tr_pred[k];
+            rep->ared[k] = hl->tr_ared[k];
+            rep->acc[k] = hl->tr_acc[k];
+            rep->cg_iters[k] = hl->tr_cg[k];
+        }
+        rep->device_ms = ms;
+        rep->status = std::isfinite(hl->f) ? PGET_OK : PGET_ENUMERIC;
+    }
+    if (!std::isfinite(hl->f)) return fail(PGET_ENUMERIC, "objective is not finite");
+    return PGET_OK;
+}
+
+}  // namespace
+
+// ========================================================================= C ABI
+namespace {
+
+template <typename T>
+static pget_status vjp_impl(Workspace& w, const void* lam, const void* mu, const void* r, void* gl, void* gm,
+                            cudaStream_t st) {
+    pack_pair<T>(w, lam, mu, w.pk_u, st);
+    CK(op_forward(w, w.pk_u, w.U, w.Jp, nullptr, st));
+    RedArgs<T> ra;
+    ra.out = (T*)w.q;
+    CK(op_vjp<T>(w, w.pk_u, w.U, r, ra, nullptr, st));
+    CK(cudaMemcpyAsync(gl, w.q, w.elt * w.nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(gm, (char*)w.q + w.elt * w.nn, w.elt * w.nn, cudaMemcpyDeviceToDevice, st));
+    return PGET_OK;
+}
+
+template <typename T>
+static pget_status cg_impl(Workspace& w, const pget_lm_params& p, const void* lam, const void* mu, double nu,
+                           const void* rhs, void* x, int32_t* iters, cudaStream_t st) {
+    const int n = w.g.n;
+    pack_pair<T>(w, lam, mu, w.pk_u, st);
+    CK(op_forward(w, w.pk_u, w.U, w.Jp, nullptr, st));
+    reg_weights<T>((const T*)lam, n, p.tv_eps, (T*)w.Wl, nullptr, st);
+    reg_weights<T>((const T*)mu, n, p.tv_eps, (T*)w.Wm, nullptr, st);
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    pget_status s = run_cg<T>(w, rhs, 1.0, nu, nullptr, p, st);
+    if (s != PGET_OK) return s;
+    CK(cudaMemcpyAsync(x, w.x, w.elt * 2 * w.nn, cudaMemcpyDeviceToDevice, st));
+    if (iters) {
+        CgState hc;
+        CK(cudaMemcpyAsync(&hc, &w.lm->cg, sizeof hc, cudaMemcpyDeviceToHost, st));
+        s = check_err(w, st);
+        if (s != PGET_OK) return s;
+        *iters = hc.iters;
+    }
+    return PGET_OK;
+}
+
+template <typename T>
+static pget_status init_impl(Workspace& w, const pget_lm_params& p, double mu_init, const void* y, void* lam,
+                             void* mu, cudaStream_t st) {
+    const size_t nn = w.nn;
+    T* u = (T*)w.ut;
+    fill<T>(u, nn, 1.0, st);
+    const double mu0 = std::min(std::max(mu_init, 0.0), p.mu_max);
+    fill<T>(u + nn, nn, mu0, st);
+    pack_vec<T>(w, u, w.pk_ut, nullptr, st);
+    CK(op_forward(w, w.pk_ut, nullptr, w.Jp, nullptr, st));
+    // sum A(1, mu0) and sum y: dot against a vector of ones kept in r
+    fill<T>((T*)w.rt, w.M, 1.0, st);
+    dot<T>((const T*)w.Jp, (const T*)w.rt, w.M, w.dpart[0], nullptr, st);
+    dot<T>((const T*)y, (const T*)w.rt, w.M, w.dpart[1], nullptr, st);
+    std::vector<double> a(kRedBlocks), b(kRedBlocks);
+    CK(cudaMemcpyAsync(a.data(), w.dpart[0], sizeof(double) * kRedBlocks, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(b.data(), w.dpart[1], sizeof(double) * kRedBlocks, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double sa = 0, sy = 0;
+    for (int k = 0; k < kRedBlocks; ++k) {
+        sa += a[k];
+        sy += b[k];
+    }
+    double c = sa > 0 ? sy / sa : 0.0;
+    c = std::min(std::max(c, 0.0), p.lambda_max);
+    fill<T>((T*)lam, nn, c, st);
+    fill<T>((T*)mu, nn, mu0, st);
+    CK(cudaGetLastError());
+    return PGET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pget_version(void) { return "pget-gb300 0.1 (sm_103a)"; }
+
+long long pget_launch_count(void) { return pget::launch_count(); }
+
+pget_status pget_profile_enable(pget_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(PGET_EINVAL, "null ctx");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    ctx->prof.reset();
+    ctx->prof.on = enable != 0;
+    return PGET_OK;
+}
+
+int32_t pget_profile_read(pget_ctx* ctx, pget_kernel_stat* out, int32_t max) {
+    if (!ctx) return 0;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    ctx->prof.collect();
+    int k = 0;
+    for (; k < kPKinds && k < max; ++k) {
+        memset(&out[k], 0, sizeof out[k]);
+        strncpy(out[k].name, kProfNames[k], sizeof out[k].name - 1);
+        out[k].launches = ctx->prof.count[k];
+        out[k].total_ms = ctx->prof.total_ms[k];
+    }
+    return k;
+}
+
+const char* pget_last_error(pget_ctx*) { return g_last_error.c_str(); }
+
+void pget_default_params(pget_lm_params* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->alpha_lambda = 1e-2;
+    o->alpha_mu = 1e-2;
+    o->tv_eps = 1e-3;
+    o->lambda_max = 2.0;
+    o->mu_max = 0.2;
+    o->max_iters = 20;
+    o->cg_max_iters = 30;
+    o->cg_rel_tol = 1e-6;
+    o->nu0_scale = 1e-3;
+    o->nu_up = 4.0;
+    o->nu_down = 0.5;
+    o->eta = 1e-3;
+    o->rho_lo = 0.25;
+    o->rho_hi = 0.75;
+    o->nu_min = 1e-12;
+    o->nu_max = 1e12;
+    o->precision = PGET_F32_KAHAN;
+}
+
+pget_status pget_create(pget_ctx** ctx, int device, size_t budget) {
+    if (!ctx) return fail(PGET_EINVAL, "null ctx pointer");
+    *ctx = nullptr;
+    int nd = 0;
+    cudaError_t e = cudaGetDeviceCount(&nd);
+    if (e != cudaSuccess) return fail(PGET_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= nd) return fail(PGET_EINVAL, "device %d out of range (%d devices)", device, nd);
+    auto c = new (std::nothrow) pget_ctx;
+    if (!c) return fail(PGET_ENOMEM, "host allocation failed");
+    c->device = device;
+    c->budget = budget;
+    *ctx = c;
+    g_last_error.clear();
+    return PGET_OK;
+}
+
+pget_status pget_destroy(pget_ctx* ctx) {
+    if (!ctx) return PGET_OK;
+    {
+        DeviceGuard dg(ctx->device);
+        cudaDeviceSynchronize();
+        ctx->ws.reset();
+        if (ctx->scratch) cudaFree(ctx->scratch);
+    }
+    delete ctx;
+    return PGET_OK;
+}
+
+pget_status pget_forward(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
+                         void* y, void* stream) {
+    if (!ctx || !lam || !mu || !y) return fail(PGET_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    pget_status s = get_workspace(ctx, g, prec, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (w->f64) pack_pair<double>(*w, lam, mu, w->pk_u, st);
+    else pack_pair<float>(*w, lam, mu, w->pk_u, st);
+    CK(op_forward(*w, w->pk_u, nullptr, y, nullptr, st));
+    return PGET_OK;
+}
+
+pget_status pget_jvp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
+                     const void* dlam, const void* dmu, void* dy, void* stream) {
+    if (!ctx || !lam || !mu || !dlam || !dmu || !dy) return fail(PGET_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    pget_status s = get_workspace(ctx, g, prec, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (w->f64) {
+        pack_pair<double>(*w, lam, mu, w->pk_u, st);
+        pack_pair<double>(*w, dlam, dmu, w->pk_p, st);
+    } else {
+        pack_pair<float>(*w, lam, mu, w->pk_u, st);
+        pack_pair<float>(*w, dlam, dmu, w->pk_p, st);
+    }
+    CK(op_jvp(*w, w->pk_u, w->pk_p, dy, nullptr, st));
+    return PGET_OK;
+}
+
+
+pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
+                     const void* r, void* glam, void* gmu, void* stream) {
+    if (!ctx || !lam || !mu || !r || !glam || !gmu) return fail(PGET_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    pget_status s = get_workspace(ctx, g, prec, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    return w->f64 ? vjp_impl<double>(*w, lam, mu, r, glam, gmu, st) : vjp_impl<float>(*w, lam, mu, r, glam, gmu, st);
+}
+
+pget_status pget_reg_apply(pget_ctx* ctx, int32_t n, int32_t prec, double alpha, double eps, const void* u,
+                           const void* v, void* out, double* value_host, void* stream) {
+    if (!ctx || !u || !v || !out) return fail(PGET_EINVAL, "null argument");
+    if (n < 2) return fail(PGET_EINVAL, "n must be >= 2");
+    if (prec != PGET_F64 && prec != PGET_F32 && prec != PGET_F32_KAHAN) return fail(PGET_EINVAL, "unknown precision");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t elt = prec == PGET_F64 ? 8 : 4;
+    const size_t need = elt * (size_t)n * n + sizeof(double) * (kRedBlocks + 1);
+    if (ctx->scratch_bytes < need) {
+        CK(cudaStreamSynchronize(st));
+        if (ctx->scratch) cudaFree(ctx->scratch);
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+        CK(cudaMalloc(&ctx->scratch, need));
+        ctx->scratch_bytes = need;
+    }
+    double* part = (double*)ctx->scratch;
+    void* W = (char*)ctx->scratch + sizeof(double) * (kRedBlocks + 1);
+    if (prec == PGET_F64) {
+        reg_weights<double>((const double*)u, n, eps, (double*)W, nullptr, st);
+        reg_apply<double>((const double*)v, (const double*)W, n, alpha, (double*)out, st);
+        if (value_host) reg_value<double>((const double*)u, n, alpha, eps, part, nullptr, st);
+    } else {
+        reg_weights<float>((const float*)u, n, eps, (float*)W, nullptr, st);
+        reg_apply<float>((const float*)v, (const float*)W, n, alpha, (float*)out, st);
+        if (value_host) reg_value<float>((const float*)u, n, alpha, eps, part, nullptr, st);
+    }
+    CK(cudaGetLastError());
+    if (value_host) {
+        finish_sum(part, part + kRedBlocks, nullptr, st);
+        CK(cudaMemcpyAsync(value_host, part + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return PGET_OK;
+}
+
+
+pget_status pget_cg_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* lam,
+                          const void* mu, double nu, const void* rhs, void* x, int32_t* iters, void* stream) {
+    if (!ctx || !lam || !mu || !rhs || !x) return fail(PGET_EINVAL, "null argument");
+    pget_status s = check_params(p);
+    if (s != PGET_OK) return s;
+    if (!(nu >= 0) || !std::isfinite(nu)) return fail(PGET_EINVAL, "nu must be finite and >= 0");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    s = get_workspace(ctx, g, p->precision, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    return w->f64 ? cg_impl<double>(*w, *p, lam, mu, nu, rhs, x, iters, st)
+                  : cg_impl<float>(*w, *p, lam, mu, nu, rhs, x, iters, st);
+}
+
+
+pget_status pget_initial_guess(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, double mu_init,
+                               const void* y, void* lam, void* mu, void* stream) {
+    if (!ctx || !y || !lam || !mu) return fail(PGET_EINVAL, "null argument");
+    pget_status s = check_params(p);
+    if (s != PGET_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    s = get_workspace(ctx, g, p->precision, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    return w->f64 ? init_impl<double>(*w, *p, mu_init, y, lam, mu, st)
+                  : init_impl<float>(*w, *p, mu_init, y, lam, mu, st);
+}
+
+pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
+                          void* lam_io, void* mu_io, pget_lm_report* rep, void* stream) {
+    if (!ctx || !y || !lam_io || !mu_io) return fail(PGET_EINVAL, "null argument");
+    pget_status s = check_params(p);
+    if (s != PGET_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    s = get_workspace(ctx, g, p->precision, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    return w->f64 ? lm_solve_impl<double>(*w, *p, y, lam_io, mu_io, lam_io, mu_io, rep, st)
+                  : lm_solve_impl<float>(*w, *p, y, lam_io, mu_io, lam_io, mu_io, rep, st);
+}
+
+pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y_host,
+                               void* lam_host, void* mu_host, int32_t init_guess, pget_lm_report* rep, void* stream) {
+    if (!ctx || !y_host || !lam_host || !mu_host) return fail(PGET_EINVAL, "null argument");
+    pget_status s = check_params(p);
+    if (s != PGET_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    s = get_workspace(ctx, g, p->precision, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nn = w->nn, e = w->elt;
+    // inputs: y into the measured-data buffer, the initial guess into x (the solve copies
+    // it into the iterate before CG first writes x)
+    CK(cudaMemcpyAsync(w->yb, y_host, e * w->M, cudaMemcpyHostToDevice, st));
+    void* ld = w->x;
+    void* md = (char*)w->x + e * nn;
+    if (init_guess) {
+        s = w->f64 ? init_impl<double>(*w, *p, 0.01, w->yb, ld, md, st)
+                   : init_impl<float>(*w, *p, 0.01, w->yb, ld, md, st);
+        if (s != PGET_OK) return s;
+    } else {
+        CK(cudaMemcpyAsync(ld, lam_host, e * nn, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(md, mu_host, e * nn, cudaMemcpyHostToDevice, st));
+    }
+    void* lx = w->x;
+    void* mx = (char*)w->x + e * nn;
+    s = w->f64 ? lm_solve_impl<double>(*w, *p, w->yb, lx, mx, w->q, (char*)w->q + e * nn, rep, st)
+               : lm_solve_impl<float>(*w, *p, w->yb, lx, mx, w->q, (char*)w->q + e * nn, rep, st);
+    if (s != PGET_OK) return s;
+    CK(cudaMemcpyAsync(lam_host, w->q, e * nn, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(mu_host, (char*)w->q + e * nn, e * nn, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return PGET_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// kernels.cuh -- device helpers and kernel launch interfaces of the CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "pget_internal.cuh"
+
+namespace pget {
+
+// host-side count of kernel launches made by the library (diagnostics)
+void note_launch(int k = 1);
+long long launch_count();
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+
+// Running sum along a ray; KAHAN selects compensated summation (the compensation holds
+// the rounding excess of the last addition, the value is s - c).
+template <typename T, bool KAHAN> struct Acc {
+    T s, c;
+    __device__ __forceinline__ void init() { s = T(0); c = T(0); }
+    __device__ __forceinline__ void add(T x) {
+        if constexpr (KAHAN) {
+            T y = x - c;
+            T t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += x;
+        }
+    }
+    __device__ __forceinline__ T val() const {
+        if constexpr (KAHAN) return s - c;
+        else return s;
+    }
+};
+
+// Sample position along one ray in the canonical frame of its view.
+//   float paths: 32.32 fixed point, exact steps (no drift along a ray);
+//   double path: X = X0 + j dX evaluated per sample.
+template <typename T> struct Pos;
+
+template <> struct Pos<float> {
+    long long X, Y, dX, dY;
+    __device__ __forceinline__ void init(const ViewDev& v, int i, int j) {
+        X = v.X00 + (long long)i * v.dXr + (long long)j * v.dXs;
+        Y = v.Y00 + (long long)i * v.dYr + (long long)j * v.dYs;
+        dX = v.dXs;
+        dY = v.dYs;
+    }
+    __device__ __forceinline__ void back() {
+        X -= dX;
+        Y -= dY;
+    }
+    __device__ __forceinline__ int ix() const { return (int)(X >> 32); }
+    __device__ __forceinline__ int iy() const { return (int)(Y >> 32); }
+    __device__ __forceinline__ float ax() const {
+        return __uint2float_rn((unsigned)(X & 0xffffffffull)) * 2.3283064365386963e-10f;
+    }
+    __device__ __forceinline__ float ay() const {
+        return __uint2float_rn((unsigned)(Y & 0xffffffffull)) * 2.3283064365386963e-10f;
+    }
+    __device__ __forceinline__ float yf() const { return __ll2float_rn(Y) * 2.3283064365386963e-10f; }
+};
+
+template <> struct Pos<double> {
+    double X0, Y0, dX, dY, X, Y, fx, fy;
+    int j;
+    __device__ __forceinline__ void eval() {
+        X = fma((double)j, dX, X0);
+        Y = fma((double)j, dY, Y0);
+        fx = floor(X);
+        fy = floor(Y);
+    }
+    __device__ __forceinline__ void init(const ViewDev& v, int i, int j_) {
+        X0 = v.X00d + i * v.dXrd;
+        Y0 = v.Y00d + i * v.dYrd;
+        dX = v.dXsd;
+        dY = v.dYsd;
+        j = j_;
+        eval();
+    }
+    __device__ __forceinline__ void back() {
+        --j;
+        eval();
+    }
+    __device__ __forceinline__ int ix() const { return (int)fx; }
+    __device__ __forceinline__ int iy() const { return (int)fy; }
+    __device__ __forceinline__ double ax() const { return X - fx; }
+    __device__ __forceinline__ double ay() const { return Y - fy; }
+    __device__ __forceinline__ float yf() const { return (float)Y; }
+};
+
+enum WalkMode { kFwd = 0, kJvp = 1, kVjp = 2 };
+
+struct WalkArgs {
+    const ViewDev* views;
+    int n, T, P, Yc, nchunks, sb_cap;
+    double h;
+    const void* u_img[2];      // padded interleaved (lambda, mu): [0] normal, [1] transposed
+    const void* p_img[2];      // JVP: padded interleaved (dlambda, dmu)
+    void* slot_val;            // FWD: per-slot ray total out (optional); VJP: in
+    int max_slots, n_det, n_banks, nb, n_sub;
+    const int* det_slot;       // [n_det][n_sub]
+    const double* w;           // [n_sub]
+    void* y_out;               // FWD / JVP: [n_angles][n_det]
+    const void* r_in;          // VJP: [n_angles][n_det]
+    const int* src_off;
+    const int* src_det;
+    const double* src_w;
+    void* gpart;               // VJP: [n_views][2][n][n], pre-flip canonical layout
+    const int* stop;           // optional: skip the launch when *stop != 0
+    int* err;                  // error flags (bit 0: sample buffer overflow)
+};
+
+struct WalkPlan {
+    int threads = 0, Yc = 0, nchunks = 0, sb_cap = 0;
+    size_t smem = 0;
+};
+
+// Plan (threads, rows per chunk, shared memory) for one walk mode.
+WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t smem_budget);
+
+// Launch one walk kernel over all views of the geometry.
+cudaError_t launch_walk(int mode, int precision, const WalkPlan& plan, const WalkArgs& a,
+                        int n_views, cudaStream_t st);
+
+}  // namespace pget

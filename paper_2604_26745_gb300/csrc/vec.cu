@@ -1,0 +1,600 @@
+// vec.cu -- image packing, the view reduction of the VJP, the prior (smoothed TV), the
+// FP64 dot products and the CG / trust-region vector and scalar steps.
+//
+// Vectors u = (lambda, mu) are planar [2][n][n] (lambda block, then mu block).  Dot
+// products accumulate in double per thread, per block (fixed tree) and over blocks in
+// block order (finish kernels), so every result is deterministic.
+#include <cmath>
+
+#include "kernels.cuh"
+#include "vec.cuh"
+
+namespace pget {
+
+// ------------------------------------------------------------------------ packing
+// planar lambda, mu -> padded interleaved images, normal ([iy+1][ix+1]) and transposed
+// ([ix+1][iy+1]); the one-pixel border stays zero (bilinear samples see zero outside).
+template <typename T>
+__global__ void pack_kernel(const T* __restrict__ lam, const T* __restrict__ mu, int n, int P,
+                            typename Vec2<T>::type* __restrict__ out_n,
+                            typename Vec2<T>::type* __restrict__ out_t, const int* skip) {
+    using T2 = typename Vec2<T>::type;
+    if (skip && *skip) return;
+    __shared__ T2 tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        int iy = by + k, ix = bx + threadIdx.x;
+        if (iy < n && ix < n) {
+            T2 v = mk2(lam[(size_t)iy * n + ix], mu[(size_t)iy * n + ix]);
+            out_n[(size_t)(iy + 1) * P + ix + 1] = v;
+            tile[k][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        int ix = bx + k, iy = by + threadIdx.x;
+        if (iy < n && ix < n) out_t[(size_t)(ix + 1) * P + iy + 1] = tile[threadIdx.x][k];
+    }
+}
+
+template <typename T>
+void pack(const T* lam, const T* mu, int n, int P, void* out_n, void* out_t, const int* skip,
+          cudaStream_t st) {
+    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+    pack_kernel<T><<<grid, block, 0, st>>>(lam, mu, n, P, (typename Vec2<T>::type*)out_n,
+                                           (typename Vec2<T>::type*)out_t, skip);
+    note_launch();
+}
+template void pack<float>(const float*, const float*, int, int, void*, void*, const int*, cudaStream_t);
+template void pack<double>(const double*, const double*, int, int, void*, void*, const int*, cudaStream_t);
+
+// ------------------------------------------------------------------------ prior
+// forward differences with a zero-flux border; W = 1/sqrt(|grad u|^2 + eps^2) or 1
+template <typename T>
+__device__ __forceinline__ void grad_at(const T* u, int n, int ix, int iy, T* gx, T* gy) {
+    const size_t i = (size_t)iy * n + ix;
+    *gx = ix < n - 1 ? u[i + 1] - u[i] : T(0);
+    *gy = iy < n - 1 ? u[i + n] - u[i] : T(0);
+}
+
+// alpha grad^T diag(W) grad v at pixel (ix, iy)
+template <typename T>
+__device__ __forceinline__ T reg_at(const T* v, const T* W, T alpha, int n, int ix, int iy) {
+    const size_t i = (size_t)iy * n + ix;
+    T gx, gy, acc = T(0);
+    grad_at(v, n, ix, iy, &gx, &gy);
+    acc -= W[i] * gx + W[i] * gy;
+    if (ix > 0) {
+        T gxl, gyl;
+        grad_at(v, n, ix - 1, iy, &gxl, &gyl);
+        acc += W[i - 1] * gxl;
+    }
+    if (iy > 0) {
+        T gxd, gyd;
+        grad_at(v, n, ix, iy - 1, &gxd, &gyd);
+        acc += W[i - n] * gyd;
+    }
+    return alpha * acc;
+}
+
+template <typename T>
+__global__ void reg_weights_kernel(const T* __restrict__ u, int n, double eps, T* __restrict__ W,
+                                   const int* skip) {
+    if (skip && *skip) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * n) return;
+    const int iy = i / n, ix = i - iy * n;
+    T gx, gy;
+    grad_at(u, n, ix, iy, &gx, &gy);
+    W[i] = eps > 0 ? T(1) / sqrt(gx * gx + gy * gy + (T)(eps * eps)) : T(1);
+}
+
+template <typename T>
+void reg_weights(const T* u, int n, double eps, T* W, const int* skip, cudaStream_t st) {
+    int tot = n * n;
+    reg_weights_kernel<T><<<(tot + 255) / 256, 256, 0, st>>>(u, n, eps, W, skip);
+    note_launch();
+}
+template void reg_weights<float>(const float*, int, double, float*, const int*, cudaStream_t);
+template void reg_weights<double>(const double*, int, double, double*, const int*, cudaStream_t);
+
+template <typename T>
+__global__ void reg_apply_kernel(const T* __restrict__ v, const T* __restrict__ W, int n, double alpha,
+                                 T* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * n) return;
+    const int iy = i / n, ix = i - iy * n;
+    out[i] = reg_at(v, W, (T)alpha, n, ix, iy);
+}
+
+template <typename T>
+void reg_apply(const T* v, const T* W, int n, double alpha, T* out, cudaStream_t st) {
+    int tot = n * n;
+    reg_apply_kernel<T><<<(tot + 255) / 256, 256, 0, st>>>(v, W, n, alpha, out);
+    note_launch();
+}
+template void reg_apply<float>(const float*, const float*, int, double, float*, cudaStream_t);
+template void reg_apply<double>(const double*, const double*, int, double, double*, cudaStream_t);
+
+// ------------------------------------------------------------------ block reduction
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) r += red[w];
+    return r;  // valid in thread 0
+}
+
+// R(u) = alpha sum sqrt(|grad u|^2 + eps^2)  or  alpha/2 sum |grad u|^2 ; per-block partials
+template <typename T>
+__global__ void reg_value_kernel(const T* __restrict__ u, int n, double alpha, double eps,
+                                 double* __restrict__ part, const int* skip) {
+    if (skip && *skip) return;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x) {
+        const int iy = i / n, ix = i - iy * n;
+        T gx, gy;
+        grad_at(u, n, ix, iy, &gx, &gy);
+        double s2 = (double)gx * gx + (double)gy * gy;
+        acc += eps > 0 ? sqrt(s2 + eps * eps) : 0.5 * s2;
+    }
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = alpha * s;
+}
+
+template <typename T>
+void reg_value(const T* u, int n, double alpha, double eps, double* part, const int* skip,
+               cudaStream_t st) {
+    reg_value_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, n, alpha, eps, part, skip);
+    note_launch();
+}
+template void reg_value<float>(const float*, int, double, double, double*, const int*, cudaStream_t);
+template void reg_value<double>(const double*, int, double, double, double*, const int*, cudaStream_t);
+
+// ------------------------------------------------------------------------ dots
+template <typename T>
+__global__ void dot_kernel(const T* __restrict__ a, const T* __restrict__ b, size_t m,
+                           double* __restrict__ part, const int* skip) {
+    if (skip && *skip) return;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename T>
+void dot(const T* a, const T* b, size_t m, double* part, const int* skip, cudaStream_t st) {
+    dot_kernel<T><<<kRedBlocks, 256, 0, st>>>(a, b, m, part, skip);
+    note_launch();
+}
+template void dot<float>(const float*, const float*, size_t, double*, const int*, cudaStream_t);
+template void dot<double>(const double*, const double*, size_t, double*, const int*, cudaStream_t);
+
+// sum kRedBlocks partials (block order) into *dst
+__global__ void finish_sum_kernel(const double* __restrict__ part, double* dst, const int* skip) {
+    if (skip && *skip) return;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < kRedBlocks; ++b) s += part[b];
+        *dst = s;
+    }
+}
+void finish_sum(const double* part, double* dst, const int* skip, cudaStream_t st) {
+    finish_sum_kernel<<<1, 32, 0, st>>>(part, dst, skip);
+    note_launch();
+}
+
+// ---------------------------------------------------------------- view reduction
+// Stage 1: block (tile, view group) sums the partial images of its views over a 32 x 32
+// pixel tile.  Views with a transposed canonical frame wrote [ix][iy]; they are summed
+// in that orientation and transposed once through shared memory.
+template <typename T, bool KAHAN>
+__global__ void reduce_views_kernel(const T* __restrict__ gpart, const int* __restrict__ vtrans, int n,
+                                    int n_views, int groups, T* __restrict__ out2, const int* skip) {
+    using T2 = typename Vec2<T>::type;
+    if (skip && *skip) return;
+    __shared__ T2 tile[32][33];
+    const int tiles_x = (n + 31) / 32;
+    const int tl = blockIdx.x % (tiles_x * tiles_x), grp = blockIdx.x / (tiles_x * tiles_x);
+    const int bx = (tl % tiles_x) * 32, by = (tl / tiles_x) * 32;
+    const int v0 = (int)((long long)n_views * grp / groups), v1 = (int)((long long)n_views * (grp + 1) / groups);
+    const size_t nn = (size_t)n * n;
+    Acc<T, KAHAN> an[2][4], at[2][4];
+    for (int f = 0; f < 2; ++f)
+        for (int k = 0; k < 4; ++k) {
+            an[f][k].init();
+            at[f][k].init();
+        }
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int v = v0; v < v1; ++v) {
+        const T* gp = gpart + (size_t)v * 2 * nn;
+        if (!vtrans[v]) {
+            for (int k = 0; k < 4; ++k) {
+                int iy = by + ty + 8 * k, ix = bx + tx;
+                if (iy < n && ix < n) {
+                    an[0][k].add(gp[(size_t)iy * n + ix]);
+                    an[1][k].add(gp[nn + (size_t)iy * n + ix]);
+                }
+            }
+        } else {
+            for (int k = 0; k < 4; ++k) {
+                int rr = bx + ty + 8 * k, cc = by + tx;  // stored [ix][iy]
+                if (rr < n && cc < n) {
+                    at[0][k].add(gp[(size_t)rr * n + cc]);
+                    at[1][k].add(gp[nn + (size_t)rr * n + cc]);
+                }
+            }
+        }
+    }
+    for (int k = 0; k < 4; ++k) tile[ty + 8 * k][tx] = mk2(at[0][k].val(), at[1][k].val());
+    __syncthreads();
+    T* o = out2 + (size_t)grp * 2 * nn;
+    for (int k = 0; k < 4; ++k) {
+        int iy = by + ty + 8 * k, ix = bx + tx;
+        if (iy < n && ix < n) {
+            T2 tv = tile[tx][ty + 8 * k];
+            o[(size_t)iy * n + ix] = an[0][k].val() + tv.x;
+            o[nn + (size_t)iy * n + ix] = an[1][k].val() + tv.y;
+        }
+    }
+}
+
+// Stage 2: out = sum over groups (+ alpha grad^T W grad v + nu v when v given);
+// per-block partial of <dotv, out> when dotv given.
+template <typename T, bool KAHAN>
+__global__ void reduce_groups_kernel(RedArgs<T> a) {
+    if (a.skip && *a.skip) return;
+    const size_t nn = (size_t)a.n * a.n;
+    double acc = 0.0;
+    const double nu = a.nu_dev ? *a.nu_dev : a.nu;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * nn; e += (size_t)gridDim.x * blockDim.x) {
+        const int f = e >= nn;
+        const size_t i = e - f * nn;
+        Acc<T, KAHAN> s;
+        s.init();
+        for (int g = 0; g < a.groups; ++g) s.add(a.in2[(size_t)g * 2 * nn + e]);
+        T val = s.val();
+        if (a.v) {
+            const int iy = (int)(i / a.n), ix = (int)(i - (size_t)iy * a.n);
+            const T* vf = a.v + f * nn;
+            val += reg_at(vf, f ? a.Wm : a.Wl, (T)(f ? a.alpha_m : a.alpha_l), a.n, ix, iy);
+            val += (T)nu * vf[i];
+        }
+        a.out[e] = val;
+        if (a.dotv) acc += (double)a.dotv[e] * (double)val;
+    }
+    if (a.dotv) {
+        double s = block_sum(acc);
+        if (threadIdx.x == 0) a.part[blockIdx.x] = s;
+    }
+}
+
+template <typename T>
+void reduce_views(const T* gpart, const int* vtrans, int n, int n_views, int groups, T* part2,
+                  const RedArgs<T>& ra, bool kahan, cudaStream_t st) {
+    const int tiles_x = (n + 31) / 32;
+    dim3 block(32, 8);
+    if (kahan)
+        reduce_views_kernel<T, true><<<tiles_x * tiles_x * groups, block, 0, st>>>(gpart, vtrans, n, n_views, groups, part2, ra.skip);
+    else
+        reduce_views_kernel<T, false><<<tiles_x * tiles_x * groups, block, 0, st>>>(gpart, vtrans, n, n_views, groups, part2, ra.skip);
+    RedArgs<T> r2 = ra;
+    r2.in2 = part2;
+    r2.groups = groups;
+    if (kahan)
+        reduce_groups_kernel<T, true><<<kRedBlocks, 256, 0, st>>>(r2);
+    else
+        reduce_groups_kernel<T, false><<<kRedBlocks, 256, 0, st>>>(r2);
+    note_launch(2);
+}
+template void reduce_views<float>(const float*, const int*, int, int, int, float*, const RedArgs<float>&, bool, cudaStream_t);
+template void reduce_views<double>(const double*, const int*, int, int, int, double*, const RedArgs<double>&, bool, cudaStream_t);
+
+// ------------------------------------------------------------------ elementwise
+template <typename T>
+__global__ void sub_dot_kernel(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, size_t m,
+                               double* __restrict__ part, const int* skip) {
+    if (skip && *skip) return;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+        T d = a[i] - b[i];
+        out[i] = d;
+        acc += (double)d * (double)d;
+    }
+    double s = block_sum(acc);
+    if (threadIdx.x == 0 && part) part[blockIdx.x] = s;
+}
+template <typename T>
+void sub_dot(const T* a, const T* b, T* out, size_t m, double* part, const int* skip, cudaStream_t st) {
+    sub_dot_kernel<T><<<kRedBlocks, 256, 0, st>>>(a, b, out, m, part, skip);
+    note_launch();
+}
+template void sub_dot<float>(const float*, const float*, float*, size_t, double*, const int*, cudaStream_t);
+template void sub_dot<double>(const double*, const double*, double*, size_t, double*, const int*, cudaStream_t);
+
+template <typename T>
+__global__ void clamp_kernel(T* __restrict__ u, size_t nn, double lmax, double mmax) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * nn; i += (size_t)gridDim.x * blockDim.x) {
+        const double hi = i < nn ? lmax : mmax;
+        T v = u[i];
+        u[i] = v < T(0) ? T(0) : (v > (T)hi ? (T)hi : v);
+    }
+}
+template <typename T>
+void clamp_box(T* u, size_t nn, double lmax, double mmax, cudaStream_t st) {
+    clamp_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, nn, lmax, mmax);
+    note_launch();
+}
+template void clamp_box<float>(float*, size_t, double, double, cudaStream_t);
+template void clamp_box<double>(double*, size_t, double, double, cudaStream_t);
+
+template <typename T>
+__global__ void fill_kernel(T* __restrict__ u, size_t m, double v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        u[i] = (T)v;
+}
+template <typename T>
+void fill(T* u, size_t m, double v, cudaStream_t st) {
+    fill_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, m, v);
+    note_launch();
+}
+template void fill<float>(float*, size_t, double, cudaStream_t);
+template void fill<double>(double*, size_t, double, cudaStream_t);
+
+// ---------------------------------------------------------------------- CG
+// x = 0, res = b, p = b; partial <b, b>
+template <typename T>
+__global__ void cg_init_kernel(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ res,
+                               T* __restrict__ p, size_t m, double scale_b, double tol,
+                               double* __restrict__ part, CgState* cg) {
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+        T v = (T)scale_b * b[i];
+        x[i] = T(0);
+        res[i] = v;
+        p[i] = v;
+        acc += (double)v * (double)v;
+    }
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cg->stop = 0;
+        cg->iters = 0;
+        cg->tol = tol;
+    }
+}
+
+__global__ void cg_finish_init_kernel(const double* __restrict__ part, CgState* cg) {
+    if (threadIdx.x || blockIdx.x) return;
+    double s = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) s += part[b];
+    cg->rr = s;
+    cg->bnorm = sqrt(s);
+    cg->stop = !(cg->bnorm > 0.0) || !isfinite(s);
+    cg->iters = 0;
+}
+
+// after q = A p and partials of <p, q>
+__global__ void cg_finish_pq_kernel(const double* __restrict__ part, CgState* cg) {
+    if (threadIdx.x || blockIdx.x || cg->stop) return;
+    double s = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) s += part[b];
+    cg->pq = s;
+    if (!(s > 0.0) || !isfinite(s)) {
+        cg->stop = 1;
+        return;
+    }
+    cg->alpha = cg->rr / s;
+}
+
+template <typename T>
+__global__ void cg_update_kernel(T* __restrict__ x, T* __restrict__ res, const T* __restrict__ p,
+                                 const T* __restrict__ q, size_t m, double* __restrict__ part,
+                                 const CgState* cg) {
+    if (cg->stop) return;
+    const T al = (T)cg->alpha;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+        x[i] += al * p[i];
+        T r = res[i] - al * q[i];
+        res[i] = r;
+        acc += (double)r * (double)r;
+    }
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void cg_finish_rr_kernel(const double* __restrict__ part, CgState* cg) {
+    if (threadIdx.x || blockIdx.x || cg->stop) return;
+    double s = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) s += part[b];
+    cg->iters += 1;
+    if (sqrt(s) <= cg->tol * cg->bnorm || !isfinite(s)) {
+        cg->stop = 1;
+        cg->rr = s;
+        return;
+    }
+    cg->beta = s / cg->rr;
+    cg->rr = s;
+}
+
+template <typename T>
+__global__ void cg_pupdate_kernel(T* __restrict__ p, const T* __restrict__ res, size_t m, const CgState* cg) {
+    if (cg->stop) return;
+    const T be = (T)cg->beta;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = res[i] + be * p[i];
+}
+
+template <typename T>
+void cg_init(const T* b, T* x, T* res, T* p, size_t m, double scale_b, double tol, double* part, CgState* cg,
+             cudaStream_t st) {
+    cg_init_kernel<T><<<kRedBlocks, 256, 0, st>>>(b, x, res, p, m, scale_b, tol, part, cg);
+    note_launch();
+    cg_finish_init_kernel<<<1, 32, 0, st>>>(part, cg);
+    note_launch();
+}
+void cg_finish_pq(const double* part, CgState* cg, cudaStream_t st) {
+    cg_finish_pq_kernel<<<1, 32, 0, st>>>(part, cg);
+    note_launch();
+}
+template <typename T>
+void cg_update(T* x, T* res, const T* p, const T* q, size_t m, double* part, CgState* cg, cudaStream_t st) {
+    cg_update_kernel<T><<<kRedBlocks, 256, 0, st>>>(x, res, p, q, m, part, cg);
+    note_launch();
+    cg_finish_rr_kernel<<<1, 32, 0, st>>>(part, cg);
+    note_launch();
+}
+template <typename T>
+void cg_pupdate(T* p, const T* res, size_t m, const CgState* cg, cudaStream_t st) {
+    cg_pupdate_kernel<T><<<kRedBlocks, 256, 0, st>>>(p, res, m, cg);
+    note_launch();
+}
+template void cg_init<float>(const float*, float*, float*, float*, size_t, double, double, double*, CgState*, cudaStream_t);
+template void cg_init<double>(const double*, double*, double*, double*, size_t, double, double, double*, CgState*, cudaStream_t);
+template void cg_update<float>(float*, float*, const float*, const float*, size_t, double*, CgState*, cudaStream_t);
+template void cg_update<double>(double*, double*, const double*, const double*, size_t, double*, CgState*, cudaStream_t);
+template void cg_pupdate<float>(float*, const float*, size_t, const CgState*, cudaStream_t);
+template void cg_pupdate<double>(double*, const double*, size_t, const CgState*, cudaStream_t);
+
+// ------------------------------------------------------------- trust region
+// ut = P_box(u + x), s = ut - u
+template <typename T>
+__global__ void lm_step_kernel(const T* __restrict__ u, const T* __restrict__ x, T* __restrict__ ut,
+                               T* __restrict__ s, size_t nn, double lmax, double mmax) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * nn; i += (size_t)gridDim.x * blockDim.x) {
+        const T hi = (T)(i < nn ? lmax : mmax);
+        T v = u[i] + x[i];
+        v = v < T(0) ? T(0) : (v > hi ? hi : v);
+        ut[i] = v;
+        s[i] = v - u[i];
+    }
+}
+template <typename T>
+void lm_step(const T* u, const T* x, T* ut, T* s, size_t nn, double lmax, double mmax, cudaStream_t st) {
+    lm_step_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, x, ut, s, nn, lmax, mmax);
+    note_launch();
+}
+template void lm_step<float>(const float*, const float*, float*, float*, size_t, double, double, cudaStream_t);
+template void lm_step<double>(const double*, const double*, double*, double*, size_t, double, double, cudaStream_t);
+
+// partials of <s, g> (part_a) and <s, H s> (part_b), H = alpha grad^T W grad per field
+template <typename T>
+__global__ void lm_model_kernel(const T* __restrict__ s, const T* __restrict__ g, const T* __restrict__ Wl,
+                                const T* __restrict__ Wm, int n, double al, double am,
+                                double* __restrict__ part_a, double* __restrict__ part_b) {
+    const size_t nn = (size_t)n * n;
+    double a = 0.0, b = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * nn; e += (size_t)gridDim.x * blockDim.x) {
+        const int f = e >= nn;
+        const size_t i = e - f * nn;
+        const int iy = (int)(i / n), ix = (int)(i - (size_t)iy * n);
+        const T* sf = s + f * nn;
+        T hs = reg_at(sf, f ? Wm : Wl, (T)(f ? am : al), n, ix, iy);
+        a += (double)s[e] * (double)g[e];
+        b += (double)sf[i] * (double)hs;
+    }
+    double sa = block_sum(a);
+    double sb = block_sum(b);
+    if (threadIdx.x == 0) {
+        part_a[blockIdx.x] = sa;
+        part_b[blockIdx.x] = sb;
+    }
+}
+template <typename T>
+void lm_model(const T* s, const T* g, const T* Wl, const T* Wm, int n, double al, double am, double* pa,
+              double* pb, cudaStream_t st) {
+    lm_model_kernel<T><<<kRedBlocks, 256, 0, st>>>(s, g, Wl, Wm, n, al, am, pa, pb);
+    note_launch();
+}
+template void lm_model<float>(const float*, const float*, const float*, const float*, int, double, double, double*, double*, cudaStream_t);
+template void lm_model<double>(const double*, const double*, const double*, const double*, int, double, double, double*, double*, cudaStream_t);
+
+// One thread: predicted and actual decrease, rho (Eq. (12)), acceptance, nu update.
+__global__ void lm_decide_kernel(LmState* L, LmParamsDev P) {
+    if (threadIdx.x || blockIdx.x) return;
+    double pred = -L->sg - 0.5 * L->JsJs - 0.5 * L->sHs;
+    double ft = 0.5 * L->rtrt + L->Rl + L->Rm;
+    double ared = L->f - ft;
+    double rho = (pred > 0.0 && isfinite(ft)) ? ared / pred : -INFINITY;
+    int acc = rho > P.eta;
+    if (acc) L->f = ft;
+    double nu = L->nu;
+    if (rho < P.rho_lo) nu *= P.nu_up;
+    else if (rho > P.rho_hi) nu *= P.nu_down;
+    nu = fmin(fmax(nu, P.nu_min * L->nu0), P.nu_max * L->nu0);
+    L->nu = nu;
+    L->accept = acc;
+    L->no_grad = !acc;
+    int k = L->iter;
+    if (k < PGET_TRACE) {
+        L->tr_f[k] = L->f;
+        L->tr_rho[k] = rho;
+        L->tr_nu[k] = nu;
+        L->tr_pred[k] = pred;
+        L->tr_ared[k] = ared;
+        L->tr_acc[k] = acc;
+        L->tr_cg[k] = L->cg.iters;
+    }
+    L->accepted += acc;
+    L->cg_total += L->cg.iters;
+    L->iter = k + 1;
+}
+void lm_decide(LmState* L, const LmParamsDev& P, cudaStream_t st) { lm_decide_kernel<<<1, 32, 0, st>>>(L, P); }
+
+// f = 1/2 |r|^2 + R_l + R_m from the finished sums (initial objective)
+__global__ void lm_init_f_kernel(LmState* L, double nu0_scale) {
+    if (threadIdx.x || blockIdx.x) return;
+    L->f = 0.5 * L->rtrt + L->Rl + L->Rm;
+    L->f0 = L->f;
+    double nu0 = (L->gg > 0.0) ? nu0_scale * L->JsJs / L->gg : 1.0;
+    if (!(nu0 > 0.0) || !isfinite(nu0)) nu0 = 1.0;
+    L->nu0 = nu0;
+    L->nu = nu0;
+    L->iter = 0;
+    L->accepted = 0;
+    L->cg_total = 0;
+    L->accept = 0;
+    L->no_grad = 1;
+}
+void lm_init_f(LmState* L, double nu0_scale, cudaStream_t st) { lm_init_f_kernel<<<1, 32, 0, st>>>(L, nu0_scale); }
+
+// conditional copy (accepted trial becomes the iterate)
+template <typename T>
+__global__ void copy_if_kernel(T* __restrict__ dst, const T* __restrict__ src, size_t m, const int* flag) {
+    if (!*flag) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+template <typename T>
+void copy_if(T* dst, const T* src, size_t m, const int* flag, cudaStream_t st) {
+    copy_if_kernel<T><<<kRedBlocks, 256, 0, st>>>(dst, src, m, flag);
+    note_launch();
+}
+template void copy_if<float>(float*, const float*, size_t, const int*, cudaStream_t);
+template void copy_if<double>(double*, const double*, size_t, const int*, cudaStream_t);
+template void copy_if<float2>(float2*, const float2*, size_t, const int*, cudaStream_t);
+template void copy_if<double2>(double2*, const double2*, size_t, const int*, cudaStream_t);
+
+// scale: y = c y (in place)
+template <typename T>
+__global__ void scale_kernel(T* __restrict__ y, size_t m, double c) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = (T)c * y[i];
+}
+template <typename T>
+void scale(T* y, size_t m, double c, cudaStream_t st) {
+    scale_kernel<T><<<kRedBlocks, 256, 0, st>>>(y, m, c);
+    note_launch();
+}
+template void scale<float>(float*, size_t, double, cudaStream_t);
+template void scale<double>(double*, size_t, double, cudaStream_t);
+
+}  // namespace pget

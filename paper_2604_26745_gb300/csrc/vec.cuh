@@ -1,0 +1,88 @@
+// vec.cuh -- launch interfaces of vec.cu and the device-resident solver state.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "kernels.cuh"
+
+namespace pget {
+
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs; fixed so reductions are deterministic
+
+struct CgState {
+    double rr, pq, alpha, beta, bnorm, tol;
+    int iters, stop;
+};
+
+struct LmState {
+    double f, f0, nu, nu0;
+    double sg, sHs, JsJs, rtrt, Rl, Rm, gg;
+    int accept, no_grad, iter, accepted, cg_total, pad;
+    CgState cg;
+    double tr_f[PGET_TRACE], tr_rho[PGET_TRACE], tr_nu[PGET_TRACE], tr_pred[PGET_TRACE], tr_ared[PGET_TRACE];
+    int tr_acc[PGET_TRACE], tr_cg[PGET_TRACE];
+};
+
+struct LmParamsDev {
+    double eta, rho_lo, rho_hi, nu_up, nu_down, nu_min, nu_max;
+};
+
+template <typename T> struct RedArgs {
+    const T* in2 = nullptr;      // set by reduce_views
+    int groups = 0;
+    int n = 0;
+    T* out = nullptr;            // [2][n][n]
+    const T* v = nullptr;        // optional: add alpha grad^T W grad v + nu v
+    const T* Wl = nullptr;
+    const T* Wm = nullptr;
+    double alpha_l = 0, alpha_m = 0;
+    double nu = 0;
+    const double* nu_dev = nullptr;  // if set, nu is read from the device
+    const T* dotv = nullptr;     // optional: per-block partials of <dotv, out>
+    double* part = nullptr;
+    const int* skip = nullptr;
+};
+
+template <typename T>
+void pack(const T* lam, const T* mu, int n, int P, void* out_n, void* out_t, const int* skip, cudaStream_t st);
+template <typename T>
+void reg_weights(const T* u, int n, double eps, T* W, const int* skip, cudaStream_t st);
+template <typename T>
+void reg_apply(const T* v, const T* W, int n, double alpha, T* out, cudaStream_t st);
+template <typename T>
+void reg_value(const T* u, int n, double alpha, double eps, double* part, const int* skip, cudaStream_t st);
+template <typename T>
+void dot(const T* a, const T* b, size_t m, double* part, const int* skip, cudaStream_t st);
+void finish_sum(const double* part, double* dst, const int* skip, cudaStream_t st);
+template <typename T>
+void reduce_views(const T* gpart, const int* vtrans, int n, int n_views, int groups, T* part2,
+                  const RedArgs<T>& ra, bool kahan, cudaStream_t st);
+template <typename T>
+void sub_dot(const T* a, const T* b, T* out, size_t m, double* part, const int* skip, cudaStream_t st);
+template <typename T>
+void clamp_box(T* u, size_t nn, double lmax, double mmax, cudaStream_t st);
+template <typename T>
+void fill(T* u, size_t m, double v, cudaStream_t st);
+template <typename T>
+void cg_init(const T* b, T* x, T* res, T* p, size_t m, double scale_b, double tol, double* part, CgState* cg,
+             cudaStream_t st);
+void cg_finish_pq(const double* part, CgState* cg, cudaStream_t st);
+template <typename T>
+void cg_update(T* x, T* res, const T* p, const T* q, size_t m, double* part, CgState* cg, cudaStream_t st);
+template <typename T>
+void cg_pupdate(T* p, const T* res, size_t m, const CgState* cg, cudaStream_t st);
+template <typename T>
+void lm_step(const T* u, const T* x, T* ut, T* s, size_t nn, double lmax, double mmax, cudaStream_t st);
+template <typename T>
+void lm_model(const T* s, const T* g, const T* Wl, const T* Wm, int n, double al, double am, double* pa,
+              double* pb, cudaStream_t st);
+void lm_decide(LmState* L, const LmParamsDev& P, cudaStream_t st);
+void lm_init_f(LmState* L, double nu0_scale, cudaStream_t st);
+template <typename T>
+void copy_if(T* dst, const T* src, size_t m, const int* flag, cudaStream_t st);
+template <typename T>
+void scale(T* y, size_t m, double c, cudaStream_t st);
+
+}  // namespace pget

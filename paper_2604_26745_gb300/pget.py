@@ -1,0 +1,283 @@
+"""Thin ctypes binding of libpget.so (include/pget.h).  Argument marshalling only: every
+step of the hot path runs in the library's CUDA kernels; torch supplies device memory
+and streams.  There is no fallback: if the library is missing, load() raises."""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpget.so")
+
+PGET_OK, PGET_EINVAL, PGET_ENOMEM, PGET_EAGAIN, PGET_ECUDA, PGET_ETIMEOUT, PGET_ENUMERIC, PGET_ENOTFOUND = range(8)
+PGET_F64, PGET_F32, PGET_F32_KAHAN = 0, 1, 2
+PGET_TRACE = 256
+
+_DTYPE = {PGET_F64: torch.float64, PGET_F32: torch.float32, PGET_F32_KAHAN: torch.float32}
+
+
+class PgetError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pget status {status}: {msg}")
+        self.status = status
+
+
+class pget_geometry(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_angles", C.c_int32), ("n_det", C.c_int32),
+                ("n_banks", C.c_int32), ("n_sub", C.c_int32), ("collimator", C.c_int32),
+                ("step", C.c_double), ("fov_radius", C.c_double), ("det_pitch", C.c_double)]
+
+
+class pget_lm_params(C.Structure):
+    _fields_ = [("alpha_lambda", C.c_double), ("alpha_mu", C.c_double), ("tv_eps", C.c_double),
+                ("lambda_max", C.c_double), ("mu_max", C.c_double), ("max_iters", C.c_int32),
+                ("cg_max_iters", C.c_int32), ("cg_rel_tol", C.c_double), ("nu0_scale", C.c_double),
+                ("nu_up", C.c_double), ("nu_down", C.c_double), ("eta", C.c_double),
+                ("rho_lo", C.c_double), ("rho_hi", C.c_double), ("nu_min", C.c_double),
+                ("nu_max", C.c_double), ("precision", C.c_int32)]
+
+
+class pget_lm_report(C.Structure):
+    _fields_ = [("iters_run", C.c_int32), ("accepted", C.c_int32), ("cg_iters_total", C.c_int32),
+                ("status", C.c_int32), ("f0", C.c_double), ("f_final", C.c_double),
+                ("nu0", C.c_double), ("nu_final", C.c_double),
+                ("f", C.c_double * PGET_TRACE), ("rho", C.c_double * PGET_TRACE),
+                ("nu", C.c_double * PGET_TRACE), ("pred", C.c_double * PGET_TRACE),
+                ("ared", C.c_double * PGET_TRACE), ("acc", C.c_int32 * PGET_TRACE),
+                ("cg_iters", C.c_int32 * PGET_TRACE), ("device_ms", C.c_double)]
+
+    def to_dict(self) -> dict:
+        k = min(self.iters_run, PGET_TRACE)
+        return {"iters_run": self.iters_run, "accepted": self.accepted,
+                "cg_iters_total": self.cg_iters_total, "status": self.status, "f0": self.f0,
+                "f_final": self.f_final, "nu0": self.nu0, "nu_final": self.nu_final,
+                "f": list(self.f[:k]), "rho": list(self.rho[:k]), "nu": list(self.nu[:k]),
+                "pred": list(self.pred[:k]), "ared": list(self.ared[:k]),
+                "acc": list(self.acc[:k]), "cg_iters": list(self.cg_iters[:k]),
+                "device_ms": self.device_ms}
+
+
+class pget_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+# exported symbols and their argument types
+_vp = C.c_void_p
+_SIGS = {
+    "pget_create": ([C.POINTER(_vp), C.c_int, C.c_size_t], C.c_int),
+    "pget_destroy": ([_vp], C.c_int),
+    "pget_default_params": ([C.POINTER(pget_lm_params)], None),
+    "pget_forward": ([_vp, C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
+    "pget_jvp": ([_vp, C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "pget_vjp": ([_vp, C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "pget_reg_apply": ([_vp, C.c_int32, C.c_int32, C.c_double, C.c_double, _vp, _vp, _vp,
+                        C.POINTER(C.c_double), _vp], C.c_int),
+    "pget_cg_solve": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
+                       C.c_double, _vp, _vp, C.POINTER(C.c_int32), _vp], C.c_int),
+    "pget_initial_guess": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), C.c_double,
+                            _vp, _vp, _vp, _vp], C.c_int),
+    "pget_lm_solve": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp,
+                       C.POINTER(pget_lm_report), _vp], C.c_int),
+    "pget_lm_solve_host": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
+                            _vp, C.c_int32, C.POINTER(pget_lm_report), _vp], C.c_int),
+    "pget_profile_enable": ([_vp, C.c_int32], C.c_int),
+    "pget_profile_read": ([_vp, C.POINTER(pget_kernel_stat), C.c_int32], C.c_int32),
+    "pget_launch_count": ([], C.c_longlong),
+    "pget_last_error": ([_vp], C.c_char_p),
+    "pget_version": ([], C.c_char_p),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpget.so; raises if it has not been built (no CPU or Python fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list:
+    return sorted(_SIGS)
+
+
+def _check(status: int, ctx=None):
+    if status != PGET_OK:
+        msg = load().pget_last_error(ctx).decode() if _lib is not None else ""
+        raise PgetError(status, msg)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def geometry(n: int, n_angles: int, n_det: int, n_sub: int = 1, collimator: int = 1,
+             n_banks: int = 0, step: float = 0.0, fov_radius: float = 0.0,
+             det_pitch: float = 0.0) -> pget_geometry:
+    return pget_geometry(n, n_angles, n_det, n_banks, n_sub, collimator, step, fov_radius, det_pitch)
+
+
+def default_params(**kw) -> pget_lm_params:
+    p = pget_lm_params()
+    load().pget_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def dtype_of(precision: int) -> torch.dtype:
+    return _DTYPE[precision]
+
+
+class Context:
+    """Owns a pget_ctx (one device, its workspace and memory budget)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        L = load()
+        h = _vp()
+        _check(L.pget_create(C.byref(h), int(device), int(mem_budget_bytes)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pget_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# --------------------------------------------------------------- entry points
+def pget_forward(ctx: Context, g: pget_geometry, precision: int, lam, mu, y=None, stream=None):
+    if y is None:
+        y = torch.empty((g.n_angles, g.n_det), dtype=lam.dtype, device=lam.device)
+    _check(load().pget_forward(ctx.h, C.byref(g), precision, _ptr(lam), _ptr(mu), _ptr(y),
+                               _stream(stream)), ctx.h)
+    return y
+
+
+def pget_jvp(ctx: Context, g: pget_geometry, precision: int, lam, mu, dlam, dmu, dy=None, stream=None):
+    if dy is None:
+        dy = torch.empty((g.n_angles, g.n_det), dtype=lam.dtype, device=lam.device)
+    _check(load().pget_jvp(ctx.h, C.byref(g), precision, _ptr(lam), _ptr(mu), _ptr(dlam),
+                           _ptr(dmu), _ptr(dy), _stream(stream)), ctx.h)
+    return dy
+
+
+def pget_vjp(ctx: Context, g: pget_geometry, precision: int, lam, mu, r, glam=None, gmu=None,
+             stream=None):
+    if glam is None:
+        glam = torch.empty_like(lam)
+    if gmu is None:
+        gmu = torch.empty_like(mu)
+    _check(load().pget_vjp(ctx.h, C.byref(g), precision, _ptr(lam), _ptr(mu), _ptr(r),
+                           _ptr(glam), _ptr(gmu), _stream(stream)), ctx.h)
+    return glam, gmu
+
+
+def pget_reg_apply(ctx: Context, n: int, precision: int, alpha: float, eps: float, u, v, out=None,
+                   want_value: bool = False, stream=None):
+    if out is None:
+        out = torch.empty_like(v)
+    val = C.c_double(0.0)
+    _check(load().pget_reg_apply(ctx.h, n, precision, alpha, eps, _ptr(u), _ptr(v), _ptr(out),
+                                 C.byref(val) if want_value else None, _stream(stream)), ctx.h)
+    return (out, val.value) if want_value else out
+
+
+def pget_cg_solve(ctx: Context, g: pget_geometry, p: pget_lm_params, lam, mu, nu: float, rhs, x=None,
+                  stream=None):
+    if x is None:
+        x = torch.empty_like(rhs)
+    it = C.c_int32(0)
+    _check(load().pget_cg_solve(ctx.h, C.byref(g), C.byref(p), _ptr(lam), _ptr(mu), float(nu),
+                                _ptr(rhs), _ptr(x), C.byref(it), _stream(stream)), ctx.h)
+    return x, it.value
+
+
+def pget_initial_guess(ctx: Context, g: pget_geometry, p: pget_lm_params, y, mu_init: float = 0.01,
+                       stream=None):
+    lam = torch.empty((g.n, g.n), dtype=y.dtype, device=y.device)
+    mu = torch.empty_like(lam)
+    _check(load().pget_initial_guess(ctx.h, C.byref(g), C.byref(p), float(mu_init), _ptr(y),
+                                     _ptr(lam), _ptr(mu), _stream(stream)), ctx.h)
+    return lam, mu
+
+
+def pget_lm_solve(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam, mu, stream=None):
+    """Solve in place (lam, mu: initial guess in, result out); returns the report dict."""
+    rep = pget_lm_report()
+    _check(load().pget_lm_solve(ctx.h, C.byref(g), C.byref(p), _ptr(y), _ptr(lam), _ptr(mu),
+                                C.byref(rep), _stream(stream)), ctx.h)
+    return rep.to_dict()
+
+
+def pget_lm_solve_host(ctx: Context, g: pget_geometry, p: pget_lm_params, y_host, lam_host,
+                       mu_host, init_guess: bool = True, stream=None):
+    """Host-buffer solve (y_host, lam_host, mu_host: CPU tensors, pinned for async copies)."""
+    for t in (y_host, lam_host, mu_host):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("host tensors must be contiguous CPU tensors")
+    rep = pget_lm_report()
+    _check(load().pget_lm_solve_host(ctx.h, C.byref(g), C.byref(p), y_host.data_ptr(),
+                                     lam_host.data_ptr(), mu_host.data_ptr(), int(bool(init_guess)),
+                                     C.byref(rep), _stream(stream)), ctx.h)
+    return rep.to_dict()
+
+
+def pget_profile_enable(ctx: Context, enable: bool = True):
+    _check(load().pget_profile_enable(ctx.h, int(bool(enable))), ctx.h)
+
+
+def pget_profile_read(ctx: Context) -> dict:
+    arr = (pget_kernel_stat * 8)()
+    k = load().pget_profile_read(ctx.h, arr, 8)
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms}
+            for i in range(k)}
+
+
+def pget_launch_count() -> int:
+    return int(load().pget_launch_count())
+
+
+def pget_version() -> str:
+    return load().pget_version().decode()
+
+
+def fov_radius(g: pget_geometry) -> float:
+    return g.fov_radius if g.fov_radius > 0 else g.n / math.sqrt(2.0)

@@ -18,3 +18,26 @@ def O():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def torch():
+    import torch as _torch
+    if not _torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    return _torch
+
+
+@pytest.fixture(scope="session")
+def P(torch):
+    from paper_2604_26745_gb300 import build, pget
+    build.build()
+    pget.load()
+    return pget
+
+
+@pytest.fixture(scope="session")
+def ctx(P):
+    c = P.Context(0)
+    yield c
+    c.close()

@@ -1,0 +1,125 @@
+"""GPU parity of the CG solve (Eq. (9)) and the LM iteration (Sec. 2.2, 3.1) against the
+FP64 oracle on identical seeded inputs (noisy data drawn once on the host)."""
+import numpy as np
+import pytest
+
+from paper_2604_26745_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel2(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _problem(O, n, na, nd, S, n_lat, radius, counts, seed):
+    go = O.geom(n, na, nd, n_sub=S)
+    ph = synth.lattice_phantom(n, n_lat, radius=radius, seed=1000 + seed)
+    y = synth.poisson_noise(O.forward(go, ph.lam, ph.mu), counts, 2000 + seed)
+    return go, ph, y
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_cg_parity(ctx, O, P, torch, prec):
+    """Before CG converges its iterates are a smooth function of the data, so the GPU
+    and oracle trajectories agree to rounding (10 steps).  Run to a 1e-10 residual both
+    land on the same solution within the conditioning of the system; past that point
+    CG iterates chase rounding noise (a 1e-15 change of the right-hand side moves the
+    oracle's own 25-step iterate by ~1e-7), so no tighter comparison is meaningful."""
+    n, na, nd, S = 24, 24, 182, 3
+    go, ph, y = _problem(O, n, na, nd, S, 3, 2.0, 1e4, 1)
+    g = P.geometry(n, na, nd, n_sub=S)
+    dt = P.dtype_of(prec)
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    b = np.random.default_rng(5).standard_normal(2 * n * n)
+    for its, nu, tol_cg, tol in ((10, 0.5, 1e-14, 1e-9 if prec == 0 else 2e-4),
+                                 (600, 50.0, 1e-9, 1e-6 if prec == 0 else 2e-3)):
+        pr = O.default_params(cg_max_iters=its, cg_rel_tol=tol_cg)
+        Wl = O.reg_weights(ph.lam, pr.tv_eps)
+        Wm = O.reg_weights(ph.mu, pr.tv_eps)
+        x_ref, it_ref = O.cg(go, pr, ph.lam, ph.mu, Wl, Wm, nu, b)
+        p = P.default_params(cg_max_iters=its, cg_rel_tol=tol_cg if prec == 0 else 1e-6, precision=prec)
+        x, it = P.pget_cg_solve(ctx, g, p, t(ph.lam), t(ph.mu), nu, t(b))
+        if its == 10:
+            assert it == it_ref == 10
+        else:
+            assert it < its and it_ref < its
+            if prec == 0:
+                assert abs(it - it_ref) <= 5
+        assert rel2(x.cpu().numpy(), x_ref) <= tol, (its, rel2(x.cpu().numpy(), x_ref))
+
+
+def test_initial_guess_parity(ctx, O, P, torch):
+    go, ph, y = _problem(O, 32, 30, 91, 1, 4, 2.0, 1e4, 2)
+    l0, m0 = O.initial_guess(go, y, mu_init=0.01)
+    g = P.geometry(32, 30, 91)
+    p = P.default_params(precision=0)
+    lam, mu = P.pget_initial_guess(ctx, g, p, torch.tensor(y, device="cuda"), 0.01)
+    assert abs(lam[0, 0].item() - l0[0, 0]) <= 1e-12 * l0[0, 0]
+    assert torch.all(mu == 0.01)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4), (1, 3e-4)])
+def test_lm_parity_stable_regime(ctx, O, P, torch, prec, tol):
+    """Six LM iterations with 8 CG steps each: in this regime the iteration is a smooth
+    function of its inputs (the oracle moves by 1e-14 under a 1e-15 change of the data),
+    so the GPU must reproduce the oracle's accept/reject pattern, objective trace and
+    iterate to rounding."""
+    n, na, nd, S = 32, 30, 182, 3
+    go, ph, y = _problem(O, n, na, nd, S, 4, 2.5, 1e4, 3)
+    pr = O.default_params(max_iters=6, cg_max_iters=8, cg_rel_tol=1e-10)
+    l0, m0 = O.initial_guess(go, y)
+    lr, mr, rep_ref = O.lm(go, pr, y, l0, m0)
+    g = P.geometry(n, na, nd, n_sub=S)
+    p = P.default_params(max_iters=6, cg_max_iters=8, cg_rel_tol=1e-10, precision=prec)
+    dt = P.dtype_of(prec)
+    lam = torch.tensor(l0, dtype=dt, device="cuda")
+    mu = torch.tensor(m0, dtype=dt, device="cuda")
+    rep = P.pget_lm_solve(ctx, g, p, torch.tensor(y, dtype=dt, device="cuda"), lam, mu)
+    assert rep["acc"] == rep_ref["acc"] and sum(rep["acc"]) >= 2
+    assert rel2(lam.cpu().numpy(), lr) <= tol
+    assert rel2(mu.cpu().numpy(), mr) <= tol
+    np.testing.assert_allclose(rep["f"], rep_ref["f"], rtol=max(tol, 1e-12))
+    np.testing.assert_allclose(rep["nu"], rep_ref["nu"], rtol=max(tol, 1e-12))
+    assert rep["cg_iters"] == rep_ref["cg_iters"]
+
+
+def test_lm_c1_against_noise_floor(ctx, O, P, torch):
+    """The plain-LM FP64 configuration (64 x 64, 9 x 9 rods r = 3, 90 angles x 91
+    detectors, 1 sub-ray, Poisson 1e4, 10 LM iterations, CG <= 50, TV prior alpha 1e-2).
+    With 50 CG steps the finite-precision iteration amplifies rounding (the oracle itself
+    moves by ~1e-3 under a 1e-15 change of the data), so the GPU result is required to be
+    as close to the oracle as the oracle is to itself under such perturbations (3x the
+    larger of two draws), with the same accept pattern and a bitwise-reproducible run."""
+    n = 64
+    go = O.geom(n, 90, 91, n_sub=1)
+    ph = synth.lattice_phantom(n, 9, radius=3.0, seed=1000)
+    y = synth.poisson_noise(O.forward(go, ph.lam, ph.mu), 1e4, 2000)
+    pr = O.default_params(max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10)
+    l0, m0 = O.initial_guess(go, y)
+    lr, mr, rep_ref = O.lm(go, pr, y, l0, m0)
+    floor_l = floor_m = floor_f = 0.0
+    for k in range(2):
+        y2 = y * (1 + 1e-15 * np.random.default_rng(k).standard_normal(y.shape))
+        l2, m2, r2 = O.lm(go, pr, y2, l0, m0)
+        floor_l = max(floor_l, rel2(l2, lr))
+        floor_m = max(floor_m, rel2(m2, mr))
+        floor_f = max(floor_f, abs(r2["f_final"] - rep_ref["f_final"]))
+    g = P.geometry(n, 90, 91, n_sub=1)
+    p = P.default_params(max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10, precision=P.PGET_F64)
+    outs = []
+    for _ in range(2):
+        lam = torch.tensor(l0, device="cuda")
+        mu = torch.tensor(m0, device="cuda")
+        rep = P.pget_lm_solve(ctx, g, p, torch.tensor(y, device="cuda"), lam, mu)
+        outs.append((lam.cpu().numpy(), mu.cpu().numpy(), rep))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    lam, mu, rep = outs[0]
+    assert rep["acc"] == rep_ref["acc"]
+    assert rel2(lam, lr) <= 3 * floor_l + 1e-9, (rel2(lam, lr), floor_l)
+    assert rel2(mu, mr) <= 3 * floor_m + 1e-9, (rel2(mu, mr), floor_m)
+    assert abs(rep["f_final"] - rep_ref["f_final"]) <= 3 * floor_f + 1e-9 * rep_ref["f_final"]
+    # the reconstruction improved on the initial guess
+    assert rel2(lam, ph.lam) < rel2(l0, ph.lam) and rel2(mu, ph.mu) < rel2(m0, ph.mu)

@@ -1,0 +1,109 @@
+"""GPU parity of the operators (forward, JVP, VJP, prior) against the FP64 oracle, called
+through the C ABI on identical seeded inputs.
+
+Tolerances (relative, max-norm over the output unless stated):
+  PGET_F64        1e-12  (same arithmetic as the oracle up to rounding order and exp)
+  PGET_F32_KAHAN  sinogram 2e-6, gradient 2e-5: float exp(-E) carries |E| 2^-24 relative
+                  error (E up to ~10 here), positions are exact (32.32 fixed point)
+  PGET_F32        sinogram 2e-5, gradient 1e-4 (uncompensated float sums of ~200 terms)
+"""
+import numpy as np
+import pytest
+
+from paper_2604_26745_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: (1e-12, 1e-12), 2: (2e-6, 2e-5), 1: (2e-5, 1e-4)}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = {
+    # name: (n, n_angles, n_det, n_sub, collimator, n_lat)
+    "c1_like": (32, 30, 91, 1, 1, 4),
+    "two_banks_s5": (40, 36, 182, 5, 1, 4),
+    "box_even_s4": (36, 20, 182, 4, 0, 3),
+    "odd_n_s3": (27, 17, 91, 3, 1, 3),
+}
+
+
+def _inputs(n, n_lat, seed):
+    ph = synth.lattice_phantom(n, n_lat, seed=seed, jitter=0.7)
+    rs = np.random.default_rng(seed)
+    return ph.lam, ph.mu, rs.standard_normal((n, n)), 0.01 * rs.standard_normal((n, n))
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("prec", [0, 2, 1])
+def test_forward_jvp_vjp_parity(ctx, O, P, torch, case, prec):
+    n, na, nd, S, col, nl = CASES[case]
+    lam, mu, dl, dm = _inputs(n, nl, 100 + n)
+    go = O.geom(n, na, nd, n_sub=S, collimator=col)
+    gg = P.geometry(n, na, nd, n_sub=S, collimator=col)
+    dt = P.dtype_of(prec)
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    tol_y, tol_g = TOL[prec]
+    y = P.pget_forward(ctx, gg, prec, t(lam), t(mu))
+    assert rel(y.cpu().numpy(), O.forward(go, lam, mu)) <= tol_y
+    dy = P.pget_jvp(ctx, gg, prec, t(lam), t(mu), t(dl), t(dm))
+    assert rel(dy.cpu().numpy(), O.jvp(go, lam, mu, dl, dm)) <= 4 * tol_y
+    r = np.random.default_rng(7).standard_normal((na, nd))
+    gl, gm = P.pget_vjp(ctx, gg, prec, t(lam), t(mu), t(r))
+    ol, om = O.vjp(go, lam, mu, r)
+    assert rel(gl.cpu().numpy(), ol) <= tol_g
+    assert rel(gm.cpu().numpy(), om) <= tol_g
+
+
+def test_adjoint_identity_gpu(ctx, P, torch):
+    n, na, nd = 48, 40, 182
+    lam, mu, dl, dm = _inputs(n, 5, 3)
+    g = P.geometry(n, na, nd, n_sub=5)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    r = np.random.default_rng(9).standard_normal((na, nd))
+    Jx = P.pget_jvp(ctx, g, 0, t(lam), t(mu), t(dl), t(dm)).cpu().numpy()
+    gl, gm = P.pget_vjp(ctx, g, 0, t(lam), t(mu), t(r))
+    lhs = float(np.sum(Jx * r))
+    rhs = float(np.sum(dl * gl.cpu().numpy()) + np.sum(dm * gm.cpu().numpy()))
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Jx) * np.linalg.norm(r) * 10
+
+
+def test_vjp_deterministic(ctx, P, torch):
+    n, na, nd = 64, 45, 182
+    lam, mu, _, _ = _inputs(n, 6, 5)
+    g = P.geometry(n, na, nd, n_sub=5)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    r = t(np.random.default_rng(2).standard_normal((na, nd)))
+    a1 = [x.clone() for x in P.pget_vjp(ctx, g, 2, t(lam), t(mu), r)]
+    a2 = P.pget_vjp(ctx, g, 2, t(lam), t(mu), r)
+    assert torch.equal(a1[0], a2[0]) and torch.equal(a1[1], a2[1])
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("eps", [1e-3, -1.0])
+def test_prior_parity(ctx, O, P, torch, prec, eps):
+    n = 45
+    ph = synth.lattice_phantom(n, 4, seed=11)
+    v = np.random.default_rng(4).standard_normal((n, n))
+    dt = P.dtype_of(prec)
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    out, val = P.pget_reg_apply(ctx, n, prec, 0.02, eps, t(ph.lam), t(v), want_value=True)
+    W = O.reg_weights(ph.lam, eps)
+    ref = O.reg_apply(W, v, 0.02)
+    tol = 1e-12 if prec == 0 else 5e-5
+    assert rel(out.cpu().numpy(), ref) <= tol
+    assert abs(val - O.reg_value(ph.lam, 0.02, eps)) <= tol * abs(val)
+
+
+def test_invalid_geometry_is_einval(ctx, P, torch):
+    x = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(P.PgetError) as e:
+        P.pget_forward(ctx, P.geometry(1, 4, 91), 2, x, x, torch.zeros((4, 91), device="cuda"))
+    assert e.value.status == P.PGET_EINVAL
+    with pytest.raises(P.PgetError) as e:
+        P.pget_forward(ctx, P.geometry(8, 4, 91, n_sub=0), 2, x, x, torch.zeros((4, 91), device="cuda"))
+    assert e.value.status == P.PGET_EINVAL
