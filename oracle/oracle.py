@@ -112,6 +112,7 @@ def lib():
         L.og_initial_guess.argtypes = [gp, dp, C.c_double, C.c_double, C.c_double, dp, dp]
         L.og_geom_info.argtypes = [gp, C.POINTER(C.c_int32), dp, dp, C.POINTER(C.c_int32)]
         L.og_num_threads.restype = C.c_int
+        L.og_set_vjp_chunks.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -241,6 +242,12 @@ def initial_guess(g: Geom, y, mu_init=0.01, lambda_max=2.0, mu_max=0.2):
                               float(mu_max), _p(lam), _p(mu)):
         raise ValueError("invalid geometry")
     return lam, mu
+
+
+def set_vjp_chunks(c: int = 32) -> None:
+    """Summation order of the VJP scatter (angle chunks, summed in order); the default 32
+    is what every other result uses.  Only the rounding changes."""
+    lib().og_set_vjp_chunks(int(c))
 
 
 def num_threads() -> int:

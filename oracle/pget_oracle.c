@@ -296,7 +296,12 @@ static void og_ray_vjp(const og_ctx* o, const og_ray* ry, const double* lam, con
     }
 }
 
-#define OG_CHUNKS 32
+/* Angle chunks of the VJP scatter.  The chunks are summed in order, so the result does
+ * not depend on the thread count; changing the chunk count only changes the summation
+ * order (a rounding-level change used by the tests to measure rounding sensitivity). */
+static int og_vjp_chunks = 32;
+
+void og_set_vjp_chunks(int c) { og_vjp_chunks = c > 0 ? c : 32; }
 
 int og_vjp(const og_geom* gin, const double* lam, const double* mu, const double* r,
            double* gl, double* gm) {
@@ -306,7 +311,7 @@ int og_vjp(const og_geom* gin, const double* lam, const double* mu, const double
     double* u = malloc(sizeof(double) * S);
     double* w = malloc(sizeof(double) * S);
     og_subrays(&o, u, w);
-    int nch = o.g.n_angles < OG_CHUNKS ? o.g.n_angles : OG_CHUNKS;
+    int nch = o.g.n_angles < og_vjp_chunks ? o.g.n_angles : og_vjp_chunks;
     /* one private image pair per fixed angle chunk, summed in chunk order: the result
      * does not depend on the thread count */
     double* part = calloc((size_t)nch * 2 * np, sizeof(double));

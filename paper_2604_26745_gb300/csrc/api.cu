@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -112,10 +113,11 @@ struct Workspace {
     ViewDev* d_views = nullptr;
     int* d_vtrans = nullptr;
     int* d_det_slot = nullptr;
-    double* d_w = nullptr;
+    void* d_w = nullptr;        // sub-ray weights in the element type of the path
     int* d_src_off = nullptr;
     int* d_src_det = nullptr;
-    double* d_src_w = nullptr;
+    void* d_src_w = nullptr;    // per-slot sub-ray weights in the element type of the path
+    int2* d_clip = nullptr;
     void* pk_u[2] = {nullptr, nullptr};
     void* pk_ut[2] = {nullptr, nullptr};
     void* pk_p[2] = {nullptr, nullptr};
@@ -162,7 +164,7 @@ static size_t workspace_bytes(const Geometry& g, int prec, int groups) {
     b += (size_t)groups * 2 * nn * elt;
     b += 4 * kRedBlocks * 8 + sizeof(LmState) + 64;
     b += V * sizeof(ViewDev) + V * 4 + (size_t)g.n_det * g.n_sub * 4 + g.n_sub * 8;
-    b += g.src_off.size() * 4 + g.src_det.size() * 12;
+    b += g.src_off.size() * 4 + g.src_det.size() * 12 + g.clip.size() * 4;
     return b;
 }
 
@@ -230,11 +232,18 @@ pget_status get_workspace(pget_ctx* ctx, const pget_geometry* gin, int prec, Wor
     w->M = (size_t)G.n_angles * G.n_det;
     w->nslots = (size_t)V * G.max_slots;
     w->img_elems = (size_t)(G.n + 2) * w->P;
-    const size_t budget_smem = 100 * 1024;
-    w->pf = plan_walk(G, w->P, kFwd, w->f64, budget_smem);
-    w->pj = plan_walk(G, w->P, kJvp, w->f64, budget_smem);
-    w->pv = plan_walk(G, w->P, kVjp, w->f64, budget_smem);
+    // shared memory per CTA: three CTAs of up to 1024 threads share an SM's 227 KB;
+    // PGET_SMEM_KB_{FWD,JVP,VJP} override for tuning
+    auto budget = [](const char* env, size_t kb) {
+        const char* v = getenv(env);
+        if (v && atoi(v) > 0) kb = (size_t)atoi(v);
+        return kb * 1024;
+    };
+    w->pf = plan_walk(G, w->P, kFwd, w->f64, budget("PGET_SMEM_KB_FWD", 64));
+    w->pj = plan_walk(G, w->P, kJvp, w->f64, budget("PGET_SMEM_KB_JVP", 64));
+    w->pv = plan_walk(G, w->P, kVjp, w->f64, budget("PGET_SMEM_KB_VJP", 72));
     const size_t e = w->elt, e2 = 2 * e;
+    (void)e2;
     CK(w->alloc(&w->d_views, sizeof(ViewDev) * V));
     CK(cudaMemcpy(w->d_views, G.views.data(), sizeof(ViewDev) * V, cudaMemcpyHostToDevice));
     std::vector<int> vt(V);
@@ -243,14 +252,21 @@ pget_status get_workspace(pget_ctx* ctx, const pget_geometry* gin, int prec, Wor
     CK(cudaMemcpy(w->d_vtrans, vt.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_det_slot, sizeof(int) * G.det_slot.size()));
     CK(cudaMemcpy(w->d_det_slot, G.det_slot.data(), sizeof(int) * G.det_slot.size(), cudaMemcpyHostToDevice));
-    CK(w->alloc(&w->d_w, sizeof(double) * G.w.size()));
-    CK(cudaMemcpy(w->d_w, G.w.data(), sizeof(double) * G.w.size(), cudaMemcpyHostToDevice));
+    auto upload_t = [&](void** dst, const std::vector<double>& src) -> cudaError_t {
+        cudaError_t er = w->alloc(dst, e * src.size());
+        if (er != cudaSuccess) return er;
+        if (w->f64) return cudaMemcpy(*dst, src.data(), 8 * src.size(), cudaMemcpyHostToDevice);
+        std::vector<float> f(src.begin(), src.end());
+        return cudaMemcpy(*dst, f.data(), 4 * f.size(), cudaMemcpyHostToDevice);
+    };
+    CK(upload_t(&w->d_w, G.w));
+    CK(w->alloc(&w->d_clip, sizeof(int) * G.clip.size()));
+    CK(cudaMemcpy(w->d_clip, G.clip.data(), sizeof(int) * G.clip.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_src_off, sizeof(int) * G.src_off.size()));
     CK(cudaMemcpy(w->d_src_off, G.src_off.data(), sizeof(int) * G.src_off.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_src_det, sizeof(int) * G.src_det.size()));
     CK(cudaMemcpy(w->d_src_det, G.src_det.data(), sizeof(int) * G.src_det.size(), cudaMemcpyHostToDevice));
-    CK(w->alloc(&w->d_src_w, sizeof(double) * G.src_w.size()));
-    CK(cudaMemcpy(w->d_src_w, G.src_w.data(), sizeof(double) * G.src_w.size(), cudaMemcpyHostToDevice));
+    CK(upload_t(&w->d_src_w, G.src_w));
     for (int l = 0; l < 2; ++l) {
         CK(w->alloc(&w->pk_u[l], e2 * w->img_elems));
         CK(w->alloc(&w->pk_ut[l], e2 * w->img_elems));
@@ -297,6 +313,7 @@ WalkArgs base_args(const Workspace& w) {
     a.src_off = w.d_src_off;
     a.src_det = w.d_src_det;
     a.src_w = w.d_src_w;
+    a.clip = w.d_clip;
     a.err = w.err;
     return a;
 }
@@ -407,7 +424,7 @@ pget_status check_err(Workspace& w, cudaStream_t st) {
     int e = 0;
     CK(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (e) return fail(PGET_ECUDA, "device error flags 0x%x (sample buffer overflow)", e);
+    if (e) return fail(PGET_ECUDA, "device error flags 0x%x (adjoint stencil bound)", e);
     return PGET_OK;
 }
 

@@ -147,6 +147,33 @@ pget_status build_geometry(const pget_geometry& in, Geometry* G, std::string* ms
             g.views[(size_t)a * g.n_banks + b] = v;
             g.views_transposed += v.transposed;
         }
+    // conservative per-ray sample ranges (host double arithmetic, once per geometry)
+    g.clip.assign((size_t)g.views.size() * g.max_slots * 2, 0);
+    for (size_t vv = 0; vv < g.views.size(); ++vv) {
+        const ViewDev& v = g.views[vv];
+        for (int i = 0; i < g.max_slots; ++i) {
+            int* c = &g.clip[(vv * g.max_slots + i) * 2];
+            c[0] = 0;
+            c[1] = -1;
+            if (i >= v.n_slots) continue;
+            double X0 = v.X00d + i * v.dXrd, Y0 = v.Y00d + i * v.dYrd;
+            double lo = 0.0, hi = g.T - 1.0;
+            lo = std::max(lo, std::ceil((-1.0 - Y0) / v.dYsd) - 1.0);
+            hi = std::min(hi, std::floor((g.n - Y0) / v.dYsd) + 1.0);
+            if (std::fabs(v.dXsd) > 1e-9) {
+                double a = (-1.0 - X0) / v.dXsd, b = (g.n - X0) / v.dXsd;
+                if (a > b) std::swap(a, b);
+                lo = std::max(lo, std::ceil(a) - 1.0);
+                hi = std::min(hi, std::floor(b) + 1.0);
+            } else if (X0 < -1.0 - 1e-6 || X0 > g.n + 1e-6) {
+                hi = lo - 1.0;
+            }
+            if (hi >= lo) {
+                c[0] = (int)lo;
+                c[1] = (int)hi;
+            }
+        }
+    }
     char key[256];
     snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%.17g/%.17g/%.17g", g.n, g.n_angles, g.n_det,
              g.n_banks, g.n_sub, g.collimator, g.h, g.r, g.p);

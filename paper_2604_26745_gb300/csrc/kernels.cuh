@@ -112,12 +112,13 @@ struct WalkArgs {
     void* slot_val;            // FWD: per-slot ray total out (optional); VJP: in
     int max_slots, n_det, n_banks, nb, n_sub;
     const int* det_slot;       // [n_det][n_sub]
-    const double* w;           // [n_sub]
+    const void* w;             // [n_sub] sub-ray weights (element type of the path)
+    const int2* clip;          // [n_views * max_slots] conservative sample range per ray
     void* y_out;               // FWD / JVP: [n_angles][n_det]
     const void* r_in;          // VJP: [n_angles][n_det]
     const int* src_off;
     const int* src_det;
-    const double* src_w;
+    const void* src_w;         // weights of the sub-rays on each slot (element type of the path)
     void* gpart;               // VJP: [n_views][2][n][n], pre-flip canonical layout
     const int* stop;           // optional: skip the launch when *stop != 0
     int* err;                  // error flags (bit 0: sample buffer overflow)

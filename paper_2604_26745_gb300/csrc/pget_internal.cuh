@@ -52,6 +52,9 @@ struct Geometry {
     std::vector<int> src_det;         // detector index within [0, n_det)
     std::vector<double> src_w;        // its weight
     std::vector<ViewDev> views;       // [n_angles * n_banks], view v = a * n_banks + b
+    // per (view, slot): conservative sample range [jlo, jhi] whose base pixel can lie in
+    // [-1, n-1]^2 (the kernels test every sample exactly); empty rays have jhi < jlo
+    std::vector<int> clip;            // [n_views * max_slots * 2]
     int views_transposed = 0;
     std::string key;                  // identifies the geometry for workspace caching
 };

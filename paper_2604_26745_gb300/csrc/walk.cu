@@ -11,12 +11,20 @@
 //   VJP (adjoint of Eq. (2)):  per sample   g_lambda = rho h exp(-E_j)
 //                                           g_mu = -rho h^2 (sum_{l<j} lambda_l e_l + lambda_j e_j / 2)
 //     with rho = sum of w_k r over the sub-rays on this slot; the far-side prefix is the
-//     ray total (from the forward pass) minus the detector-side suffix.  The samples of a
-//     chunk are kept in shared memory and every pixel of the chunk's rows then GATHERS
-//     the bilinear contributions of the samples whose footprint covers it (no atomics).
-//     Pixel rows shared by two chunks are carried in shared memory.  Each view writes
-//     its own partial image; reduce_views sums them in a fixed order.
+//     ray total (from the forward pass) minus the detector-side suffix.
+//
+// Scatter-free adjoint.  A sample touches the four pixels of its bilinear cell: columns
+// ix0, ix0+1 of rows iy0, iy0+1.  Every ray crosses a pixel row with at most three
+// samples whose cells touch that row (the canonical frame guarantees |dX| <= |dY| per
+// step), and those cells lie within four consecutive columns.  While walking, the
+// thread that owns a ray accumulates, for each row of the current chunk, its exact
+// bilinear contributions into a private 4-column stencil in shared memory (origin c0 per
+// (ray, row)).  After the chunk every pixel GATHERS from the stencils of the few rays
+// whose footprint covers it: no atomics, no write conflicts, deterministic order.  Rows
+// shared by consecutive chunks are completed through a carried pixel row; each view
+// writes its own partial image, reduce_views sums them in a fixed order.
 #include <atomic>
+#include <climits>
 #include <cstdio>
 
 #include "kernels.cuh"
@@ -27,44 +35,29 @@ static std::atomic<long long> g_launches{0};
 void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
-// ray clipping: conservative j range of samples whose base pixel can be inside
-// [-1, n-1]^2; the exact per-sample test inside the walk decides
-__device__ __forceinline__ void clip_ray(const ViewDev& v, int i, int n, int T, int* jlo, int* jhi) {
-    double X0 = v.X00d + i * v.dXrd, Y0 = v.Y00d + i * v.dYrd;
-    double lo = 0.0, hi = T - 1.0;
-    lo = fmax(lo, ceil((-1.0 - Y0) / v.dYsd) - 1.0);
-    hi = fmin(hi, floor((n - Y0) / v.dYsd) + 1.0);
-    if (fabs(v.dXsd) > 1e-9) {
-        double a = (-1.0 - X0) / v.dXsd, b = (n - X0) / v.dXsd;
-        if (a > b) {
-            double t = a;
-            a = b;
-            b = t;
-        }
-        lo = fmax(lo, ceil(a) - 1.0);
-        hi = fmin(hi, floor(b) + 1.0);
-    } else if (X0 < -1.0 - 1e-6 || X0 > n + 1e-6) {
-        hi = lo - 1.0;
-    }
-    if (hi < lo) {
-        *jlo = 0;
-        *jhi = -1;
-    } else {
-        *jlo = (int)lo;
-        *jhi = (int)hi;
-    }
-}
+constexpr short kNoRow = -30000;  // stencil origin of a (ray, row) the ray never touched
 
-// copy canonical rows [row_lo, row_lo + nrows) of a padded layout into shared memory
+// Stencil columns per (ray, row).  The cells touching one row span at most three base
+// columns; the float paths step positions in exact 32.32 fixed point so four columns
+// always suffice, the double path evaluates positions per sample and keeps one column
+// of slack for rounding at exactly 45-degree views.
+template <typename T> constexpr int stencil_width() { return sizeof(T) == 8 ? 5 : 4; }
+
+// Copy canonical rows [row_lo, row_lo + nrows) of a padded layout into shared memory:
+// one warp per row, 16-byte vectors (P is even, so a row of float2 is a whole number of
+// 16-byte vectors; a double2 is one vector).
 template <typename T2>
 __device__ __forceinline__ void stage_rows(T2* __restrict__ dst, const T2* __restrict__ src, int P,
                                            int n, int flipped, int row_lo, int nrows) {
-    const int total = nrows * P;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int rr = e / P, col = e - rr * P;
-        int r = row_lo + rr;
-        int gr = (flipped ? (n - 1 - r) : r) + 1;
-        dst[e] = src[(size_t)gr * P + col];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int per = 16 / sizeof(T2);  // elements per 16-byte vector
+    const int nvec = P / per;
+    for (int rr = warp; rr < nrows; rr += nw) {
+        const int r = row_lo + rr;
+        const int gr = (flipped ? (n - 1 - r) : r) + 1;
+        const float4* s = reinterpret_cast<const float4*>(src + (size_t)gr * P);
+        float4* d = reinterpret_cast<float4*>(dst + (size_t)rr * P);
+        for (int c = lane; c < nvec; c += 32) d[c] = s[c];
     }
 }
 
@@ -79,6 +72,7 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     const int nth = blockDim.x;
     const bool active = tid < ns;
     const T h = (T)A.h;
+    constexpr int SW = stencil_width<T>();
 
     size_t off = 0;
     T2* cu = (T2*)(sm + off);
@@ -90,33 +84,25 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     }
     T* sval = (T*)(sm + off);
     off += sizeof(T2) * (size_t)nth;  // T2-sized slots keep the next arrays aligned
-    T2 *SBg = nullptr, *SBa = nullptr, *carry0 = nullptr, *carry1 = nullptr;
-    int *SBi = nullptr, *scnt = nullptr;
-    float* sYf = nullptr;
-    const int cap = A.sb_cap;
+    T2 *ST = nullptr, *carry0 = nullptr, *carry1 = nullptr;
+    short* C0 = nullptr;
     if constexpr (MODE == kVjp) {
-        SBg = (T2*)(sm + off);
-        off += sizeof(T2) * (size_t)cap * nth;
-        SBa = (T2*)(sm + off);
-        off += sizeof(T2) * (size_t)cap * nth;
+        ST = (T2*)(sm + off);  // [(row * SW + k) * nth + ray]
+        off += sizeof(T2) * (size_t)(Yc + 1) * SW * nth;
         carry0 = (T2*)(sm + off);
         off += sizeof(T2) * (size_t)n;
         carry1 = (T2*)(sm + off);
         off += sizeof(T2) * (size_t)n;
-        SBi = (int*)(sm + off);
-        off += sizeof(int) * (size_t)cap * nth;
-        scnt = (int*)(sm + off);
-        off += sizeof(int) * (size_t)nth;
-        sYf = (float*)(sm + off);
-        off += sizeof(float) * (size_t)nth;
+        C0 = (short*)(sm + off);  // [row * nth + ray]
+        off += sizeof(short) * (size_t)(Yc + 1) * nth;
     }
 
     const T2* ug = (const T2*)A.u_img[vp.transposed];
     const T2* pg = (MODE == kJvp) ? (const T2*)A.p_img[vp.transposed] : nullptr;
 
-    int jlo = 0, jhi = -1;
-    if (active) clip_ray(vp, tid, n, A.T, &jlo, &jhi);
-    int j = jhi;
+    const int2 jr = active ? A.clip[(size_t)v * A.max_slots + tid] : make_int2(0, -1);
+    const int jlo = jr.x;
+    int j = jr.y;
     Pos<T> pos;
     pos.init(vp, active ? tid : 0, j);
     Acc<T, KAHAN> S, q, dS;
@@ -129,18 +115,24 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
             const int q0 = A.src_off[vp.bank * A.max_slots + tid];
             const int q1 = A.src_off[vp.bank * A.max_slots + tid + 1];
             const T* r = (const T*)A.r_in + (size_t)vp.angle * A.n_det;
+            const T* sw = (const T*)A.src_w;
             T acc = T(0);
-            for (int e = q0; e < q1; ++e) acc += (T)A.src_w[e] * r[A.src_det[e]];
+            for (int e = q0; e < q1; ++e) acc += sw[e] * r[A.src_det[e]];
             rho = acc;
             Utot = ((const T*)A.slot_val)[(size_t)v * A.max_slots + tid];
         }
     }
-    // gather geometry of this view (float is enough to bound candidates)
+    // stencil origin offset: walking down, X moves by -dXs per step; the first sample
+    // touching a row then has the largest (dXs > 0) or smallest (dXs < 0) base column
+    const int base = vp.dXs > 0 ? SW - 2 : 0;
+    int cur_row = INT_MIN;
+    int c0_lo = 0, c0_hi = 0;
+    // candidate rays of a pixel (float bounds; the stencil origin decides exactly)
     const float X00f = (float)vp.X00d, Y00f = (float)vp.Y00d;
     const float dXrf = (float)vp.dXrd, dYrf = (float)vp.dYrd;
     const float invR2 = 1.0f / (dXrf * dXrf + dYrf * dYrf);
     const float wI = (fabsf(dXrf) + fabsf(dYrf)) * invR2 + 0.01f;
-    const float invdY = (float)(1.0 / vp.dYsd);
+    const float inv_n = 1.0f / (float)n;
 
     for (int ck = 0; ck < A.nchunks; ++ck) {
         const int row_hi = n - 1 - ck * Yc;
@@ -149,8 +141,11 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         __syncthreads();
         stage_rows(cu, ug, P, n, vp.flipped, row_lo, nrows);
         if constexpr (MODE == kJvp) stage_rows(cp, pg, P, n, vp.flipped, row_lo, nrows);
+        if constexpr (MODE == kVjp) {
+            for (int rr = 0; rr < nrows; ++rr) C0[rr * nth + tid] = kNoRow;
+            cur_row = INT_MIN;  // the stencil rows of this chunk start empty
+        }
         __syncthreads();
-        int cnt = 0;
         if (active) {
             while (j >= jlo) {
                 const int iy0 = pos.iy();
@@ -180,15 +175,40 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                         const T Qh = (Utot - q.val()) - T(0.5) * la;
                         const T gl = rho * h * at;
                         const T gm = -rho * h * h * Qh;
-                        if (cnt == 0) sYf[tid] = pos.yf();
-                        if (cnt < cap) {
-                            SBg[cnt * nth + tid] = mk2(gl, gm);
-                            SBa[cnt * nth + tid] = mk2(ax, ay);
-                            SBi[cnt * nth + tid] = (ix0 + 1) | ((iy0 + 1) << 16);
-                        } else {
-                            atomicOr(A.err, 1);
+                        const int rl = iy0 - row_lo;  // lower row of the cell; upper is rl + 1
+                        if (iy0 != cur_row) {
+                            if (iy0 + 1 != cur_row) {
+                                c0_hi = ix0 - base;
+                                C0[(rl + 1) * nth + tid] = (short)c0_hi;
+                                for (int k = 0; k < SW; ++k) ST[((rl + 1) * SW + k) * nth + tid] = mk2(T(0), T(0));
+                            } else {
+                                c0_hi = c0_lo;
+                            }
+                            c0_lo = ix0 - base;
+                            C0[rl * nth + tid] = (short)c0_lo;
+                            for (int k = 0; k < SW; ++k) ST[(rl * SW + k) * nth + tid] = mk2(T(0), T(0));
+                            cur_row = iy0;
                         }
-                        ++cnt;
+                        const int ol = ix0 - c0_lo, oh = ix0 - c0_hi;
+                        if ((unsigned)ol <= (unsigned)(SW - 2) && (unsigned)oh <= (unsigned)(SW - 2)) {
+                            T2* pl = ST + (size_t)(rl * SW + ol) * nth + tid;
+                            T2* ph = ST + (size_t)((rl + 1) * SW + oh) * nth + tid;
+                            T2 t0 = pl[0], t1 = pl[nth], t2 = ph[0], t3 = ph[nth];
+                            t0.x += w00 * gl;
+                            t0.y += w00 * gm;
+                            t1.x += w10 * gl;
+                            t1.y += w10 * gm;
+                            t2.x += w01 * gl;
+                            t2.y += w01 * gm;
+                            t3.x += w11 * gl;
+                            t3.y += w11 * gm;
+                            pl[0] = t0;
+                            pl[nth] = t1;
+                            ph[0] = t2;
+                            ph[nth] = t3;
+                        } else {
+                            atomicOr(A.err, 2);  // geometry bound violated: report, never write out of range
+                        }
                         q.add(la);
                     }
                     S.add(m);
@@ -198,7 +218,6 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
             }
         }
         if constexpr (MODE == kVjp) {
-            scnt[tid] = active ? min(cnt, cap) : 0;
             __syncthreads();
             const int r0 = max(row_lo, 0), r1 = min(row_hi + 1, n - 1);
             const int nout = (r1 - r0 + 1) * n;
@@ -206,28 +225,18 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
             T2* carry_wr = (ck & 1) ? carry1 : carry0;
             T* gp = (T*)A.gpart + (size_t)v * 2 * n * n;
             for (int e = tid; e < nout; e += nth) {
-                const int Yr = r0 + e / n, Xc = e - (e / n) * n;
+                const int dy = __float2int_rz(((float)e + 0.5f) * inv_n);
+                const int Yr = r0 + dy, Xc = e - dy * n;
+                const int rl = Yr - row_lo;
                 const float fi = ((float)Xc - X00f) * dXrf * invR2 + ((float)Yr - Y00f) * dYrf * invR2;
                 const int ilo = max(0, (int)ceilf(fi - wI)), ihi = min(ns - 1, (int)floorf(fi + wI));
                 T gl = T(0), gm = T(0);
                 for (int i = ilo; i <= ihi; ++i) {
-                    const int c = scnt[i];
-                    if (c == 0) continue;
-                    int k = max(0, (int)floorf((sYf[i] - (float)(Yr + 1)) * invdY) - 1);
-                    for (; k < c; ++k) {
-                        const int idx = SBi[k * nth + i];
-                        const int iy0 = (idx >> 16) - 1;
-                        if (iy0 > Yr) continue;
-                        if (iy0 < Yr - 1) break;
-                        const int dx = Xc - ((idx & 0xffff) - 1);
-                        if (dx != 0 && dx != 1) continue;
-                        const T2 axy = SBa[k * nth + i];
-                        const T2 gg = SBg[k * nth + i];
-                        const T wx = dx == 0 ? T(1) - axy.x : axy.x;
-                        const T wy = iy0 == Yr ? T(1) - axy.y : axy.y;
-                        const T wgt = wx * wy;
-                        gl += wgt * gg.x;
-                        gm += wgt * gg.y;
+                    const int k = Xc - (int)C0[rl * nth + i];
+                    if ((unsigned)k < (unsigned)SW) {
+                        const T2 s = ST[(rl * SW + k) * nth + i];
+                        gl += s.x;
+                        gm += s.y;
                     }
                 }
                 if (ck > 0 && Yr == row_hi + 1) {
@@ -253,20 +262,21 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         }
         __syncthreads();
         T* y = (T*)A.y_out + (size_t)vp.angle * A.n_det + (size_t)vp.bank * A.nb;
+        const T* wk = (const T*)A.w;
         for (int d = tid; d < A.nb; d += nth) {
             const int* ds = A.det_slot + (size_t)(vp.bank * A.nb + d) * A.n_sub;
             T acc = T(0);
-            for (int k = 0; k < A.n_sub; ++k) acc += (T)A.w[k] * sval[ds[k]];
+            for (int k = 0; k < A.n_sub; ++k) acc += wk[k] * sval[ds[k]];
             y[d] = h * acc;
         }
     }
 }
 
-static size_t walk_smem(int mode, bool f64, int threads, int Yc, int P, int n, int cap) {
+static size_t walk_smem(int mode, bool f64, int threads, int Yc, int P, int n) {
     size_t s2 = f64 ? 16 : 8;
     size_t b = s2 * (size_t)(Yc + 1) * P * (mode == kJvp ? 2 : 1) + s2 * threads;
-    if (mode == kVjp) b += (2 * s2 + 4) * (size_t)cap * threads + 2 * s2 * n + 8 * (size_t)threads;
-    return b;
+    if (mode == kVjp) b += s2 * (size_t)(Yc + 1) * (f64 ? 5 : 4) * threads + 2 * s2 * n + 2 * (size_t)(Yc + 1) * threads;
+    return (b + 15) / 16 * 16;
 }
 
 WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget) {
@@ -274,14 +284,13 @@ WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget) 
     pl.threads = ((g.max_slots + 31) / 32) * 32;
     int best = 1;
     for (int Yc = 1; Yc <= g.n + 1; ++Yc) {
-        int cap = (mode == kVjp) ? (int)(Yc * 1.41421357 / g.h) + 3 : 0;
-        if (walk_smem(mode, f64, pl.threads, Yc, P, g.n, cap) <= budget) best = Yc;
+        if (walk_smem(mode, f64, pl.threads, Yc, P, g.n) <= budget) best = Yc;
         else break;
     }
     pl.Yc = best;
     pl.nchunks = (g.n + 1 + best - 1) / best;
-    pl.sb_cap = (mode == kVjp) ? (int)(best * 1.41421357 / g.h) + 3 : 0;
-    pl.smem = walk_smem(mode, f64, pl.threads, best, P, g.n, pl.sb_cap);
+    pl.sb_cap = 0;
+    pl.smem = walk_smem(mode, f64, pl.threads, best, P, g.n);
     return pl;
 }
 

