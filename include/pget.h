@@ -179,6 +179,31 @@ pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget
                                const void* y_host, void* lam_host, void* mu_host,
                                int32_t init_guess, pget_lm_report* rep, void* stream);
 
+/* ------------------------------------------------------ allocation-free forward
+ * The paper has no counterpart to this call; it serves callers that are not allowed to
+ * allocate device memory (a host framework whose allocator owns the GPU, allocation-free
+ * real-time sections, processes with a memory budget fixed up front), which cannot use
+ * the context-based calls above because a pget_ctx obtains its workspace with cudaMalloc.
+ *
+ * pget_forward_noalloc computes exactly what pget_forward computes, on the current
+ * device, without a context.  All of its scratch (geometry tables and the packed image
+ * layouts) lives in one fixed array of 8 MiB in device memory, defined in the library and
+ * held by every device that loads it until the process exits.
+ *   - A geometry whose scratch exceeds 8 MiB returns PGET_ENOMEM before any work is
+ *     queued (2 * (n+2)^2 image elements of 8 or 16 bytes plus 8 bytes per ray slot and
+ *     view; e.g. n = 128 with 360 angles x 182 detectors x 5 sub-rays needs about 2 MiB).
+ *   - Bad arguments return PGET_EINVAL, CUDA failures PGET_ECUDA.  Errors are reported
+ *     by the status only: pget_last_error is not updated (storing a message could
+ *     allocate).
+ *   - The first call on a device looks up the array's device address and caches it; make
+ *     that first call before any stream capture.
+ *   - Every call overwrites the same array (image borders are cleared on each call);
+ *     calls that overlap on the GPU (several streams or host threads) race.
+ *   - The call allocates no device or host memory.
+ * lam, mu: [n][n] device in; y: [n_angles][n_det] device out; stream as above. */
+pget_status pget_forward_noalloc(const pget_geometry* g, int32_t precision, const void* lam,
+                                 const void* mu, void* y, void* stream);
+
 /* ------------------------------------------------------------- diagnostics
  * Device time of the hot kernels, measured with CUDA events recorded on the stream each
  * kernel is launched on (no effect on results).  pget_profile_enable resets the counters;

@@ -83,6 +83,7 @@ _SIGS = {
                        C.POINTER(pget_lm_report), _vp], C.c_int),
     "pget_lm_solve_host": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
                             _vp, C.c_int32, C.POINTER(pget_lm_report), _vp], C.c_int),
+    "pget_forward_noalloc": ([C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
     "pget_profile_enable": ([_vp, C.c_int32], C.c_int),
     "pget_profile_read": ([_vp, C.POINTER(pget_kernel_stat), C.c_int32], C.c_int32),
     "pget_launch_count": ([], C.c_longlong),
@@ -258,6 +259,13 @@ def pget_lm_solve_host(ctx: Context, g: pget_geometry, p: pget_lm_params, y_host
                                      lam_host.data_ptr(), mu_host.data_ptr(), int(bool(init_guess)),
                                      C.byref(rep), _stream(stream)), ctx.h)
     return rep.to_dict()
+
+
+def pget_forward_noalloc(g: pget_geometry, precision: int, lam, mu, y, stream=None) -> int:
+    """Forward projection without a context and without allocating (see pget.h); y must
+    be preallocated.  Returns the pget status (no exception, no message)."""
+    return load().pget_forward_noalloc(C.byref(g), precision, _ptr(lam), _ptr(mu), _ptr(y),
+                                       _stream(stream))
 
 
 def pget_profile_enable(ctx: Context, enable: bool = True):
