@@ -101,6 +101,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_request_ids(rank: int, world: int, per_rank: int) -> list:
+    """Phantom seeds of the requests one rank reconstructs (disjoint across ranks)."""
+    return [rank * per_rank + k for k in range(per_rank)]
+
+
 def make_problem(P, ctx, torch, seed: int, device: str):
     from paper_2604_26745_gb300 import synth
     W = WORKLOAD
@@ -222,8 +227,8 @@ def main():
                          precision=prec)
     nsteps = args.warmup + args.steps
     probs = []
-    for k in range(nsteps):
-        g, ph, y = make_problem(P, ctx, torch, 97 * rank + k, dev)
+    for k in rank_request_ids(rank, world, nsteps):
+        g, ph, y = make_problem(P, ctx, torch, k, dev)
         probs.append((g, ph, torch.tensor(y, dtype=torch.float32, device=dev)))
     lam = torch.empty((W["n"], W["n"]), dtype=torch.float32, device=dev)
     mu = torch.empty_like(lam)

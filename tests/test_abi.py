@@ -1,0 +1,77 @@
+"""The C ABI on a machine without a GPU: the library builds, loads, and exports every
+function include/pget.h declares; the Python binding binds exactly those; structure
+layouts agree between the header and the binding.  No compute call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pget.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pget_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_26745_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("pget_forward", "pget_jvp", "pget_vjp", "pget_lm_solve", "pget_cg_solve",
+                 "pget_reg_apply", "pget_create", "pget_destroy", "pget_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L, path = lib
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_binding_matches_header(lib):
+    from paper_2604_26745_gb300 import pget
+    assert sorted(pget.exported_symbols()) == _declared()
+
+
+def test_struct_sizes_match_header(lib):
+    """Compile a tiny C program against the header and compare sizeof with ctypes."""
+    import subprocess
+    import tempfile
+    from paper_2604_26745_gb300 import pget
+    prog = r'''
+#include <stdio.h>
+#include "pget.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(pget_geometry), sizeof(pget_lm_params),
+         sizeof(pget_lm_report), sizeof(pget_kernel_stat));
+  return 0;
+}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "s.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "s")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(x) for x in out]
+    assert sizes == [ctypes.sizeof(pget.pget_geometry), ctypes.sizeof(pget.pget_lm_params),
+                     ctypes.sizeof(pget.pget_lm_report), ctypes.sizeof(pget.pget_kernel_stat)]
+
+
+def test_no_gpu_calls_fail_cleanly(lib):
+    """Without a device, creating a context returns an error status, never aborts."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2604_26745_gb300 import pget
+    with pytest.raises(pget.PgetError):
+        pget.Context(0)
+    assert pget.pget_version().startswith("pget-gb300")

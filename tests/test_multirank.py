@@ -1,0 +1,52 @@
+"""Multi-rank host logic of bench.py on CPU: two gloo ranks each time their own
+(independent) requests, the job time is the max over ranks and the throughput counts
+every rank's requests (weak scaling, no collective on the data path)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, q):
+    import time
+
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    # each rank "reconstructs" its own request ids with a rank-dependent cost
+    ids = bench.rank_request_ids(rank, world, 8)
+    t0 = time.perf_counter()
+    time.sleep(0.05 * (rank + 1))
+    elapsed = time.perf_counter() - t0
+    t = torch.tensor([elapsed], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    q.put((rank, ids, float(t.item()), elapsed))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_weak_scaling():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, ids0, tmax0, e0), (r1, ids1, tmax1, e1) = res
+    assert tmax0 == tmax1 and abs(tmax0 - max(e0, e1)) < 1e-12
+    assert not set(ids0) & set(ids1)  # independent work per rank
+    assert len(ids0) == len(ids1) == 8
