@@ -179,6 +179,33 @@ pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget
                                const void* y_host, void* lam_host, void* mu_host,
                                int32_t init_guess, pget_lm_report* rep, void* stream);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of reconstructions: each accepted request gets an in-flight slot
+ * (its own workspace, stream and captured LM graph, all state on the device); requests
+ * that arrive while others run are admitted as soon as a slot and device memory are
+ * free, and their kernels overlap on the GPU with those of the requests in flight.
+ * Results are identical to pget_lm_solve on the same inputs (the kernels are
+ * deterministic and a slot shares nothing with other slots).
+ *
+ * pget_submit: y ([n_angles][n_det]) and the optional initial guess lam0, mu0 ([n][n];
+ *   both NULL: the pget_initial_guess reading with mu_init 0.01) are device pointers in
+ *   the element type of p->precision; they are copied into slot memory before the call
+ *   returns, so the caller may free them afterwards.  Returns PGET_EAGAIN when every slot
+ *   is busy or the memory budget of the context is in use (retry after a poll),
+ *   PGET_ENOMEM when the request can never fit the budget, PGET_EINVAL for bad
+ *   arguments.  Up to 8 requests are in flight (environment PGET_MAX_INFLIGHT, <= 64).
+ * pget_poll: *done = 0 while the request runs; when it has finished, copies the result
+ *   into lam_out / mu_out (device, may be NULL), fills *rep (host, may be NULL), frees the
+ *   slot and sets *done = 1.  PGET_ENOTFOUND for an unknown or already collected ticket.
+ * pget_cancel: drops a request (its queued kernels finish first; they cannot be aborted).
+ * pget_inflight: number of occupied slots. */
+pget_status pget_submit(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
+                        const void* lam0, const void* mu0, uint64_t* ticket);
+pget_status pget_poll(pget_ctx* ctx, uint64_t ticket, void* lam_out, void* mu_out, pget_lm_report* rep,
+                      int* done);
+pget_status pget_cancel(pget_ctx* ctx, uint64_t ticket);
+int32_t pget_inflight(pget_ctx* ctx);
+
 /* ------------------------------------------------------ allocation-free forward
  * The paper has no counterpart to this call; it serves callers that are not allowed to
  * allocate device memory (a host framework whose allocator owns the GPU, allocation-free

@@ -62,15 +62,36 @@ struct Profiler {
         cudaEventCreate(&e);
         return e;
     }
+    bool capturing = false;        // records become event nodes of a CUDA graph
+    std::vector<Rec> captured;
     void begin(int kind, cudaStream_t st) {
         if (!on) return;
         Rec r{kind, get(), get()};
-        cudaEventRecord(r.a, st);
-        pending.push_back(r);
+        if (capturing) {
+            cudaEventRecordWithFlags(r.a, st, cudaEventRecordExternal);
+            captured.push_back(r);
+        } else {
+            cudaEventRecord(r.a, st);
+            pending.push_back(r);
+        }
     }
     void end(cudaStream_t st) {
-        if (!on || pending.empty()) return;
-        cudaEventRecord(pending.back().b, st);
+        if (!on) return;
+        if (capturing) {
+            if (!captured.empty()) cudaEventRecordWithFlags(captured.back().b, st, cudaEventRecordExternal);
+        } else if (!pending.empty()) {
+            cudaEventRecord(pending.back().b, st);
+        }
+    }
+    // after a replay of a graph captured with profiling on (stream synchronised)
+    void collect_graph(const std::vector<Rec>& recs) {
+        for (auto& r : recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                total_ms[r.kind] += ms;
+                count[r.kind] += 1;
+            }
+        }
     }
     void collect() {
         for (auto& r : pending) {
@@ -118,6 +139,12 @@ struct Workspace {
     int* d_src_det = nullptr;
     void* d_src_w = nullptr;    // per-slot sub-ray weights in the element type of the path
     int2* d_clip = nullptr;
+    // adjoint view groups: CTA g sums views group_view[group_off[g] .. group_off[g+1]),
+    // all of one canonical orientation (gtrans[g]), into partial image g
+    int n_groups = 0;
+    int* d_group_off = nullptr;
+    int* d_group_view = nullptr;
+    int* d_gtrans = nullptr;
     void* pk_u[2] = {nullptr, nullptr};
     void* pk_ut[2] = {nullptr, nullptr};
     void* pk_p[2] = {nullptr, nullptr};
@@ -131,8 +158,28 @@ struct Workspace {
     int* err = nullptr;
     std::vector<void*> allocs;
     size_t bytes = 0;
+    // CUDA graph of the LM body (everything between the input copies and the result copy)
+    cudaStream_t cap_stream = nullptr;
+    LmState* host_lm = nullptr;      // pinned copy of the device LM state after a solve
+    int* host_err = nullptr;         // pinned copy of the device error flags
+    cudaEvent_t t0 = nullptr, t1 = nullptr;  // solve timing (stream events)
+    std::string graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<Profiler::Rec> graph_events;
+    long long graph_launches = 0;
+    bool graph_used = false;
 
     ~Workspace() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        for (auto& r : graph_events) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (host_lm) cudaFreeHost(host_lm);
+        if (host_err) cudaFreeHost(host_err);
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
         for (void* a : allocs) cudaFree(a);
     }
     template <typename X>
@@ -170,8 +217,31 @@ static size_t workspace_bytes(const Geometry& g, int prec, int groups) {
 
 }  // namespace pget
 
+namespace pget {
+// One in-flight reconstruction of the serving path: its own workspace (kept for reuse
+// while the slot is free), stream, captured LM graph and completion event.
+struct Slot {
+    enum State { kFree = 0, kRunning = 1, kDone = 2 };
+    int state = kFree;
+    uint64_t ticket = 0;
+    std::unique_ptr<Workspace> ws;
+    std::string ws_key;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    pget_status launch_status = PGET_OK;
+    ~Slot() {
+        if (stream) cudaStreamSynchronize(stream);
+        ws.reset();
+        if (done) cudaEventDestroy(done);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+}  // namespace pget
+
 struct pget_ctx {
     Profiler prof;
+    std::vector<std::unique_ptr<pget::Slot>> slots;
+    uint64_t next_ticket = 1;
     int device = 0;
     size_t budget = 0;
     std::mutex mu;
@@ -196,29 +266,28 @@ struct DeviceGuard {
     }
 };
 
-pget_status get_workspace(pget_ctx* ctx, const pget_geometry* gin, int prec, Workspace** out) {
+// Resolve and validate a geometry; the key identifies (geometry, precision).
+pget_status resolve(const pget_geometry* gin, int prec, Geometry* g, std::string* key, int* groups,
+                    size_t* need) {
     if (!gin) return fail(PGET_EINVAL, "null geometry");
     if (prec != PGET_F64 && prec != PGET_F32 && prec != PGET_F32_KAHAN)
         return fail(PGET_EINVAL, "unknown precision %d", prec);
-    Geometry g;
     std::string msg;
-    pget_status s = build_geometry(*gin, &g, &msg);
+    pget_status s = build_geometry(*gin, g, &msg);
     if (s != PGET_OK) return fail(s, "%s", msg.c_str());
-    std::string key = g.key + "#" + std::to_string(prec);
-    if (ctx->ws && ctx->ws_key == key) {
-        *out = ctx->ws.get();
-        return PGET_OK;
-    }
+    *key = g->key + "#" + std::to_string(prec);
+    const int V = g->n_angles * g->n_banks;
+    const int tiles = ((g->n + 31) / 32) * ((g->n + 31) / 32);
+    *groups = std::max(1, std::min(V, (2 * kRedBlocks + tiles - 1) / tiles));
+    *need = workspace_bytes(*g, prec, *groups);
+    return PGET_OK;
+}
+
+size_t serving_bytes(const pget_ctx* ctx);
+
+// Allocate and initialise a workspace for a resolved geometry (no budget check).
+pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, std::unique_ptr<Workspace>* out) {
     const int V = g.n_angles * g.n_banks;
-    const int tiles = ((g.n + 31) / 32) * ((g.n + 31) / 32);
-    int groups = std::max(1, std::min(V, (2 * kRedBlocks + tiles - 1) / tiles));
-    size_t need = workspace_bytes(g, prec, groups);
-    size_t held = ctx->ws ? ctx->ws->bytes : 0;
-    if (ctx->budget && need > ctx->budget)
-        return fail(PGET_ENOMEM, "workspace needs %zu bytes, budget %zu", need, ctx->budget);
-    (void)held;
-    ctx->ws.reset();
-    ctx->ws_key.clear();
     auto w = std::make_unique<Workspace>();
     w->g = std::move(g);
     Geometry& G = w->g;
@@ -242,6 +311,32 @@ pget_status get_workspace(pget_ctx* ctx, const pget_geometry* gin, int prec, Wor
     w->pf = plan_walk(G, w->P, kFwd, w->f64, budget("PGET_SMEM_KB_FWD", 64));
     w->pj = plan_walk(G, w->P, kJvp, w->f64, budget("PGET_SMEM_KB_JVP", 64));
     w->pv = plan_walk(G, w->P, kVjp, w->f64, budget("PGET_SMEM_KB_VJP", 72));
+    // views per adjoint CTA: one by default (the hardware scheduler balances single-view
+    // CTAs across SMs best); PGET_VJP_VIEWS_PER_CTA > 1 groups views of one orientation,
+    // which shrinks the partial images but assigns work statically; 0 sizes groups so that
+    // every CTA is resident at once
+    int K = 1;
+    if (const char* kv = getenv("PGET_VJP_VIEWS_PER_CTA")) {
+        K = atoi(kv);
+        if (K <= 0) {
+            int sms = 1;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+            const int slots = std::max(1, sms * walk_occupancy(kVjp, prec, w->pv));
+            K = std::max(1, (V + slots - 1) / slots);
+        }
+    }
+    std::vector<int> goff{0}, gview, gtrans;
+    for (int cls = 0; cls < 2; ++cls) {
+        std::vector<int> vs;
+        for (int v = 0; v < V; ++v)
+            if (G.views[v].transposed == cls) vs.push_back(v);
+        for (size_t i = 0; i < vs.size(); i += K) {
+            for (size_t k = i; k < std::min(vs.size(), i + (size_t)K); ++k) gview.push_back(vs[k]);
+            goff.push_back((int)gview.size());
+            gtrans.push_back(cls);
+        }
+    }
+    w->n_groups = (int)gtrans.size();
     const size_t e = w->elt, e2 = 2 * e;
     (void)e2;
     CK(w->alloc(&w->d_views, sizeof(ViewDev) * V));
@@ -282,12 +377,47 @@ pget_status get_workspace(pget_ctx* ctx, const pget_geometry* gin, int prec, Wor
     CK(w->alloc(&w->Jp, e * w->M));
     CK(w->alloc(&w->U, e * w->nslots));
     CK(w->alloc(&w->Ut, e * w->nslots));
-    CK(w->alloc(&w->gpart, e * (size_t)V * 2 * w->nn));
+    CK(w->alloc(&w->gpart, e * (size_t)w->n_groups * 2 * w->nn));
+    CK(w->alloc(&w->d_group_off, sizeof(int) * goff.size()));
+    CK(cudaMemcpy(w->d_group_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_group_view, sizeof(int) * gview.size()));
+    CK(cudaMemcpy(w->d_group_view, gview.data(), sizeof(int) * gview.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_gtrans, sizeof(int) * gtrans.size()));
+    CK(cudaMemcpy(w->d_gtrans, gtrans.data(), sizeof(int) * gtrans.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->part2, e * (size_t)groups * 2 * w->nn));
     for (int k = 0; k < 4; ++k) CK(w->alloc(&w->dpart[k], sizeof(double) * kRedBlocks));
     CK(w->alloc(&w->lm, sizeof(LmState)));
     CK(w->alloc(&w->err, sizeof(int) * 4));
+    CK(cudaMallocHost(&w->host_lm, sizeof(LmState)));
+    CK(cudaMallocHost(&w->host_err, sizeof(int) * 4));
+    CK(cudaEventCreate(&w->t0));
+    CK(cudaEventCreate(&w->t1));
     w->prof = &ctx->prof;
+    *out = std::move(w);
+    return PGET_OK;
+}
+
+// The workspace of the direct (non-serving) calls: reused while the geometry and
+// precision stay the same; counted against the budget together with serving slots.
+pget_status get_workspace(pget_ctx* ctx, const pget_geometry* gin, int prec, Workspace** out) {
+    Geometry g;
+    std::string key;
+    int groups = 1;
+    size_t need = 0;
+    pget_status s = resolve(gin, prec, &g, &key, &groups, &need);
+    if (s != PGET_OK) return s;
+    if (ctx->ws && ctx->ws_key == key) {
+        *out = ctx->ws.get();
+        return PGET_OK;
+    }
+    if (ctx->budget && need + serving_bytes(ctx) > ctx->budget)
+        return fail(PGET_ENOMEM, "workspace needs %zu bytes, budget %zu (serving slots hold %zu)", need,
+                    ctx->budget, serving_bytes(ctx));
+    ctx->ws.reset();
+    ctx->ws_key.clear();
+    std::unique_ptr<Workspace> w;
+    s = make_workspace(ctx, std::move(g), prec, groups, &w);
+    if (s != PGET_OK) return s;
     ctx->ws = std::move(w);
     ctx->ws_key = key;
     *out = ctx->ws.get();
@@ -362,16 +492,19 @@ cudaError_t op_vjp(Workspace& w, void* const pku[2], const void* U, const void* 
     a.slot_val = (void*)U;
     a.r_in = r;
     a.gpart = w.gpart;
+    a.group_off = w.d_group_off;
+    a.group_view = w.d_group_view;
     a.stop = stop;
     w.prof->begin(kPVjp, st);
-    cudaError_t e = launch_walk(kVjp, w.prec, w.pv, a, w.n_views, st);
+    cudaError_t e = launch_walk(kVjp, w.prec, w.pv, a, w.n_groups, st);
     w.prof->end(st);
     if (e != cudaSuccess) return e;
     ra.n = w.g.n;
     ra.skip = stop;
     w.prof->begin(kPRed, st);
-    reduce_views<T>((const T*)w.gpart, w.d_vtrans, w.g.n, w.n_views, w.groups, (T*)w.part2, ra,
-                    w.prec == PGET_F32_KAHAN, st);
+    // the view sum is already two-level (<= ~40 terms per level): plain sums suffice;
+    // the Kahan compensation of PGET_F32_KAHAN applies along rays
+    reduce_views<T>((const T*)w.gpart, w.d_gtrans, w.g.n, w.n_groups, w.groups, (T*)w.part2, ra, false, st);
     w.prof->end(st);
     return cudaGetLastError();
 }
@@ -379,12 +512,12 @@ cudaError_t op_vjp(Workspace& w, void* const pku[2], const void* U, const void* 
 template <typename T>
 void pack_vec(const Workspace& w, const void* vec, void* const pk[2], const int* skip, cudaStream_t st) {
     const T* a = (const T*)vec;
-    pack<T>(a, a + w.nn, w.g.n, w.P, pk[0], pk[1], skip, st);
+    pack<T>(a, a + w.nn, w.g.n, w.P, attenuation_scale(w.g), pk[0], pk[1], skip, st);
 }
 
 template <typename T>
 void pack_pair(const Workspace& w, const void* lam, const void* mu, void* const pk[2], cudaStream_t st) {
-    pack<T>((const T*)lam, (const T*)mu, w.g.n, w.P, pk[0], pk[1], nullptr, st);
+    pack<T>((const T*)lam, (const T*)mu, w.g.n, w.P, attenuation_scale(w.g), pk[0], pk[1], nullptr, st);
 }
 
 // CG on (J^T J + H + nu I) x = scale_b * b, H and U at the packed iterate pk_u
@@ -450,20 +583,14 @@ pget_status check_params(const pget_lm_params* p) {
 }
 
 // LM solve on device pointers (y, u0 planar inputs copied into the workspace)
+// The LM iteration proper: reads yb and the initial guess in u, leaves the result in u
+// and the scalars and traces in w.lm.  Only kernel launches (no host synchronisation),
+// so it can be captured as a CUDA graph.
 template <typename T>
-pget_status lm_solve_impl(Workspace& w, const pget_lm_params& p, const void* y, const void* lam,
-                          const void* mu, void* lam_out, void* mu_out, pget_lm_report* rep, cudaStream_t st) {
+pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
     const size_t nn = w.nn, M = w.M;
     const int n = w.g.n;
     LmState* L = w.lm;
-    cudaEvent_t ev0, ev1;
-    CK(cudaEventCreate(&ev0));
-    CK(cudaEventCreate(&ev1));
-    CK(cudaEventRecord(ev0, st));
-    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-    if (y != w.yb) CK(cudaMemcpyAsync(w.yb, y, w.elt * M, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(w.u, lam, w.elt * nn, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync((char*)w.u + w.elt * nn, mu, w.elt * nn, cudaMemcpyDeviceToDevice, st));
     clamp_box<T>((T*)w.u, nn, p.lambda_max, p.mu_max, st);
     pack_vec<T>(w, w.u, w.pk_u, nullptr, st);
     T* u = (T*)w.u;
@@ -536,18 +663,89 @@ pget_status lm_solve_impl(Workspace& w, const pget_lm_params& p, const void* y, 
         }
         CK(cudaGetLastError());
     }
-    CK(cudaMemcpyAsync(lam_out, w.u, w.elt * nn, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(mu_out, (char*)w.u + w.elt * nn, w.elt * nn, cudaMemcpyDeviceToDevice, st));
-    CK(cudaEventRecord(ev1, st));
-    std::unique_ptr<LmState> hl(new LmState);
-    CK(cudaMemcpyAsync(hl.get(), L, sizeof(LmState), cudaMemcpyDeviceToHost, st));
-    pget_status es = check_err(w, st);
+    return PGET_OK;
+}
+
+// key of a captured LM graph: every parameter baked into its kernels
+static std::string graph_key(const pget_lm_params& p, bool prof) {
+    std::string k((const char*)&p, sizeof p);
+    k += prof ? "P" : "N";
+    return k;
+}
+
+// Enqueue one LM solve on st: yb and the initial guess in u must already be in the
+// workspace.  The body runs as a captured CUDA graph (replayed while the parameters stay
+// the same); afterwards the device state and error flags are copied to pinned host
+// memory.  Nothing here waits for the device.
+template <typename T>
+pget_status lm_launch(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
+    CK(cudaEventRecord(w.t0, st));
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    const char* ng = getenv("PGET_NO_GRAPH");
+    const bool use_graph = !(ng && atoi(ng) > 0);
+    if (use_graph) {
+        const std::string key = graph_key(p, w.prof->on);
+        if (!w.graph_exec || w.graph_key != key) {
+            if (w.graph_exec) {
+                cudaGraphExecDestroy(w.graph_exec);
+                w.graph_exec = nullptr;
+            }
+            for (auto& r : w.graph_events) {
+                cudaEventDestroy(r.a);
+                cudaEventDestroy(r.b);
+            }
+            w.graph_events.clear();
+            if (!w.cap_stream) CK(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
+            CK(prepare_walk(kFwd, w.prec, w.pf));
+            CK(prepare_walk(kJvp, w.prec, w.pj));
+            CK(prepare_walk(kVjp, w.prec, w.pv));
+            const long long l0 = launch_count();
+            CK(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
+            w.prof->capturing = true;
+            pget_status bs = lm_body<T>(w, p, w.cap_stream);
+            w.prof->capturing = false;
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(w.cap_stream, &graph);
+            std::vector<Profiler::Rec> recs;
+            recs.swap(w.prof->captured);
+            if (bs != PGET_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return bs;
+            }
+            if (ce != cudaSuccess) return fail(PGET_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&w.graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                w.graph_exec = nullptr;
+                return fail(PGET_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            }
+            w.graph_key = key;
+            w.graph_events = std::move(recs);
+            w.graph_launches = launch_count() - l0;
+        } else {
+            note_launch((int)w.graph_launches);
+        }
+        CK(cudaGraphLaunch(w.graph_exec, st));
+    } else {
+        pget_status bs = lm_body<T>(w, p, st);
+        if (bs != PGET_OK) return bs;
+    }
+    CK(cudaEventRecord(w.t1, st));
+    CK(cudaMemcpyAsync(w.host_lm, w.lm, sizeof(LmState), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w.host_err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    w.graph_used = use_graph;
+    return PGET_OK;
+}
+
+// After the stream of an lm_launch has completed: profiler counters, error flags and
+// the report (from the pinned copies).
+pget_status lm_finish(Workspace& w, pget_lm_report* rep) {
     w.prof->collect();
+    if (w.graph_used && w.prof->on) w.prof->collect_graph(w.graph_events);
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    if (es != PGET_OK) return es;
+    cudaEventElapsedTime(&ms, w.t0, w.t1);
+    if (*w.host_err) return fail(PGET_ECUDA, "device error flags 0x%x (adjoint stencil bound)", *w.host_err);
+    const LmState* hl = w.host_lm;
     if (rep) {
         memset(rep, 0, sizeof *rep);
         rep->iters_run = hl->iter;
@@ -572,6 +770,56 @@ pget_status lm_solve_impl(Workspace& w, const pget_lm_params& p, const void* y, 
     }
     if (!std::isfinite(hl->f)) return fail(PGET_ENUMERIC, "objective is not finite");
     return PGET_OK;
+}
+
+template <typename T>
+pget_status lm_solve_impl(Workspace& w, const pget_lm_params& p, const void* y, const void* lam,
+                          const void* mu, void* lam_out, void* mu_out, pget_lm_report* rep, cudaStream_t st) {
+    const size_t nn = w.nn;
+    if (y != w.yb) CK(cudaMemcpyAsync(w.yb, y, w.elt * w.M, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(w.u, lam, w.elt * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync((char*)w.u + w.elt * nn, mu, w.elt * nn, cudaMemcpyDeviceToDevice, st));
+    pget_status s = lm_launch<T>(w, p, st);
+    if (s != PGET_OK) return s;
+    CK(cudaMemcpyAsync(lam_out, w.u, w.elt * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(mu_out, (char*)w.u + w.elt * nn, w.elt * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return lm_finish(w, rep);
+}
+
+size_t serving_bytes(const pget_ctx* ctx) {
+    size_t b = 0;
+    for (auto& sl : ctx->slots)
+        if (sl->ws) b += sl->ws->bytes;
+    return b;
+}
+
+// Initial guess on the device without host synchronisation (serving path): lambda is
+// the constant c = sum y / sum A(1, mu0) (clamped to the box), mu = mu0.
+template <typename T>
+pget_status init_async(Workspace& w, const pget_lm_params& p, double mu_init, void* lam, void* mu, cudaStream_t st) {
+    const size_t nn = w.nn;
+    T* u = (T*)w.ut;
+    fill<T>(u, nn, 1.0, st);
+    const double mu0 = std::min(std::max(mu_init, 0.0), p.mu_max);
+    fill<T>(u + nn, nn, mu0, st);
+    pack_vec<T>(w, u, w.pk_ut, nullptr, st);
+    CK(op_forward(w, w.pk_ut, nullptr, w.Jp, nullptr, st));
+    fill<T>((T*)w.rt, w.M, 1.0, st);
+    dot<T>((const T*)w.Jp, (const T*)w.rt, w.M, w.dpart[0], nullptr, st);
+    finish_sum(w.dpart[0], &w.lm->init_sa, nullptr, st);
+    dot<T>((const T*)w.yb, (const T*)w.rt, w.M, w.dpart[1], nullptr, st);
+    finish_sum(w.dpart[1], &w.lm->init_sy, nullptr, st);
+    fill_ratio<T>((T*)lam, nn, &w.lm->init_sy, &w.lm->init_sa, p.lambda_max, st);
+    fill<T>((T*)mu, nn, mu0, st);
+    CK(cudaGetLastError());
+    return PGET_OK;
+}
+
+int max_inflight() {
+    const char* v = getenv("PGET_MAX_INFLIGHT");
+    int k = v ? atoi(v) : 0;
+    return k > 0 ? std::min(k, 64) : 8;
 }
 
 }  // namespace
@@ -722,6 +970,7 @@ pget_status pget_destroy(pget_ctx* ctx) {
     {
         DeviceGuard dg(ctx->device);
         cudaDeviceSynchronize();
+        ctx->slots.clear();
         ctx->ws.reset();
         if (ctx->scratch) cudaFree(ctx->scratch);
     }
@@ -897,6 +1146,146 @@ pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget
     CK(cudaMemcpyAsync(mu_host, (char*)w->q + e * nn, e * nn, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return PGET_OK;
+}
+
+pget_status pget_submit(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
+                        const void* lam0, const void* mu0, uint64_t* ticket) {
+    if (!ctx || !y || !ticket) return fail(PGET_EINVAL, "null argument");
+    if ((lam0 == nullptr) != (mu0 == nullptr)) return fail(PGET_EINVAL, "give both lam0 and mu0, or neither");
+    pget_status s = check_params(p);
+    if (s != PGET_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Geometry geo;
+    std::string key;
+    int groups = 1;
+    size_t need = 0;
+    s = resolve(g, p->precision, &geo, &key, &groups, &need);
+    if (s != PGET_OK) return s;
+    if (ctx->budget && need > ctx->budget)
+        return fail(PGET_ENOMEM, "request needs %zu bytes of workspace, budget is %zu", need, ctx->budget);
+    if (ctx->slots.empty())
+        for (int k = 0; k < max_inflight(); ++k) ctx->slots.emplace_back(new Slot);
+    // a free slot, preferably one whose cached workspace fits this request as is
+    Slot* sl = nullptr;
+    for (auto& c : ctx->slots)
+        if (c->state == Slot::kFree && c->ws && c->ws_key == key) {
+            sl = c.get();
+            break;
+        }
+    if (!sl)
+        for (auto& c : ctx->slots)
+            if (c->state == Slot::kFree && !c->ws) {
+                sl = c.get();
+                break;
+            }
+    if (!sl)
+        for (auto& c : ctx->slots)
+            if (c->state == Slot::kFree) {
+                sl = c.get();
+                break;
+            }
+    if (!sl) return fail(PGET_EAGAIN, "all %zu serving slots are busy", ctx->slots.size());
+    if (!(sl->ws && sl->ws_key == key)) {
+        sl->ws.reset();
+        sl->ws_key.clear();
+        size_t held = serving_bytes(ctx) + (ctx->ws ? ctx->ws->bytes : 0);
+        if (ctx->budget && held + need > ctx->budget) {
+            // release workspaces cached by other free slots, then re-check
+            for (auto& c : ctx->slots)
+                if (c->state == Slot::kFree && c->ws) {
+                    c->ws.reset();
+                    c->ws_key.clear();
+                }
+            held = serving_bytes(ctx) + (ctx->ws ? ctx->ws->bytes : 0);
+            if (held + need > ctx->budget)
+                return fail(PGET_EAGAIN, "device memory budget in use (%zu of %zu bytes held, %zu needed)", held,
+                            ctx->budget, need);
+        }
+        std::unique_ptr<Workspace> w;
+        s = make_workspace(ctx, std::move(geo), p->precision, groups, &w);
+        if (s != PGET_OK) return s;
+        sl->ws = std::move(w);
+        sl->ws_key = key;
+    }
+    if (!sl->stream) CK(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
+    if (!sl->done) CK(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
+    Workspace& w = *sl->ws;
+    cudaStream_t st = sl->stream;
+    const size_t nn = w.nn, e = w.elt;
+    // inputs into slot memory; the caller may free its buffers when this call returns
+    CK(cudaMemcpyAsync(w.yb, y, e * w.M, cudaMemcpyDeviceToDevice, st));
+    if (lam0) {
+        CK(cudaMemcpyAsync(w.u, lam0, e * nn, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync((char*)w.u + e * nn, mu0, e * nn, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    if (!lam0) {
+        s = w.f64 ? init_async<double>(w, *p, 0.01, w.u, (char*)w.u + e * nn, st)
+                  : init_async<float>(w, *p, 0.01, w.u, (char*)w.u + e * nn, st);
+        if (s != PGET_OK) return s;
+    }
+    s = w.f64 ? lm_launch<double>(w, *p, st) : lm_launch<float>(w, *p, st);
+    if (s != PGET_OK) return s;
+    CK(cudaEventRecord(sl->done, st));
+    sl->state = Slot::kRunning;
+    sl->ticket = ctx->next_ticket++;
+    *ticket = sl->ticket;
+    return PGET_OK;
+}
+
+pget_status pget_poll(pget_ctx* ctx, uint64_t ticket, void* lam_out, void* mu_out, pget_lm_report* rep, int* done) {
+    if (!ctx || !done) return fail(PGET_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    *done = 0;
+    Slot* sl = nullptr;
+    for (auto& c : ctx->slots)
+        if (c->state != Slot::kFree && c->ticket == ticket) sl = c.get();
+    if (!sl) return fail(PGET_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    if (sl->state == Slot::kRunning) {
+        cudaError_t q = cudaEventQuery(sl->done);
+        if (q == cudaErrorNotReady) return PGET_OK;
+        if (q != cudaSuccess) {
+            sl->state = Slot::kFree;
+            sl->ws.reset();
+            sl->ws_key.clear();
+            *done = 1;
+            return fail(PGET_ECUDA, "request %llu: %s", (unsigned long long)ticket, cudaGetErrorString(q));
+        }
+        sl->state = Slot::kDone;
+    }
+    Workspace& w = *sl->ws;
+    const size_t nn = w.nn, e = w.elt;
+    if (lam_out) CK(cudaMemcpyAsync(lam_out, w.u, e * nn, cudaMemcpyDeviceToDevice, sl->stream));
+    if (mu_out) CK(cudaMemcpyAsync(mu_out, (char*)w.u + e * nn, e * nn, cudaMemcpyDeviceToDevice, sl->stream));
+    CK(cudaStreamSynchronize(sl->stream));
+    pget_status s = lm_finish(w, rep);
+    sl->state = Slot::kFree;
+    *done = 1;
+    return s;
+}
+
+pget_status pget_cancel(pget_ctx* ctx, uint64_t ticket) {
+    if (!ctx) return fail(PGET_EINVAL, "null ctx");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    for (auto& c : ctx->slots)
+        if (c->state != Slot::kFree && c->ticket == ticket) {
+            // kernels cannot be aborted once queued: wait for them, then drop the result
+            cudaStreamSynchronize(c->stream);
+            c->state = Slot::kFree;
+            return PGET_OK;
+        }
+    return fail(PGET_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+}
+
+int32_t pget_inflight(pget_ctx* ctx) {
+    if (!ctx) return 0;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int k = 0;
+    for (auto& c : ctx->slots) k += c->state != Slot::kFree;
+    return k;
 }
 
 }  // extern "C"

@@ -21,8 +21,29 @@ template <> struct Vec2<double> { using type = double2; };
 __device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
 
-__device__ __forceinline__ float exp_(float x) { return expf(x); }
-__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ float exp2_(float x) { return exp2f(x); }
+__device__ __forceinline__ double exp2_(double x) { return exp2(x); }
+
+// w00 a00 + w10 a10 + w01 a01 + w11 a11 on (lambda, mu) pairs; packed FP32x2 on float
+__device__ __forceinline__ float2 bilerp2(float w00, float w10, float w01, float w11, float2 a00, float2 a10,
+                                          float2 a01, float2 a11) {
+    float2 r = __fmul2_rn(make_float2(w00, w00), a00);
+    r = __ffma2_rn(make_float2(w10, w10), a10, r);
+    r = __ffma2_rn(make_float2(w01, w01), a01, r);
+    return __ffma2_rn(make_float2(w11, w11), a11, r);
+}
+__device__ __forceinline__ double2 bilerp2(double w00, double w10, double w01, double w11, double2 a00,
+                                           double2 a10, double2 a01, double2 a11) {
+    return make_double2(w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x,
+                        w00 * a00.y + w10 * a10.y + w01 * a01.y + w11 * a11.y);
+}
+// t + w g on pairs
+__device__ __forceinline__ float2 fma2(float w, float2 g, float2 t) { return __ffma2_rn(make_float2(w, w), g, t); }
+__device__ __forceinline__ double2 fma2(double w, double2 g, double2 t) {
+    return make_double2(t.x + w * g.x, t.y + w * g.y);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
 // Running sum along a ray; KAHAN selects compensated summation (the compensation holds
 // the rounding excess of the last addition, the value is s - c).
@@ -106,6 +127,8 @@ enum WalkMode { kFwd = 0, kJvp = 1, kVjp = 2 };
 struct WalkArgs {
     const ViewDev* views;
     int n, T, P, Yc, nchunks, sb_cap;
+    int Ps;                    // shared-memory row pitch of a staged chunk (elements)
+    int nst;                   // VJP: stride between stencil planes (>= threads)
     double h;
     const void* u_img[2];      // padded interleaved (lambda, mu): [0] normal, [1] transposed
     const void* p_img[2];      // JVP: padded interleaved (dlambda, dmu)
@@ -120,17 +143,28 @@ struct WalkArgs {
     const int* src_det;
     const void* src_w;         // weights of the sub-rays on each slot (element type of the path)
     void* gpart;               // VJP: [n_views][2][n][n], pre-flip canonical layout
+    const int* group_off;      // VJP: CTA g handles views group_view[group_off[g] .. group_off[g+1])
+    const int* group_view;     //      (null: CTA g handles view g)
     const int* stop;           // optional: skip the launch when *stop != 0
     int* err;                  // error flags (bit 0: sample buffer overflow)
 };
 
 struct WalkPlan {
-    int threads = 0, Yc = 0, nchunks = 0, sb_cap = 0;
+    int threads = 0, Yc = 0, nchunks = 0, sb_cap = 0, Ps = 0, nst = 0;
     size_t smem = 0;
 };
 
+// h log2(e): the packed images hold mu in units where the attenuation sum is a power of 2
+inline double attenuation_scale(const Geometry& g) { return g.h * 1.4426950408889634; }
+
 // Plan (threads, rows per chunk, shared memory) for one walk mode.
 WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t smem_budget);
+
+// Permit the planned dynamic shared memory (call before capturing a graph).
+cudaError_t prepare_walk(int mode, int precision, const WalkPlan& plan);
+
+// Resident CTAs per SM of a planned walk kernel.
+int walk_occupancy(int mode, int precision, const WalkPlan& plan);
 
 // Launch one walk kernel over all views of the geometry.
 cudaError_t launch_walk(int mode, int precision, const WalkPlan& plan, const WalkArgs& a,

@@ -14,8 +14,10 @@ namespace pget {
 // ------------------------------------------------------------------------ packing
 // planar lambda, mu -> padded interleaved images, normal ([iy+1][ix+1]) and transposed
 // ([ix+1][iy+1]); the one-pixel border stays zero (bilinear samples see zero outside).
+// The second component is stored as mu * mu_scale (the ray kernels take h log2(e), so
+// the attenuation sum is directly the exponent of 2).
 template <typename T>
-__global__ void pack_kernel(const T* __restrict__ lam, const T* __restrict__ mu, int n, int P,
+__global__ void pack_kernel(const T* __restrict__ lam, const T* __restrict__ mu, int n, int P, T mu_scale,
                             typename Vec2<T>::type* __restrict__ out_n,
                             typename Vec2<T>::type* __restrict__ out_t, const int* skip) {
     using T2 = typename Vec2<T>::type;
@@ -25,7 +27,7 @@ __global__ void pack_kernel(const T* __restrict__ lam, const T* __restrict__ mu,
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         int iy = by + k, ix = bx + threadIdx.x;
         if (iy < n && ix < n) {
-            T2 v = mk2(lam[(size_t)iy * n + ix], mu[(size_t)iy * n + ix]);
+            T2 v = mk2(lam[(size_t)iy * n + ix], mu_scale * mu[(size_t)iy * n + ix]);
             out_n[(size_t)(iy + 1) * P + ix + 1] = v;
             tile[k][threadIdx.x] = v;
         }
@@ -38,15 +40,15 @@ __global__ void pack_kernel(const T* __restrict__ lam, const T* __restrict__ mu,
 }
 
 template <typename T>
-void pack(const T* lam, const T* mu, int n, int P, void* out_n, void* out_t, const int* skip,
+void pack(const T* lam, const T* mu, int n, int P, double mu_scale, void* out_n, void* out_t, const int* skip,
           cudaStream_t st) {
     dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-    pack_kernel<T><<<grid, block, 0, st>>>(lam, mu, n, P, (typename Vec2<T>::type*)out_n,
+    pack_kernel<T><<<grid, block, 0, st>>>(lam, mu, n, P, (T)mu_scale, (typename Vec2<T>::type*)out_n,
                                            (typename Vec2<T>::type*)out_t, skip);
     note_launch();
 }
-template void pack<float>(const float*, const float*, int, int, void*, void*, const int*, cudaStream_t);
-template void pack<double>(const double*, const double*, int, int, void*, void*, const int*, cudaStream_t);
+template void pack<float>(const float*, const float*, int, int, double, void*, void*, const int*, cudaStream_t);
+template void pack<double>(const double*, const double*, int, int, double, void*, void*, const int*, cudaStream_t);
 
 // ------------------------------------------------------------------------ prior
 // forward differences with a zero-flux border; W = 1/sqrt(|grad u|^2 + eps^2) or 1
@@ -213,6 +215,7 @@ __global__ void reduce_views_kernel(const T* __restrict__ gpart, const int* __re
             at[f][k].init();
         }
     const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll 2
     for (int v = v0; v < v1; ++v) {
         const T* gp = gpart + (size_t)v * 2 * nn;
         if (!vtrans[v]) {
@@ -596,5 +599,21 @@ void scale(T* y, size_t m, double c, cudaStream_t st) {
 }
 template void scale<float>(float*, size_t, double, cudaStream_t);
 template void scale<double>(double*, size_t, double, cudaStream_t);
+
+template <typename T>
+__global__ void fill_ratio_kernel(T* __restrict__ u, size_t m, const double* num, const double* den, double hi) {
+    const double d = *den;
+    double c = d > 0.0 ? *num / d : 0.0;
+    c = c < 0.0 ? 0.0 : (c > hi ? hi : c);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        u[i] = (T)c;
+}
+template <typename T>
+void fill_ratio(T* u, size_t m, const double* num, const double* den, double hi, cudaStream_t st) {
+    fill_ratio_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, m, num, den, hi);
+    note_launch();
+}
+template void fill_ratio<float>(float*, size_t, const double*, const double*, double, cudaStream_t);
+template void fill_ratio<double>(double*, size_t, const double*, const double*, double, cudaStream_t);
 
 }  // namespace pget

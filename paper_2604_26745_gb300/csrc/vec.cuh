@@ -19,6 +19,7 @@ struct CgState {
 struct LmState {
     double f, f0, nu, nu0;
     double sg, sHs, JsJs, rtrt, Rl, Rm, gg;
+    double init_sa, init_sy;         // initial guess: sum A(1, mu0) and sum y
     int accept, no_grad, iter, accepted, cg_total, pad;
     CgState cg;
     double tr_f[PGET_TRACE], tr_rho[PGET_TRACE], tr_nu[PGET_TRACE], tr_pred[PGET_TRACE], tr_ared[PGET_TRACE];
@@ -46,7 +47,8 @@ template <typename T> struct RedArgs {
 };
 
 template <typename T>
-void pack(const T* lam, const T* mu, int n, int P, void* out_n, void* out_t, const int* skip, cudaStream_t st);
+void pack(const T* lam, const T* mu, int n, int P, double mu_scale, void* out_n, void* out_t, const int* skip,
+          cudaStream_t st);
 template <typename T>
 void reg_weights(const T* u, int n, double eps, T* W, const int* skip, cudaStream_t st);
 template <typename T>
@@ -84,5 +86,8 @@ template <typename T>
 void copy_if(T* dst, const T* src, size_t m, const int* flag, cudaStream_t st);
 template <typename T>
 void scale(T* y, size_t m, double c, cudaStream_t st);
+// u[i] = clamp(*num / *den, 0, hi) (0 when *den <= 0), for i < m
+template <typename T>
+void fill_ratio(T* u, size_t m, const double* num, const double* den, double hi, cudaStream_t st);
 
 }  // namespace pget

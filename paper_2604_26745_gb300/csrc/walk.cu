@@ -47,7 +47,7 @@ template <typename T> constexpr int stencil_width() { return sizeof(T) == 8 ? 5 
 // one warp per row, 16-byte vectors (P is even, so a row of float2 is a whole number of
 // 16-byte vectors; a double2 is one vector).
 template <typename T2>
-__device__ __forceinline__ void stage_rows(T2* __restrict__ dst, const T2* __restrict__ src, int P,
+__device__ __forceinline__ void stage_rows(T2* __restrict__ dst, const T2* __restrict__ src, int P, int Ps,
                                            int n, int flipped, int row_lo, int nrows) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     constexpr int per = 16 / sizeof(T2);  // elements per 16-byte vector
@@ -56,7 +56,7 @@ __device__ __forceinline__ void stage_rows(T2* __restrict__ dst, const T2* __res
         const int r = row_lo + rr;
         const int gr = (flipped ? (n - 1 - r) : r) + 1;
         const float4* s = reinterpret_cast<const float4*>(src + (size_t)gr * P);
-        float4* d = reinterpret_cast<float4*>(dst + (size_t)rr * P);
+        float4* d = reinterpret_cast<float4*>(dst + (size_t)rr * Ps);
         for (int c = lane; c < nvec; c += 32) d[c] = s[c];
     }
 }
@@ -66,21 +66,18 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char sm[];
     if (A.stop && *A.stop) return;
-    const int v = blockIdx.x;
-    const ViewDev vp = A.views[v];
-    const int n = A.n, P = A.P, Yc = A.Yc, ns = vp.n_slots, tid = threadIdx.x;
-    const int nth = blockDim.x;
-    const bool active = tid < ns;
+    const int n = A.n, P = A.P, Ps = A.Ps, Yc = A.Yc, tid = threadIdx.x;
+    const int nth = A.nst;  // stencil plane stride (>= blockDim.x)
     const T h = (T)A.h;
     constexpr int SW = stencil_width<T>();
 
     size_t off = 0;
     T2* cu = (T2*)(sm + off);
-    off += sizeof(T2) * (size_t)(Yc + 1) * P;
+    off += sizeof(T2) * (size_t)(Yc + 1) * Ps;
     T2* cp = nullptr;
     if constexpr (MODE == kJvp) {
         cp = (T2*)(sm + off);
-        off += sizeof(T2) * (size_t)(Yc + 1) * P;
+        off += sizeof(T2) * (size_t)(Yc + 1) * Ps;
     }
     T* sval = (T*)(sm + off);
     off += sizeof(T2) * (size_t)nth;  // T2-sized slots keep the next arrays aligned
@@ -97,6 +94,17 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         off += sizeof(short) * (size_t)(Yc + 1) * nth;
     }
 
+    // the views of this CTA: one view, or (VJP) a group of views sharing the canonical
+    // orientation whose adjoint images are summed into the group's partial image
+    const int g = blockIdx.x;
+    const int gb = A.group_off ? A.group_off[g] : g;
+    const int ge = A.group_off ? A.group_off[g + 1] : g + 1;
+    for (int gi = gb; gi < ge; ++gi) {
+    const int v = A.group_view ? A.group_view[gi] : gi;
+    const bool first_view = gi == gb;
+    const ViewDev vp = A.views[v];
+    const int ns = vp.n_slots;
+    const bool active = tid < ns;
     const T2* ug = (const T2*)A.u_img[vp.transposed];
     const T2* pg = (MODE == kJvp) ? (const T2*)A.p_img[vp.transposed] : nullptr;
 
@@ -139,8 +147,8 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         const int row_lo = max(-1, row_hi - Yc + 1);
         const int nrows = row_hi - row_lo + 2;
         __syncthreads();
-        stage_rows(cu, ug, P, n, vp.flipped, row_lo, nrows);
-        if constexpr (MODE == kJvp) stage_rows(cp, pg, P, n, vp.flipped, row_lo, nrows);
+        stage_rows(cu, ug, P, Ps, n, vp.flipped, row_lo, nrows);
+        if constexpr (MODE == kJvp) stage_rows(cp, pg, P, Ps, n, vp.flipped, row_lo, nrows);
         if constexpr (MODE == kVjp) {
             for (int rr = 0; rr < nrows; ++rr) C0[rr * nth + tid] = kNoRow;
             cur_row = INT_MIN;  // the stencil rows of this chunk start empty
@@ -153,23 +161,22 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                 const int ix0 = pos.ix();
                 if (iy0 <= row_hi && ix0 >= -1 && ix0 <= n - 1) {
                     const T ax = pos.ax(), ay = pos.ay();
-                    const int o = (iy0 - row_lo) * P + ix0 + 1;
-                    const T2 a00 = cu[o], a10 = cu[o + 1], a01 = cu[o + P], a11 = cu[o + P + 1];
+                    const int o = (iy0 - row_lo) * Ps + ix0 + 1;
+                    const T2 a00 = cu[o], a10 = cu[o + 1], a01 = cu[o + Ps], a11 = cu[o + Ps + 1];
                     const T w11 = ax * ay, w10 = ax - w11, w01 = ay - w11;
                     const T w00 = (T(1) - ax) - w01;
-                    const T l = w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x;
-                    const T m = w00 * a00.y + w10 * a10.y + w01 * a01.y + w11 * a11.y;
-                    const T E = h * (S.val() + T(0.5) * m);
-                    const T at = exp_(-E);
+                    const T2 lm = bilerp2(w00, w10, w01, w11, a00, a10, a01, a11);
+                    const T l = lm.x, m = lm.y;  // m is mu h log2(e)
+                    const T at = exp2_(-(S.val() + T(0.5) * m));
                     if constexpr (MODE == kFwd) {
                         q.add(l * at);
                     } else if constexpr (MODE == kJvp) {
-                        const T2 b00 = cp[o], b10 = cp[o + 1], b01 = cp[o + P], b11 = cp[o + P + 1];
-                        const T dl = w00 * b00.x + w10 * b10.x + w01 * b01.x + w11 * b11.x;
-                        const T dm = w00 * b00.y + w10 * b10.y + w01 * b01.y + w11 * b11.y;
-                        const T dE = h * (dS.val() + T(0.5) * dm);
-                        q.add(at * (dl - l * dE));
-                        dS.add(dm);
+                        const T2 b00 = cp[o], b10 = cp[o + 1], b01 = cp[o + Ps], b11 = cp[o + Ps + 1];
+                        const T2 dd = bilerp2(w00, w10, w01, w11, b00, b10, b01, b11);
+                        // dE in natural units: ln 2 (dS + dm/2) with dS, dm scaled like m
+                        const T dE = T(0.6931471805599453) * (dS.val() + T(0.5) * dd.y);
+                        q.add(at * (dd.x - l * dE));
+                        dS.add(dd.y);
                     } else {
                         const T la = l * at;
                         const T Qh = (Utot - q.val()) - T(0.5) * la;
@@ -193,19 +200,12 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                         if ((unsigned)ol <= (unsigned)(SW - 2) && (unsigned)oh <= (unsigned)(SW - 2)) {
                             T2* pl = ST + (size_t)(rl * SW + ol) * nth + tid;
                             T2* ph = ST + (size_t)((rl + 1) * SW + oh) * nth + tid;
-                            T2 t0 = pl[0], t1 = pl[nth], t2 = ph[0], t3 = ph[nth];
-                            t0.x += w00 * gl;
-                            t0.y += w00 * gm;
-                            t1.x += w10 * gl;
-                            t1.y += w10 * gm;
-                            t2.x += w01 * gl;
-                            t2.y += w01 * gm;
-                            t3.x += w11 * gl;
-                            t3.y += w11 * gm;
-                            pl[0] = t0;
-                            pl[nth] = t1;
-                            ph[0] = t2;
-                            ph[nth] = t3;
+                            const T2 g2 = mk2(gl, gm);
+                            const T2 t0 = pl[0], t1 = pl[nth], t2 = ph[0], t3 = ph[nth];
+                            pl[0] = fma2(w00, g2, t0);
+                            pl[nth] = fma2(w10, g2, t1);
+                            ph[0] = fma2(w01, g2, t2);
+                            ph[nth] = fma2(w11, g2, t3);
                         } else {
                             atomicOr(A.err, 2);  // geometry bound violated: report, never write out of range
                         }
@@ -223,32 +223,32 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
             const int nout = (r1 - r0 + 1) * n;
             T2* carry_rd = (ck & 1) ? carry0 : carry1;
             T2* carry_wr = (ck & 1) ? carry1 : carry0;
-            T* gp = (T*)A.gpart + (size_t)v * 2 * n * n;
-            for (int e = tid; e < nout; e += nth) {
+            T* gp = (T*)A.gpart + (size_t)g * 2 * n * n;
+            for (int e = tid; e < nout; e += blockDim.x) {
                 const int dy = __float2int_rz(((float)e + 0.5f) * inv_n);
                 const int Yr = r0 + dy, Xc = e - dy * n;
                 const int rl = Yr - row_lo;
                 const float fi = ((float)Xc - X00f) * dXrf * invR2 + ((float)Yr - Y00f) * dYrf * invR2;
                 const int ilo = max(0, (int)ceilf(fi - wI)), ihi = min(ns - 1, (int)floorf(fi + wI));
-                T gl = T(0), gm = T(0);
+                T2 acc = mk2(T(0), T(0));
                 for (int i = ilo; i <= ihi; ++i) {
                     const int k = Xc - (int)C0[rl * nth + i];
-                    if ((unsigned)k < (unsigned)SW) {
-                        const T2 s = ST[(rl * SW + k) * nth + i];
-                        gl += s.x;
-                        gm += s.y;
-                    }
+                    if ((unsigned)k < (unsigned)SW) acc = add2(acc, ST[(rl * SW + k) * nth + i]);
                 }
-                if (ck > 0 && Yr == row_hi + 1) {
-                    gl += carry_rd[Xc].x;
-                    gm += carry_rd[Xc].y;
-                }
+                if (ck > 0 && Yr == row_hi + 1) acc = add2(acc, carry_rd[Xc]);
                 if (Yr == row_lo && ck < A.nchunks - 1) {
-                    carry_wr[Xc] = mk2(gl, gm);
+                    carry_wr[Xc] = acc;
                 } else {
                     const int row = vp.flipped ? (n - 1 - Yr) : Yr;
-                    gp[(size_t)row * n + Xc] = gl;
-                    gp[(size_t)n * n + (size_t)row * n + Xc] = gm;
+                    T* o0 = gp + (size_t)row * n + Xc;
+                    T* o1 = o0 + (size_t)n * n;
+                    if (first_view) {
+                        *o0 = acc.x;
+                        *o1 = acc.y;
+                    } else {
+                        *o0 += acc.x;
+                        *o1 += acc.y;
+                    }
                 }
             }
         }
@@ -263,45 +263,126 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         __syncthreads();
         T* y = (T*)A.y_out + (size_t)vp.angle * A.n_det + (size_t)vp.bank * A.nb;
         const T* wk = (const T*)A.w;
-        for (int d = tid; d < A.nb; d += nth) {
+        for (int d = tid; d < A.nb; d += blockDim.x) {
             const int* ds = A.det_slot + (size_t)(vp.bank * A.nb + d) * A.n_sub;
             T acc = T(0);
             for (int k = 0; k < A.n_sub; ++k) acc += wk[k] * sval[ds[k]];
             y[d] = h * acc;
         }
     }
+    __syncthreads();  // the next view of the group reuses shared memory
+    }
+
 }
 
-static size_t walk_smem(int mode, bool f64, int threads, int Yc, int P, int n) {
+// shared-memory row pitch: rows of one staged chunk start 16 words apart modulo the 32
+// banks, so lanes sampling two neighbouring rows do not collide
+static int smem_pitch(int P, bool f64) {
+    const int words = f64 ? 4 : 2;
+    int Ps = P;
+    while ((Ps * words) % 32 != 16) Ps += f64 ? 1 : 2;
+    return Ps;
+}
+
+// stencil plane stride: consecutive planes start 8 words apart modulo the banks, so
+// pixels gathering different columns of one ray's stencil do not collide
+static int stencil_stride(int threads, bool f64) {
+    const int words = f64 ? 4 : 2;
+    int s = threads;
+    while ((s * words) % 32 != 8) ++s;
+    return s;
+}
+
+static size_t walk_smem(int mode, bool f64, int threads, int Yc, int Ps, int nst, int n) {
     size_t s2 = f64 ? 16 : 8;
-    size_t b = s2 * (size_t)(Yc + 1) * P * (mode == kJvp ? 2 : 1) + s2 * threads;
-    if (mode == kVjp) b += s2 * (size_t)(Yc + 1) * (f64 ? 5 : 4) * threads + 2 * s2 * n + 2 * (size_t)(Yc + 1) * threads;
+    size_t b = s2 * (size_t)(Yc + 1) * Ps * (mode == kJvp ? 2 : 1) + s2 * nst;
+    if (mode == kVjp) b += s2 * (size_t)(Yc + 1) * (f64 ? 5 : 4) * nst + 2 * s2 * n + 2 * (size_t)(Yc + 1) * nst;
+    (void)threads;
     return (b + 15) / 16 * 16;
 }
 
 WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget) {
     WalkPlan pl;
     pl.threads = ((g.max_slots + 31) / 32) * 32;
+    pl.Ps = smem_pitch(P, f64);
+    pl.nst = mode == kVjp ? stencil_stride(pl.threads, f64) : pl.threads;
     int best = 1;
     for (int Yc = 1; Yc <= g.n + 1; ++Yc) {
-        if (walk_smem(mode, f64, pl.threads, Yc, P, g.n) <= budget) best = Yc;
+        if (walk_smem(mode, f64, pl.threads, Yc, pl.Ps, pl.nst, g.n) <= budget) best = Yc;
         else break;
     }
     pl.Yc = best;
     pl.nchunks = (g.n + 1 + best - 1) / best;
     pl.sb_cap = 0;
-    pl.smem = walk_smem(mode, f64, pl.threads, best, P, g.n);
+    pl.smem = walk_smem(mode, f64, pl.threads, best, pl.Ps, pl.nst, g.n);
     return pl;
 }
 
+// dynamic shared memory already permitted for each instantiation (set outside any
+// stream capture: prepare_walk runs before a CUDA graph is captured)
 template <typename T, bool K, int M>
-static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a, int n_views, cudaStream_t st) {
+static cudaError_t allow_smem(size_t bytes) {
+    static size_t allowed = 0;
+    if (bytes <= allowed) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<T, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) allowed = bytes;
+    return e;
+}
+
+template <typename T, bool K, int M>
+static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_views, cudaStream_t st) {
     auto kern = walk_kernel<T, K, M>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    cudaError_t e = allow_smem<T, K, M>(pl.smem);
     if (e != cudaSuccess) return e;
+    WalkArgs a = a0;
+    a.Ps = pl.Ps;
+    a.nst = pl.nst;
     kern<<<n_views, pl.threads, pl.smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
+}
+
+template <typename T, bool K, int M>
+static int occ_one(const WalkPlan& pl) {
+    auto kern = walk_kernel<T, K, M>;
+    if (allow_smem<T, K, M>(pl.smem) != cudaSuccess) return 1;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pl.threads, pl.smem) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+int walk_occupancy(int mode, int precision, const WalkPlan& pl) {
+#define PGET_O(T, K)                                      \
+    switch (mode) {                                       \
+        case kFwd: return occ_one<T, K, kFwd>(pl);        \
+        case kJvp: return occ_one<T, K, kJvp>(pl);        \
+        default: return occ_one<T, K, kVjp>(pl);          \
+    }
+    if (precision == PGET_F64) {
+        PGET_O(double, false)
+    } else if (precision == PGET_F32) {
+        PGET_O(float, false)
+    } else {
+        PGET_O(float, true)
+    }
+#undef PGET_O
+}
+
+cudaError_t prepare_walk(int mode, int precision, const WalkPlan& pl) {
+#define PGET_P(T, K)                                           \
+    switch (mode) {                                            \
+        case kFwd: return allow_smem<T, K, kFwd>(pl.smem);     \
+        case kJvp: return allow_smem<T, K, kJvp>(pl.smem);     \
+        default: return allow_smem<T, K, kVjp>(pl.smem);       \
+    }
+    if (precision == PGET_F64) {
+        PGET_P(double, false)
+    } else if (precision == PGET_F32) {
+        PGET_P(float, false)
+    } else {
+        PGET_P(float, true)
+    }
+#undef PGET_P
 }
 
 cudaError_t launch_walk(int mode, int precision, const WalkPlan& pl, const WalkArgs& a, int n_views,

@@ -83,6 +83,11 @@ _SIGS = {
                        C.POINTER(pget_lm_report), _vp], C.c_int),
     "pget_lm_solve_host": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
                             _vp, C.c_int32, C.POINTER(pget_lm_report), _vp], C.c_int),
+    "pget_submit": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp,
+                     C.POINTER(C.c_uint64)], C.c_int),
+    "pget_poll": ([_vp, C.c_uint64, _vp, _vp, C.POINTER(pget_lm_report), C.POINTER(C.c_int)], C.c_int),
+    "pget_cancel": ([_vp, C.c_uint64], C.c_int),
+    "pget_inflight": ([_vp], C.c_int32),
     "pget_forward_noalloc": ([C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
     "pget_profile_enable": ([_vp, C.c_int32], C.c_int),
     "pget_profile_read": ([_vp, C.POINTER(pget_kernel_stat), C.c_int32], C.c_int32),
@@ -259,6 +264,32 @@ def pget_lm_solve_host(ctx: Context, g: pget_geometry, p: pget_lm_params, y_host
                                      lam_host.data_ptr(), mu_host.data_ptr(), int(bool(init_guess)),
                                      C.byref(rep), _stream(stream)), ctx.h)
     return rep.to_dict()
+
+
+def pget_submit(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam0=None, mu0=None) -> int:
+    """Queue a reconstruction; returns its ticket.  Raises PgetError (status PGET_EAGAIN
+    when no slot or memory is free right now)."""
+    t = C.c_uint64(0)
+    _check(load().pget_submit(ctx.h, C.byref(g), C.byref(p), _ptr(y), _ptr(lam0), _ptr(mu0),
+                              C.byref(t)), ctx.h)
+    return t.value
+
+
+def pget_poll(ctx: Context, ticket: int, lam_out=None, mu_out=None):
+    """(done, report): report is None while the request still runs."""
+    rep = pget_lm_report()
+    done = C.c_int(0)
+    _check(load().pget_poll(ctx.h, C.c_uint64(ticket), _ptr(lam_out), _ptr(mu_out), C.byref(rep),
+                            C.byref(done)), ctx.h)
+    return bool(done.value), (rep.to_dict() if done.value else None)
+
+
+def pget_cancel(ctx: Context, ticket: int):
+    _check(load().pget_cancel(ctx.h, C.c_uint64(ticket)), ctx.h)
+
+
+def pget_inflight(ctx: Context) -> int:
+    return int(load().pget_inflight(ctx.h))
 
 
 def pget_forward_noalloc(g: pget_geometry, precision: int, lam, mu, y, stream=None) -> int:

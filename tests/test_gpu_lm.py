@@ -172,3 +172,21 @@ def test_lm_c2_geometry_stable_regime(ctx, O, P, torch):
     assert rep["acc"] == rep_ref["acc"]
     assert rel2(lam.cpu().numpy(), lr) <= 1e-4
     assert rel2(mu.cpu().numpy(), mr) <= 1e-4
+
+
+def test_graph_replay_matches_direct_launches(ctx, O, P, torch, monkeypatch):
+    """The LM body runs as a captured CUDA graph by default; replays and the direct
+    (graph-free) launch sequence must give bitwise-identical results."""
+    n, na, nd, S = 48, 60, 182, 5
+    go, ph, y = _problem(O, n, na, nd, S, 5, 2.5, 1e5, 7)
+    g = P.geometry(n, na, nd, n_sub=S)
+    p = P.default_params(max_iters=4, cg_max_iters=10, precision=P.PGET_F32_KAHAN)
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    outs = []
+    for no_graph in ("0", "0", "1"):
+        monkeypatch.setenv("PGET_NO_GRAPH", no_graph)
+        lam, mu = P.pget_initial_guess(ctx, g, p, yd)
+        rep = P.pget_lm_solve(ctx, g, p, yd, lam, mu)
+        outs.append((lam.clone(), mu.clone(), rep["f"]))
+    for o in outs[1:]:
+        assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1]) and o[2] == outs[0][2]
