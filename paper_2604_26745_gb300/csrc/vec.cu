@@ -179,14 +179,20 @@ void dot(const T* a, const T* b, size_t m, double* part, const int* skip, cudaSt
 template void dot<float>(const float*, const float*, size_t, double*, const int*, cudaStream_t);
 template void dot<double>(const double*, const double*, size_t, double*, const int*, cudaStream_t);
 
-// sum kRedBlocks partials (block order) into *dst
+// Sum of the kRedBlocks partials by one warp in a fixed order (lane l adds partials
+// l, l+32, ...; then a fixed shuffle tree): deterministic, and the loads overlap.
+__device__ __forceinline__ double warp_sum_partials(const double* __restrict__ part) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < kRedBlocks; b += 32) s += part[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;  // the same value in every lane
+}
+
+// sum kRedBlocks partials into *dst
 __global__ void finish_sum_kernel(const double* __restrict__ part, double* dst, const int* skip) {
     if (skip && *skip) return;
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < kRedBlocks; ++b) s += part[b];
-        *dst = s;
-    }
+    const double s = warp_sum_partials(part);
+    if (threadIdx.x == 0) *dst = s;
 }
 void finish_sum(const double* part, double* dst, const int* skip, cudaStream_t st) {
     finish_sum_kernel<<<1, 32, 0, st>>>(part, dst, skip);
@@ -375,9 +381,8 @@ __global__ void cg_init_kernel(const T* __restrict__ b, T* __restrict__ x, T* __
 }
 
 __global__ void cg_finish_init_kernel(const double* __restrict__ part, CgState* cg) {
-    if (threadIdx.x || blockIdx.x) return;
-    double s = 0.0;
-    for (int b = 0; b < kRedBlocks; ++b) s += part[b];
+    const double s = warp_sum_partials(part);
+    if (threadIdx.x) return;
     cg->rr = s;
     cg->bnorm = sqrt(s);
     cg->stop = !(cg->bnorm > 0.0) || !isfinite(s);
@@ -386,9 +391,9 @@ __global__ void cg_finish_init_kernel(const double* __restrict__ part, CgState* 
 
 // after q = A p and partials of <p, q>
 __global__ void cg_finish_pq_kernel(const double* __restrict__ part, CgState* cg) {
-    if (threadIdx.x || blockIdx.x || cg->stop) return;
-    double s = 0.0;
-    for (int b = 0; b < kRedBlocks; ++b) s += part[b];
+    if (cg->stop) return;
+    const double s = warp_sum_partials(part);
+    if (threadIdx.x) return;
     cg->pq = s;
     if (!(s > 0.0) || !isfinite(s)) {
         cg->stop = 1;
@@ -415,9 +420,9 @@ __global__ void cg_update_kernel(T* __restrict__ x, T* __restrict__ res, const T
 }
 
 __global__ void cg_finish_rr_kernel(const double* __restrict__ part, CgState* cg) {
-    if (threadIdx.x || blockIdx.x || cg->stop) return;
-    double s = 0.0;
-    for (int b = 0; b < kRedBlocks; ++b) s += part[b];
+    if (cg->stop) return;
+    const double s = warp_sum_partials(part);
+    if (threadIdx.x) return;
     cg->iters += 1;
     if (sqrt(s) <= cg->tol * cg->bnorm || !isfinite(s)) {
         cg->stop = 1;
