@@ -553,12 +553,19 @@ pget_status run_cg(Workspace& w, const void* b, double scale_b, double nu, const
     return PGET_OK;
 }
 
+// device error flags: bit 1 an adjoint stencil bound was violated (never expected: the
+// geometry guarantees it), bit 2 a chunk copy did not complete within the wait limit
+pget_status flags_status(int e) {
+    if (e & 4) return fail(PGET_ETIMEOUT, "device error flags 0x%x (chunk copy wait timed out)", e);
+    if (e) return fail(PGET_ECUDA, "device error flags 0x%x (adjoint stencil bound)", e);
+    return PGET_OK;
+}
+
 pget_status check_err(Workspace& w, cudaStream_t st) {
     int e = 0;
     CK(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (e) return fail(PGET_ECUDA, "device error flags 0x%x (adjoint stencil bound)", e);
-    return PGET_OK;
+    return flags_status(e);
 }
 
 void params_dev(const pget_lm_params& p, LmParamsDev* d) {
@@ -744,7 +751,7 @@ pget_status lm_finish(Workspace& w, pget_lm_report* rep) {
     if (w.graph_used && w.prof->on) w.prof->collect_graph(w.graph_events);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, w.t0, w.t1);
-    if (*w.host_err) return fail(PGET_ECUDA, "device error flags 0x%x (adjoint stencil bound)", *w.host_err);
+    if (*w.host_err) return flags_status(*w.host_err);
     const LmState* hl = w.host_lm;
     if (rep) {
         memset(rep, 0, sizeof *rep);

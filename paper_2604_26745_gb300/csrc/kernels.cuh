@@ -146,7 +146,7 @@ struct WalkArgs {
     const int* group_off;      // VJP: CTA g handles views group_view[group_off[g] .. group_off[g+1])
     const int* group_view;     //      (null: CTA g handles view g)
     const int* stop;           // optional: skip the launch when *stop != 0
-    int* err;                  // error flags (bit 0: sample buffer overflow)
+    int* err;                  // error flags (bit 1: adjoint stencil bound, bit 2: chunk copy wait timed out)
 };
 
 struct WalkPlan {

@@ -44,9 +44,67 @@ constexpr short kNoRow = -30000;  // stencil origin of a (ray, row) the ray neve
 // of slack for rounding at exactly 45-degree views.
 template <typename T> constexpr int stencil_width() { return sizeof(T) == 8 ? 5 : 4; }
 
-// Copy canonical rows [row_lo, row_lo + nrows) of a padded layout into shared memory:
-// one warp per row, 16-byte vectors (P is even, so a row of float2 is a whole number of
-// 16-byte vectors; a double2 is one vector).
+// ---- chunk staging: TMA bulk copies (cp.async.bulk) completing on an mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mb_init(unsigned long long* mb, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+// make the initialised barriers visible to the async proxy (the copy engine)
+__device__ __forceinline__ void mb_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// order earlier generic-proxy accesses of shared memory before later async-proxy writes
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mb_expect_tx(unsigned long long* mb, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* mb) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mb))
+                 : "memory");
+}
+__device__ __forceinline__ bool mb_try_wait(unsigned long long* mb, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(mb)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for a phase of a chunk barrier.  Bounded: after ~4M polls (far beyond any copy
+// time) it sets error bit 2 and returns, so a lost copy never hangs the GPU; every
+// thread still reaches every barrier of the kernel.
+__device__ __forceinline__ void mb_wait(unsigned long long* mb, unsigned parity, int* err) {
+    unsigned it = 0;
+    while (!mb_try_wait(mb, parity)) {
+        if (++it > (1u << 22)) {
+            atomicOr(err, 4);
+            break;
+        }
+    }
+}
+
+// Copy canonical rows [row_lo, row_lo + nrows) of a padded layout into a shared-memory
+// chunk (row pitch Ps): one bulk copy per row of P elements, issued by the lanes of one
+// warp in parallel (lane k takes rows k, k + 32, ...).  Row bytes, source and destination
+// offsets are multiples of 16 (P and Ps even).
+template <typename T2>
+__device__ __forceinline__ void issue_rows(T2* dst, const T2* src, int P, int Ps, int n, int flipped, int row_lo,
+                                           int nrows, unsigned long long* mb, int lane) {
+    const unsigned bytes = (unsigned)(P * sizeof(T2));
+    for (int rr = lane; rr < nrows; rr += 32) {
+        const int r = row_lo + rr;
+        const int gr = (flipped ? (n - 1 - r) : r) + 1;
+        bulk_g2s(dst + (size_t)rr * Ps, src + (size_t)gr * P, bytes, mb);
+    }
+}
+
+// Copy canonical rows [row_lo, row_lo + nrows) of a padded layout into shared memory with
+// plain loads: one warp per row, 16-byte vectors (P is even, so a row of float2 is a whole
+// number of 16-byte vectors; a double2 is one vector).
 template <typename T2>
 __device__ __forceinline__ void stage_rows(T2* __restrict__ dst, const T2* __restrict__ src, int P, int Ps,
                                            int n, int flipped, int row_lo, int nrows) {
@@ -62,6 +120,13 @@ __device__ __forceinline__ void stage_rows(T2* __restrict__ dst, const T2* __res
     }
 }
 
+// rows of chunk ck: base rows row_hi down to row_lo, staged rows row_lo .. row_hi + 1
+__device__ __forceinline__ void chunk_rows(int n, int Yc, int ck, int* row_hi, int* row_lo, int* nrows) {
+    *row_hi = n - 1 - ck * Yc;
+    *row_lo = max(-1, *row_hi - Yc + 1);
+    *nrows = *row_hi - *row_lo + 2;
+}
+
 template <typename T, bool KAHAN, int MODE>
 __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     using T2 = typename Vec2<T>::type;
@@ -72,14 +137,16 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     const T h = (T)A.h;
     constexpr int SW = stencil_width<T>();
 
+    // row buffers: the forward and the JVP double-buffer their chunks, which arrive by TMA
+    // bulk copies (the next chunk is copied while the current one is walked); the adjoint
+    // stages its single buffer with plain loads of all warps between its chunks (measured
+    // faster there: its short chunks alternate walk and gather phases)
+    constexpr int NB = MODE == kVjp ? 1 : 2;
+    constexpr bool TMA = MODE != kVjp;
+    const size_t rbytes = sizeof(T2) * (size_t)(Yc + 1) * Ps;  // one staged image chunk
     size_t off = 0;
-    T2* cu = (T2*)(sm + off);
-    off += sizeof(T2) * (size_t)(Yc + 1) * Ps;
-    T2* cp = nullptr;
-    if constexpr (MODE == kJvp) {
-        cp = (T2*)(sm + off);
-        off += sizeof(T2) * (size_t)(Yc + 1) * Ps;
-    }
+    T2* const cu0 = (T2*)sm;  // buffer 0: (lambda, mu) [, (dlambda, dmu)]; buffer 1 follows
+    off += NB * rbytes * (MODE == kJvp ? 2 : 1);
     T* sval = (T*)(sm + off);
     off += sizeof(T2) * (size_t)nth;  // T2-sized slots keep the next arrays aligned
     T2 *ST = nullptr, *carry0 = nullptr, *carry1 = nullptr;
@@ -94,6 +161,14 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         C0 = (short*)(sm + off);  // [row * nth + ray]
         off += sizeof(short) * (size_t)(Yc + 1) * nth;
     }
+    off = (off + 7) / 8 * 8;
+    unsigned long long* mb = (unsigned long long*)(sm + off);  // one barrier per row buffer
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) mb_init(&mb[b], 1);
+        mb_init_fence();
+    }
+    __syncthreads();
+    unsigned phase = 0;  // bit b: parity of the next completed phase of buffer b
 
     // the views of this CTA: one view, or (VJP) a group of views sharing the canonical
     // orientation whose adjoint images are summed into the group's partial image
@@ -143,18 +218,44 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     const float wI = (fabsf(dXrf) + fabsf(dYrf)) * invR2 + 0.01f;
     const float inv_n = 1.0f / (float)n;
 
+    // copy of chunk ck into buffer b, issued by warp 0: lane 0 announces the bytes on the
+    // buffer's barrier, then every lane issues its rows
+    auto issue = [&](int ck, int b) {
+        int rh, rl, nr;
+        chunk_rows(n, Yc, ck, &rh, &rl, &nr);
+        if (tid == 0) {
+            proxy_fence();
+            mb_expect_tx(&mb[b], (unsigned)(nr * P * sizeof(T2)) * (MODE == kJvp ? 2u : 1u));
+        }
+        __syncwarp();
+        T2* dst = (T2*)((unsigned char*)cu0 + (size_t)b * rbytes * (MODE == kJvp ? 2 : 1));
+        issue_rows(dst, ug, P, Ps, n, vp.flipped, rl, nr, &mb[b], tid);
+        if constexpr (MODE == kJvp)
+            issue_rows((T2*)((unsigned char*)dst + rbytes), pg, P, Ps, n, vp.flipped, rl, nr, &mb[b], tid);
+    };
+    if (TMA && tid < 32) issue(0, 0);  // the buffers are free: the previous view ended with a barrier
+
     for (int ck = 0; ck < A.nchunks; ++ck) {
-        const int row_hi = n - 1 - ck * Yc;
-        const int row_lo = max(-1, row_hi - Yc + 1);
-        const int nrows = row_hi - row_lo + 2;
-        __syncthreads();
-        stage_rows(cu, ug, P, Ps, n, vp.flipped, row_lo, nrows);
-        if constexpr (MODE == kJvp) stage_rows(cp, pg, P, Ps, n, vp.flipped, row_lo, nrows);
+        int row_hi, row_lo, nrows;
+        chunk_rows(n, Yc, ck, &row_hi, &row_lo, &nrows);
+        const int b = NB == 2 ? (ck & 1) : 0;
+        if constexpr (NB == 2)  // buffer b ^ 1 was released by the barrier ending chunk ck - 1
+            if (tid < 32 && ck + 1 < A.nchunks) issue(ck + 1, b ^ 1);
         if constexpr (MODE == kVjp) {
+            __syncthreads();  // the gather of chunk ck - 1 has read every stencil
             for (int rr = 0; rr < nrows; ++rr) C0[rr * nth + tid] = kNoRow;
             cur_row = INT_MIN;  // the stencil rows of this chunk start empty
         }
-        __syncthreads();
+        if constexpr (TMA) {
+            mb_wait(&mb[b], (phase >> b) & 1u, A.err);
+            phase ^= 1u << b;
+        } else {
+            stage_rows(cu0, ug, P, Ps, n, vp.flipped, row_lo, nrows);
+            __syncthreads();
+        }
+        const T2* cu = (const T2*)((const unsigned char*)cu0 + (size_t)b * rbytes * (MODE == kJvp ? 2 : 1));
+        const T2* cp = (const T2*)((const unsigned char*)cu + rbytes);  // JVP only
+        (void)cp;
         if (active) {
             while (j >= jlo) {
                 const int iy0 = pos.iy();
@@ -218,8 +319,8 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                 pos.back();
             }
         }
+        __syncthreads();  // every walk of chunk ck is done: its row buffer is free
         if constexpr (MODE == kVjp) {
-            __syncthreads();
             const int r0 = max(row_lo, 0), r1 = min(row_hi + 1, n - 1);
             const int nout = (r1 - r0 + 1) * n;
             T2* carry_rd = (ck & 1) ? carry0 : carry1;
@@ -298,8 +399,10 @@ static int stencil_stride(int threads, bool f64) {
 
 static size_t walk_smem(int mode, bool f64, int threads, int Yc, int Ps, int nst, int n) {
     size_t s2 = f64 ? 16 : 8;
-    size_t b = s2 * (size_t)(Yc + 1) * Ps * (mode == kJvp ? 2 : 1) + s2 * nst;
+    const size_t nbuf = mode == kVjp ? 1 : 2;  // row buffers (see the kernel)
+    size_t b = nbuf * s2 * (size_t)(Yc + 1) * Ps * (mode == kJvp ? 2 : 1) + s2 * nst;
     if (mode == kVjp) b += s2 * (size_t)(Yc + 1) * (f64 ? 5 : 4) * nst + 2 * s2 * n + 2 * (size_t)(Yc + 1) * nst;
+    b = (b + 7) / 8 * 8 + 8 * nbuf;  // chunk barriers
     (void)threads;
     return (b + 15) / 16 * 16;
 }
