@@ -203,8 +203,10 @@ void finish_sum(const double* part, double* dst, const int* skip, cudaStream_t s
 // Stage 1: block (tile, view group) sums the partial images of its views over a 32 x 32
 // pixel tile.  Views with a transposed canonical frame wrote [ix][iy]; they are summed
 // in that orientation and transposed once through shared memory.
+// (float: at most 64 registers, so that four 256-thread blocks fit an SM and the
+// tiles x groups grid of about 2 x 304 blocks runs in a single wave)
 template <typename T, bool KAHAN>
-__global__ void reduce_views_kernel(const T* __restrict__ gpart, const int* __restrict__ vtrans, int n,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 && !KAHAN ? 4 : 3) reduce_views_kernel(const T* __restrict__ gpart, const int* __restrict__ vtrans, int n,
                                     int n_views, int groups, T* __restrict__ out2, const int* skip) {
     using T2 = typename Vec2<T>::type;
     if (skip && *skip) return;
@@ -221,7 +223,8 @@ __global__ void reduce_views_kernel(const T* __restrict__ gpart, const int* __re
             at[f][k].init();
         }
     const int tx = threadIdx.x, ty = threadIdx.y;
-#pragma unroll 2
+    constexpr int kUnroll = sizeof(T) == 4 && !KAHAN ? 4 : 2;  // loads in flight within 64 registers
+#pragma unroll kUnroll
     for (int v = v0; v < v1; ++v) {
         const T* gp = gpart + (size_t)v * 2 * nn;
         if (!vtrans[v]) {
