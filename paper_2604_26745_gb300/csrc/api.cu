@@ -139,6 +139,7 @@ struct Workspace {
     int* d_src_det = nullptr;
     void* d_src_w = nullptr;    // per-slot sub-ray weights in the element type of the path
     int2* d_clip = nullptr;
+    int2* d_win = nullptr;       // adjoint ray windows [view][chunk]
     // adjoint view groups: CTA g sums views group_view[group_off[g] .. group_off[g+1]),
     // all of one canonical orientation (gtrans[g]), into partial image g
     int n_groups = 0;
@@ -212,6 +213,7 @@ static size_t workspace_bytes(const Geometry& g, int prec, int groups) {
     b += 4 * kRedBlocks * 8 + sizeof(LmState) + 64;
     b += V * sizeof(ViewDev) + V * 4 + (size_t)g.n_det * g.n_sub * 4 + g.n_sub * 8;
     b += g.src_off.size() * 4 + g.src_det.size() * 12 + g.clip.size() * 4;
+    b += V * (size_t)(g.n + 1) * 8;     // adjoint ray windows (at most n + 1 chunks per view)
     return b;
 }
 
@@ -310,7 +312,11 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     };
     w->pf = plan_walk(G, w->P, kFwd, w->f64, budget("PGET_SMEM_KB_FWD", 64));
     w->pj = plan_walk(G, w->P, kJvp, w->f64, budget("PGET_SMEM_KB_JVP", 64));
-    w->pv = plan_walk(G, w->P, kVjp, w->f64, budget("PGET_SMEM_KB_VJP", 72));
+    {
+        std::vector<int2> rows;
+        ray_rows(G, w->f64, &rows);
+        w->pv = plan_walk(G, w->P, kVjp, w->f64, budget("PGET_SMEM_KB_VJP", 72), &rows);
+    }
     // views per adjoint CTA: one by default (the hardware scheduler balances single-view
     // CTAs across SMs best); PGET_VJP_VIEWS_PER_CTA > 1 groups views of one orientation,
     // which shrinks the partial images but assigns work statically; 0 sizes groups so that
@@ -357,6 +363,8 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     CK(upload_t(&w->d_w, G.w));
     CK(w->alloc(&w->d_clip, sizeof(int) * G.clip.size()));
     CK(cudaMemcpy(w->d_clip, G.clip.data(), sizeof(int) * G.clip.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_win, sizeof(int2) * w->pv.win.size()));
+    CK(cudaMemcpy(w->d_win, w->pv.win.data(), sizeof(int2) * w->pv.win.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_src_off, sizeof(int) * G.src_off.size()));
     CK(cudaMemcpy(w->d_src_off, G.src_off.data(), sizeof(int) * G.src_off.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_src_det, sizeof(int) * G.src_det.size()));
@@ -492,6 +500,7 @@ cudaError_t op_vjp(Workspace& w, void* const pku[2], const void* U, const void* 
     a.slot_val = (void*)U;
     a.r_in = r;
     a.gpart = w.gpart;
+    a.win = w.d_win;
     a.group_off = w.d_group_off;
     a.group_view = w.d_group_view;
     a.stop = stop;

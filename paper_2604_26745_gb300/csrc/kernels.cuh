@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <type_traits>
+#include <vector>
 
 #include "pget_internal.cuh"
 
@@ -104,8 +105,8 @@ template <> struct Pos<double> {
         fy = floor(Y);
     }
     __device__ __forceinline__ void init(const ViewDev& v, int i, int j_) {
-        X0 = v.X00d + i * v.dXrd;
-        Y0 = v.Y00d + i * v.dYrd;
+        X0 = fma((double)i, v.dXrd, v.X00d);  // explicit fma: the host repeats it exactly
+        Y0 = fma((double)i, v.dYrd, v.Y00d);
         dX = v.dXsd;
         dY = v.dYsd;
         j = j_;
@@ -143,6 +144,8 @@ struct WalkArgs {
     const int* src_det;
     const void* src_w;         // weights of the sub-rays on each slot (element type of the path)
     void* gpart;               // VJP: [n_views][2][n][n], pre-flip canonical layout
+    const int2* win;           // VJP: [n_views][nchunks] (first slot, count) of the rays with
+                               //      samples in the chunk; stencil column = slot - first
     const int* group_off;      // VJP: CTA g handles views group_view[group_off[g] .. group_off[g+1])
     const int* group_view;     //      (null: CTA g handles view g)
     const int* stop;           // optional: skip the launch when *stop != 0
@@ -152,13 +155,21 @@ struct WalkArgs {
 struct WalkPlan {
     int threads = 0, Yc = 0, nchunks = 0, sb_cap = 0, Ps = 0, nst = 0;
     size_t smem = 0;
+    std::vector<int2> win;  // VJP: [view][chunk] ray window of each chunk
 };
+
+// Rows of the first (largest j) and last valid sample of every ray, computed with the
+// kernels' own arithmetic (32.32 fixed point, or double fma); (INT_MIN, INT_MIN) for a
+// ray without valid samples.  [view][max_slots].
+void ray_rows(const Geometry& g, bool f64, std::vector<int2>* rows);
 
 // h log2(e): the packed images hold mu in units where the attenuation sum is a power of 2
 inline double attenuation_scale(const Geometry& g) { return g.h * 1.4426950408889634; }
 
 // Plan (threads, rows per chunk, shared memory) for one walk mode.
-WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t smem_budget);
+// The adjoint plan needs the ray rows (ray_rows) to size its stencil windows.
+WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t smem_budget,
+                   const std::vector<int2>* rows = nullptr);
 
 // Permit the planned dynamic shared memory (call before capturing a graph).
 cudaError_t prepare_walk(int mode, int precision, const WalkPlan& plan);

@@ -23,7 +23,9 @@
 // whose footprint covers it: no atomics, no write conflicts, deterministic order.  Rows
 // shared by consecutive chunks are completed through a carried pixel row; each view
 // writes its own partial image, reduce_views sums them in a fixed order.
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <climits>
 #include <cstdio>
 #include <cstdlib>
@@ -147,8 +149,8 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     size_t off = 0;
     T2* const cu0 = (T2*)sm;  // buffer 0: (lambda, mu) [, (dlambda, dmu)]; buffer 1 follows
     off += NB * rbytes * (MODE == kJvp ? 2 : 1);
-    T* sval = (T*)(sm + off);
-    off += sizeof(T2) * (size_t)nth;  // T2-sized slots keep the next arrays aligned
+    T* sval = (T*)(sm + off);  // forward / JVP: ray totals
+    if constexpr (MODE != kVjp) off += sizeof(T2) * (size_t)nth;  // T2-sized: keeps alignment
     T2 *ST = nullptr, *carry0 = nullptr, *carry1 = nullptr;
     short* C0 = nullptr;
     if constexpr (MODE == kVjp) {
@@ -241,9 +243,18 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         const int b = NB == 2 ? (ck & 1) : 0;
         if constexpr (NB == 2)  // buffer b ^ 1 was released by the barrier ending chunk ck - 1
             if (tid < 32 && ck + 1 < A.nchunks) issue(ck + 1, b ^ 1);
+        // adjoint: stencil columns cover the window of rays with samples in this chunk
+        int wa = 0, wn = 0, ts = 0;
+        bool in_win = false;
         if constexpr (MODE == kVjp) {
+            const int2 wv = A.win ? A.win[(size_t)v * A.nchunks + ck] : make_int2(0, ns);
+            wa = wv.x;
+            wn = wv.y;
+            ts = tid - wa;
+            in_win = (unsigned)ts < (unsigned)wn;
             __syncthreads();  // the gather of chunk ck - 1 has read every stencil
-            for (int rr = 0; rr < nrows; ++rr) C0[rr * nth + tid] = kNoRow;
+            if (tid < wn)
+                for (int rr = 0; rr < nrows; ++rr) C0[rr * nth + tid] = kNoRow;
             cur_row = INT_MIN;  // the stencil rows of this chunk start empty
         }
         if constexpr (TMA) {
@@ -285,23 +296,24 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                         const T gl = rho * h * at;
                         const T gm = -rho * h * h * Qh;
                         const int rl = iy0 - row_lo;  // lower row of the cell; upper is rl + 1
-                        if (iy0 != cur_row) {
+                        if (iy0 != cur_row && in_win) {
                             if (iy0 + 1 != cur_row) {
                                 c0_hi = ix0 - base;
-                                C0[(rl + 1) * nth + tid] = (short)c0_hi;
-                                for (int k = 0; k < SW; ++k) ST[((rl + 1) * SW + k) * nth + tid] = mk2(T(0), T(0));
+                                C0[(rl + 1) * nth + ts] = (short)c0_hi;
+                                for (int k = 0; k < SW; ++k) ST[((rl + 1) * SW + k) * nth + ts] = mk2(T(0), T(0));
                             } else {
                                 c0_hi = c0_lo;
                             }
                             c0_lo = ix0 - base;
-                            C0[rl * nth + tid] = (short)c0_lo;
-                            for (int k = 0; k < SW; ++k) ST[(rl * SW + k) * nth + tid] = mk2(T(0), T(0));
+                            C0[rl * nth + ts] = (short)c0_lo;
+                            for (int k = 0; k < SW; ++k) ST[(rl * SW + k) * nth + ts] = mk2(T(0), T(0));
                             cur_row = iy0;
                         }
                         const int ol = ix0 - c0_lo, oh = ix0 - c0_hi;
-                        if ((unsigned)ol <= (unsigned)(SW - 2) && (unsigned)oh <= (unsigned)(SW - 2)) {
-                            T2* pl = ST + (size_t)(rl * SW + ol) * nth + tid;
-                            T2* ph = ST + (size_t)((rl + 1) * SW + oh) * nth + tid;
+                        // in_win holds by construction of the windows; never write outside them
+                        if ((unsigned)ol <= (unsigned)(SW - 2) && (unsigned)oh <= (unsigned)(SW - 2) && in_win) {
+                            T2* pl = ST + (size_t)(rl * SW + ol) * nth + ts;
+                            T2* ph = ST + (size_t)((rl + 1) * SW + oh) * nth + ts;
                             const T2 g2 = mk2(gl, gm);
                             const T2 t0 = pl[0], t1 = pl[nth], t2 = ph[0], t3 = ph[nth];
                             pl[0] = fma2(w00, g2, t0);
@@ -331,11 +343,11 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                 const int Yr = r0 + dy, Xc = e - dy * n;
                 const int rl = Yr - row_lo;
                 const float fi = ((float)Xc - X00f) * dXrf * invR2 + ((float)Yr - Y00f) * dYrf * invR2;
-                const int ilo = max(0, (int)ceilf(fi - wI)), ihi = min(ns - 1, (int)floorf(fi + wI));
+                const int ilo = max(0, (int)ceilf(fi - wI - wa)), ihi = min(wn - 1, (int)floorf(fi + wI - wa));
                 T2 acc = mk2(T(0), T(0));
-                for (int i = ilo; i <= ihi; ++i) {
-                    const int k = Xc - (int)C0[rl * nth + i];
-                    if ((unsigned)k < (unsigned)SW) acc = add2(acc, ST[(rl * SW + k) * nth + i]);
+                for (int t = ilo; t <= ihi; ++t) {  // window columns of the candidate rays
+                    const int k = Xc - (int)C0[rl * nth + t];
+                    if ((unsigned)k < (unsigned)SW) acc = add2(acc, ST[(rl * SW + k) * nth + t]);
                 }
                 if (ck > 0 && Yr == row_hi + 1) acc = add2(acc, carry_rd[Xc]);
                 if (Yr == row_lo && ck < A.nchunks - 1) {
@@ -397,20 +409,111 @@ static int stencil_stride(int threads, bool f64) {
     return s;
 }
 
+void ray_rows(const Geometry& g, bool f64, std::vector<int2>* rows) {
+    const int V = (int)g.views.size(), ms = g.max_slots, n = g.n;
+    rows->assign((size_t)V * ms, make_int2(INT_MIN, INT_MIN));
+    for (int v = 0; v < V; ++v) {
+        const ViewDev& vp = g.views[v];
+        for (int i = 0; i < vp.n_slots; ++i) {
+            const int jlo = g.clip[((size_t)v * ms + i) * 2], jhi = g.clip[((size_t)v * ms + i) * 2 + 1];
+            // base pixel of sample j, exactly as the kernels compute it
+            auto cell = [&](int j, long long* ix, long long* iy) {
+                if (f64) {
+                    const double X0 = std::fma((double)i, vp.dXrd, vp.X00d);
+                    const double Y0 = std::fma((double)i, vp.dYrd, vp.Y00d);
+                    *ix = (long long)std::floor(std::fma((double)j, vp.dXsd, X0));
+                    *iy = (long long)std::floor(std::fma((double)j, vp.dYsd, Y0));
+                } else {
+                    *ix = (vp.X00 + (long long)i * vp.dXr + (long long)j * vp.dXs) >> 32;
+                    *iy = (vp.Y00 + (long long)i * vp.dYr + (long long)j * vp.dYs) >> 32;
+                }
+            };
+            auto valid = [&](int j, long long* iy) {
+                long long ix;
+                cell(j, &ix, iy);
+                return ix >= -1 && ix <= n - 1 && *iy >= -1 && *iy <= n - 1;
+            };
+            // the valid samples of a straight ray are one contiguous range of j
+            long long iy = 0;
+            int j1 = jhi;
+            while (j1 >= jlo && !valid(j1, &iy)) --j1;
+            if (j1 < jlo) continue;
+            const int first = (int)iy;
+            int j0 = jlo;
+            while (!valid(j0, &iy)) ++j0;
+            (*rows)[(size_t)v * ms + i] = make_int2(first, (int)iy);
+        }
+    }
+}
+
+// Ray windows of a chunk height: per (view, chunk) the first slot and the number of slots
+// spanning every ray with a valid sample in the chunk.  Returns the widest window.
+static int chunk_windows(const Geometry& g, const std::vector<int2>& rows, int Yc, int nchunks,
+                         std::vector<int2>* win) {
+    const int V = (int)g.views.size(), ms = g.max_slots, n = g.n;
+    if (win) win->assign((size_t)V * nchunks, make_int2(0, 0));
+    std::vector<int> lo(nchunks), hi(nchunks);
+    int widest = 0;
+    for (int v = 0; v < V; ++v) {
+        std::fill(lo.begin(), lo.end(), INT_MAX);
+        std::fill(hi.begin(), hi.end(), -1);
+        for (int i = 0; i < g.views[v].n_slots; ++i) {
+            const int2 r = rows[(size_t)v * ms + i];
+            if (r.x == INT_MIN) continue;
+            // rows run from n - 1 (chunk 0) down to -1; r.x >= r.y
+            const int k0 = (n - 1 - r.x) / Yc, k1 = (n - 1 - r.y) / Yc;
+            for (int k = k0; k <= k1; ++k) {
+                lo[k] = std::min(lo[k], i);
+                hi[k] = std::max(hi[k], i);
+            }
+        }
+        for (int k = 0; k < nchunks; ++k) {
+            if (hi[k] < 0) continue;
+            if (win) (*win)[(size_t)v * nchunks + k] = make_int2(lo[k], hi[k] - lo[k] + 1);
+            widest = std::max(widest, hi[k] - lo[k] + 1);
+        }
+    }
+    return widest;
+}
+
 static size_t walk_smem(int mode, bool f64, int threads, int Yc, int Ps, int nst, int n) {
     size_t s2 = f64 ? 16 : 8;
     const size_t nbuf = mode == kVjp ? 1 : 2;  // row buffers (see the kernel)
-    size_t b = nbuf * s2 * (size_t)(Yc + 1) * Ps * (mode == kJvp ? 2 : 1) + s2 * nst;
+    size_t b = nbuf * s2 * (size_t)(Yc + 1) * Ps * (mode == kJvp ? 2 : 1) + (mode == kVjp ? 0 : s2 * nst);
     if (mode == kVjp) b += s2 * (size_t)(Yc + 1) * (f64 ? 5 : 4) * nst + 2 * s2 * n + 2 * (size_t)(Yc + 1) * nst;
     b = (b + 7) / 8 * 8 + 8 * nbuf;  // chunk barriers
     (void)threads;
     return (b + 15) / 16 * 16;
 }
 
-WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget) {
+WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, const std::vector<int2>* rows) {
     WalkPlan pl;
     pl.threads = ((g.max_slots + 31) / 32) * 32;
     pl.Ps = smem_pitch(P, f64);
+    if (mode == kVjp && rows) {
+        // tallest chunk whose stencils (as wide as the widest ray window) fit the budget;
+        // the window widens with the chunk height, so the fit is monotone in Yc
+        auto fits = [&](int Yc, int* nst) {
+            const int nch = (g.n + 1 + Yc - 1) / Yc;
+            const int W = std::max(1, chunk_windows(g, *rows, Yc, nch, nullptr));
+            *nst = stencil_stride(W, f64);
+            return walk_smem(mode, f64, pl.threads, Yc, pl.Ps, *nst, g.n) <= budget;
+        };
+        int lo = 1, hi = g.n + 1, nst = 0;
+        while (lo < hi) {  // largest Yc in [1, n + 1] that fits (Yc = 1 if none does)
+            const int mid = (lo + hi + 1) / 2;
+            if (fits(mid, &nst)) lo = mid;
+            else hi = mid - 1;
+        }
+        fits(lo, &nst);
+        pl.Yc = lo;
+        pl.nchunks = (g.n + 1 + lo - 1) / lo;
+        pl.nst = nst;
+        pl.sb_cap = 0;
+        pl.smem = walk_smem(mode, f64, pl.threads, lo, pl.Ps, nst, g.n);
+        chunk_windows(g, *rows, lo, pl.nchunks, &pl.win);
+        return pl;
+    }
     pl.nst = mode == kVjp ? stencil_stride(pl.threads, f64) : pl.threads;
     int best = 1;
     for (int Yc = 1; Yc <= g.n + 1; ++Yc) {
