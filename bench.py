@@ -36,6 +36,25 @@ WORKLOAD_NAME = ("single-request LM: 128x128 grid, 9x9 rods r=5, 360 angles x 18
 METRIC = "recon/s"
 SUB = (16, 16)
 
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
+# (profiles/walk_kernels_single128.md), valid only for the kernel source it was taken on:
+# reported while csrc/walk.cu and csrc/kernels.cuh hash to these values, null otherwise.
+TRAFFIC = {"walk_vjp": {"bytes": 3130880 + 33636608,
+                        "walk.cu": "96dd6a17e5e06cd11277ccb2a18258f0270563cf1d4ffff882499d67ff1f6c36",
+                        "kernels.cuh": "0aae84d337a6f8619a196917ff87b520935a95ab4a442496d32ac3d8b45fe936"}}
+
+
+def captured_traffic(kernel: str):
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    for f in ("walk.cu", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2604_26745_gb300", "csrc", f), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != t[f]:
+                return None
+    return t["bytes"]
+
 
 def _args():
     ap = argparse.ArgumentParser()
@@ -337,7 +356,8 @@ def main():
                                                  key=lambda k: kern[k]["total_ms"])
     achieved = kern[dk]["achieved_gbs"]
     roof = {"kernel": dk, "bound": "smem", "achieved": round(achieved, 1), "peak": round(smem_peak, 1),
-            "unit": "GB/s", "frac": round(achieved / smem_peak, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / smem_peak, 4), "traffic": captured_traffic(dk),
+            "traffic_unit": "DRAM bytes read + written per launch (ncu)",
             "peak_source": "derived: 152 SMs x 128 B/clk shared-memory bandwidth x median sampled SM clock",
             "algorithmic_bytes_per_launch": bytes_per_sample[dk] * counts["distinct_ray_samples"],
             "units_per_launch": counts["distinct_ray_samples"],
