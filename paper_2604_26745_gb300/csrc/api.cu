@@ -243,6 +243,15 @@ struct Slot {
 struct pget_ctx {
     Profiler prof;
     std::vector<std::unique_ptr<pget::Slot>> slots;
+    // idle serving workspaces (with their captured graphs), reused by geometry key so that
+    // a stream of mixed sizes does not allocate and free device memory per request
+    struct Idle {
+        std::string key;
+        std::unique_ptr<pget::Workspace> ws;
+        uint64_t last_use = 0;
+    };
+    std::vector<Idle> pool;
+    uint64_t use_clock = 0;
     uint64_t next_ticket = 1;
     int device = 0;
     size_t budget = 0;
@@ -286,6 +295,7 @@ pget_status resolve(const pget_geometry* gin, int prec, Geometry* g, std::string
 }
 
 size_t serving_bytes(const pget_ctx* ctx);
+bool evict_idle(pget_ctx* ctx);
 
 // Allocate and initialise a workspace for a resolved geometry (no budget check).
 pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, std::unique_ptr<Workspace>* out) {
@@ -418,6 +428,9 @@ pget_status get_workspace(pget_ctx* ctx, const pget_geometry* gin, int prec, Wor
         *out = ctx->ws.get();
         return PGET_OK;
     }
+    if (ctx->budget)  // idle serving workspaces give way to the direct path
+        while (need + serving_bytes(ctx) > ctx->budget && evict_idle(ctx)) {
+        }
     if (ctx->budget && need + serving_bytes(ctx) > ctx->budget)
         return fail(PGET_ENOMEM, "workspace needs %zu bytes, budget %zu (serving slots hold %zu)", need,
                     ctx->budget, serving_bytes(ctx));
@@ -807,7 +820,25 @@ size_t serving_bytes(const pget_ctx* ctx) {
     size_t b = 0;
     for (auto& sl : ctx->slots)
         if (sl->ws) b += sl->ws->bytes;
+    for (auto& e : ctx->pool) b += e.ws->bytes;
     return b;
+}
+
+// Free the least recently used idle workspace; false when the pool is empty.
+bool evict_idle(pget_ctx* ctx) {
+    if (ctx->pool.empty()) return false;
+    size_t k = 0;
+    for (size_t i = 1; i < ctx->pool.size(); ++i)
+        if (ctx->pool[i].last_use < ctx->pool[k].last_use) k = i;
+    ctx->pool.erase(ctx->pool.begin() + k);
+    return true;
+}
+
+// Memory the serving path may hold without a budget: a quarter of the device.
+size_t default_serving_cap() {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || tot == 0) return (size_t)8 << 30;
+    return tot / 4;
 }
 
 // Initial guess on the device without host synchronisation (serving path): lambda is
@@ -987,6 +1018,7 @@ pget_status pget_destroy(pget_ctx* ctx) {
         DeviceGuard dg(ctx->device);
         cudaDeviceSynchronize();
         ctx->slots.clear();
+        ctx->pool.clear();
         ctx->ws.reset();
         if (ctx->scratch) cudaFree(ctx->scratch);
     }
@@ -1203,21 +1235,27 @@ pget_status pget_submit(pget_ctx* ctx, const pget_geometry* g, const pget_lm_par
             }
     if (!sl) return fail(PGET_EAGAIN, "all %zu serving slots are busy", ctx->slots.size());
     if (!(sl->ws && sl->ws_key == key)) {
-        sl->ws.reset();
+        // park the slot's workspace (idle: its last request was collected) and take an
+        // idle one of this geometry if there is one
+        if (sl->ws) ctx->pool.push_back({sl->ws_key, std::move(sl->ws), ++ctx->use_clock});
         sl->ws_key.clear();
-        size_t held = serving_bytes(ctx) + (ctx->ws ? ctx->ws->bytes : 0);
-        if (ctx->budget && held + need > ctx->budget) {
-            // release workspaces cached by other free slots, then re-check
-            for (auto& c : ctx->slots)
-                if (c->state == Slot::kFree && c->ws) {
-                    c->ws.reset();
-                    c->ws_key.clear();
-                }
-            held = serving_bytes(ctx) + (ctx->ws ? ctx->ws->bytes : 0);
-            if (held + need > ctx->budget)
-                return fail(PGET_EAGAIN, "device memory budget in use (%zu of %zu bytes held, %zu needed)", held,
-                            ctx->budget, need);
+        for (size_t i = 0; i < ctx->pool.size(); ++i)
+            if (ctx->pool[i].key == key) {
+                sl->ws = std::move(ctx->pool[i].ws);
+                sl->ws_key = key;
+                ctx->pool.erase(ctx->pool.begin() + i);
+                break;
+            }
+    }
+    if (!sl->ws) {
+        // a new workspace: make room by freeing idle ones, least recently used first
+        auto held = [&] { return serving_bytes(ctx) + (ctx->ws ? ctx->ws->bytes : 0); };
+        const size_t cap = ctx->budget ? ctx->budget : default_serving_cap();
+        while (held() + need > cap && evict_idle(ctx)) {
         }
+        if (ctx->budget && held() + need > ctx->budget)
+            return fail(PGET_EAGAIN, "device memory budget in use (%zu of %zu bytes held, %zu needed)", held(),
+                        ctx->budget, need);
         std::unique_ptr<Workspace> w;
         s = make_workspace(ctx, std::move(geo), p->precision, groups, &w);
         if (s != PGET_OK) return s;
