@@ -140,6 +140,10 @@ struct Workspace {
     void* d_src_w = nullptr;    // per-slot sub-ray weights in the element type of the path
     int2* d_clip = nullptr;
     int2* d_win = nullptr;       // adjoint ray windows [view][chunk]
+    // test aids of the failure path (0 in normal use): extra expected bytes on the first
+    // chunk copy of every walk, and the chunk-copy wait limit
+    int tx_extra = 0;
+    long long wait_ns = 0;
     // adjoint view groups: CTA g sums views group_view[group_off[g] .. group_off[g+1]),
     // all of one canonical orientation (gtrans[g]), into partial image g
     int n_groups = 0;
@@ -410,6 +414,8 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     CK(cudaMallocHost(&w->host_err, sizeof(int) * 4));
     CK(cudaEventCreate(&w->t0));
     CK(cudaEventCreate(&w->t1));
+    if (const char* v = getenv("PGET_TEST_TX_EXTRA")) w->tx_extra = std::max(0, atoi(v)) / 16 * 16;
+    if (const char* v = getenv("PGET_TEST_WAIT_NS")) w->wait_ns = std::max(0LL, atoll(v));
     w->prof = &ctx->prof;
     *out = std::move(w);
     return PGET_OK;
@@ -466,6 +472,8 @@ WalkArgs base_args(const Workspace& w) {
     a.src_w = w.d_src_w;
     a.clip = w.d_clip;
     a.err = w.err;
+    a.tx_extra = w.tx_extra;
+    a.wait_ns = w.wait_ns;
     return a;
 }
 

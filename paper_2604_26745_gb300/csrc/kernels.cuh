@@ -149,6 +149,9 @@ struct WalkArgs {
     const int* group_off;      // VJP: CTA g handles views group_view[group_off[g] .. group_off[g+1])
     const int* group_view;     //      (null: CTA g handles view g)
     const int* stop;           // optional: skip the launch when *stop != 0
+    long long wait_ns;         // limit of one chunk-copy wait (0: 1 s)
+    int tx_extra;              // test aid: bytes added to the first chunk's expected copy
+                               // size, so that its wait runs out (0 in normal use)
     int* err;                  // error flags (bit 1: adjoint stencil bound, bit 2: chunk copy wait timed out)
 };
 

@@ -76,17 +76,20 @@ __device__ __forceinline__ bool mb_try_wait(unsigned long long* mb, unsigned par
         : "memory");
     return ok != 0;
 }
-// Wait for a phase of a chunk barrier.  Bounded: after ~4M polls (far beyond any copy
-// time) it sets error bit 2 and returns, so a lost copy never hangs the GPU; every
-// thread still reaches every barrier of the kernel.
-__device__ __forceinline__ void mb_wait(unsigned long long* mb, unsigned parity, int* err) {
-    unsigned it = 0;
-    while (!mb_try_wait(mb, parity)) {
-        if (++it > (1u << 22)) {
-            atomicOr(err, 4);
-            break;
-        }
-    }
+// Wait for a phase of a chunk barrier, for at most limit_ns of device time (globaltimer).
+// Returns false when the limit ran out: the caller records the error and stops issuing
+// copies, so a lost copy never hangs the GPU.
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mb_wait(unsigned long long* mb, unsigned parity, long long limit_ns) {
+    if (mb_try_wait(mb, parity)) return true;
+    const unsigned long long t0 = gtimer_ns();
+    while (!mb_try_wait(mb, parity))
+        if (gtimer_ns() - t0 > (unsigned long long)limit_ns) return false;
+    return true;
 }
 
 // Copy canonical rows [row_lo, row_lo + nrows) of a padded layout into a shared-memory
@@ -165,12 +168,17 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     }
     off = (off + 7) / 8 * 8;
     unsigned long long* mb = (unsigned long long*)(sm + off);  // one barrier per row buffer
+    int* s_abort = (int*)(mb + NB);  // set when a copy wait ran out: no further copies
     if (tid == 0) {
         for (int b = 0; b < NB; ++b) mb_init(&mb[b], 1);
         mb_init_fence();
+        *s_abort = 0;
     }
     __syncthreads();
-    unsigned phase = 0;  // bit b: parity of the next completed phase of buffer b
+    unsigned phase = 0;    // bit b: parity of the next completed phase of buffer b
+    unsigned pend = 0;     // bit b: a copy into buffer b was issued and not yet waited for
+    bool aborted = false;  // uniform copy of *s_abort, refreshed after barriers
+    const long long wait_ns = A.wait_ns > 0 ? A.wait_ns : 1000000000LL;
 
     // the views of this CTA: one view, or (VJP) a group of views sharing the canonical
     // orientation whose adjoint images are summed into the group's partial image
@@ -227,7 +235,8 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         chunk_rows(n, Yc, ck, &rh, &rl, &nr);
         if (tid == 0) {
             proxy_fence();
-            mb_expect_tx(&mb[b], (unsigned)(nr * P * sizeof(T2)) * (MODE == kJvp ? 2u : 1u));
+            mb_expect_tx(&mb[b], (unsigned)(nr * P * sizeof(T2)) * (MODE == kJvp ? 2u : 1u) +
+                                     (ck == 0 ? (unsigned)A.tx_extra : 0u));
         }
         __syncwarp();
         T2* dst = (T2*)((unsigned char*)cu0 + (size_t)b * rbytes * (MODE == kJvp ? 2 : 1));
@@ -235,14 +244,20 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         if constexpr (MODE == kJvp)
             issue_rows((T2*)((unsigned char*)dst + rbytes), pg, P, Ps, n, vp.flipped, rl, nr, &mb[b], tid);
     };
-    if (TMA && tid < 32) issue(0, 0);  // the buffers are free: the previous view ended with a barrier
+    if (TMA && !aborted) {  // the buffers are free: the previous view ended with a barrier
+        if (tid < 32) issue(0, 0);
+        pend |= 1u;
+    }
 
     for (int ck = 0; ck < A.nchunks; ++ck) {
         int row_hi, row_lo, nrows;
         chunk_rows(n, Yc, ck, &row_hi, &row_lo, &nrows);
         const int b = NB == 2 ? (ck & 1) : 0;
         if constexpr (NB == 2)  // buffer b ^ 1 was released by the barrier ending chunk ck - 1
-            if (tid < 32 && ck + 1 < A.nchunks) issue(ck + 1, b ^ 1);
+            if (!aborted && ck + 1 < A.nchunks) {
+                if (tid < 32) issue(ck + 1, b ^ 1);
+                pend |= 1u << (b ^ 1);
+            }
         // adjoint: stencil columns cover the window of rays with samples in this chunk
         int wa = 0, wn = 0, ts = 0;
         bool in_win = false;
@@ -258,8 +273,14 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
             cur_row = INT_MIN;  // the stencil rows of this chunk start empty
         }
         if constexpr (TMA) {
-            mb_wait(&mb[b], (phase >> b) & 1u, A.err);
-            phase ^= 1u << b;
+            if (pend & (1u << b)) {  // after an abort the buffer holds stale rows: results are void
+                if (!mb_wait(&mb[b], (phase >> b) & 1u, wait_ns)) {
+                    atomicOr(A.err, 4);
+                    *s_abort = 1;
+                }
+                phase ^= 1u << b;
+                pend &= ~(1u << b);
+            }
         } else {
             stage_rows(cu0, ug, P, Ps, n, vp.flipped, row_lo, nrows);
             __syncthreads();
@@ -332,6 +353,7 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
             }
         }
         __syncthreads();  // every walk of chunk ck is done: its row buffer is free
+        if constexpr (TMA) aborted = *s_abort != 0;
         if constexpr (MODE == kVjp) {
             const int r0 = max(row_lo, 0), r1 = min(row_hi + 1, n - 1);
             const int nout = (r1 - r0 + 1) * n;
@@ -481,7 +503,7 @@ static size_t walk_smem(int mode, bool f64, int threads, int Yc, int Ps, int nst
     const size_t nbuf = mode == kVjp ? 1 : 2;  // row buffers (see the kernel)
     size_t b = nbuf * s2 * (size_t)(Yc + 1) * Ps * (mode == kJvp ? 2 : 1) + (mode == kVjp ? 0 : s2 * nst);
     if (mode == kVjp) b += s2 * (size_t)(Yc + 1) * (f64 ? 5 : 4) * nst + 2 * s2 * n + 2 * (size_t)(Yc + 1) * nst;
-    b = (b + 7) / 8 * 8 + 8 * nbuf;  // chunk barriers
+    b = (b + 7) / 8 * 8 + 8 * nbuf + 8;  // chunk barriers and the abort flag
     (void)threads;
     return (b + 15) / 16 * 16;
 }
