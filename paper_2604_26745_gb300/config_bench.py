@@ -1,0 +1,176 @@
+"""Throughput and precision of the hot path on the other standard workloads (the
+single-request LM is bench.py, the mixed request stream is serving_bench.py).
+
+  python -m paper_2604_26745_gb300.config_bench --config plain64|diff256|stress512 [--count K]
+
+plain64    plain LM in FP64: 64 x 64, 9 x 9 rods r = 3, 90 angles x 91 detectors x 1 ray,
+           Poisson 1e4, 10 LM iterations, CG <= 50 (tol 1e-10); K reconstructions
+           (phantom seeds 1000+i, noise 2000+i): recon/s and p50/p99 latency.
+diff256    differentiation: K pairs (lambda, mu) on 256 x 256 (17 x 17 rods r = 5),
+           360 x 182 x 5: gradient of 1/2 |A(lambda, mu) - y|^2 through the autograd
+           wrapper (pairs/s, FP32-Kahan and FP64) and the memory the recompute saves.
+stress512  precision stress: K reconstructions on 512 x 512 (17 x 17 rods r = 10, rod
+           mu ~ U(0.05, 0.12)), 720 x 182 x 9, Poisson 1e6, 10 LM iterations, CG <= 30,
+           in FP32, FP32-Kahan and FP64: recon/s per precision and, per result, the
+           relative L2 distance of the FP32 and FP32-Kahan sinogram, gradient and final
+           reconstruction from the FP64 GPU path on the same input.
+
+Prints one JSON line per configuration.  Timing: CUDA events on the current stream around
+each reconstruction (after one untimed warm-up), data resident in HBM.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import statistics
+
+import numpy as np
+import torch
+
+from . import build, pget as P, synth
+
+
+def _rel(a, b) -> float:
+    a = a.double().ravel()
+    b = b.double().ravel()
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
+def _timed_solve(ctx, g, p, y):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    lam, mu = P.pget_initial_guess(ctx, g, p, y)
+    rep = P.pget_lm_solve(ctx, g, p, y, lam, mu)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), lam, mu, rep
+
+
+def plain64(k: int) -> dict:
+    g = P.geometry(64, 90, 91, n_sub=1)
+    p = P.default_params(max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10, precision=P.PGET_F64)
+    ms = []
+    with P.Context(0) as ctx:
+        ys = []
+        for i in range(k):
+            ph = synth.lattice_phantom(64, 9, radius=3.0, seed=1000 + i)
+            yc = P.pget_forward(ctx, g, P.PGET_F64, torch.tensor(ph.lam, device="cuda"),
+                                torch.tensor(ph.mu, device="cuda"))
+            ys.append(torch.tensor(synth.poisson_noise(yc.cpu().numpy(), 1e4, 2000 + i), device="cuda"))
+        _timed_solve(ctx, g, p, ys[0])  # warm-up: workspace and captured graph
+        for y in ys:
+            ms.append(_timed_solve(ctx, g, p, y)[0])
+    return {"config": "plain LM FP64: 64x64, 9x9 rods r=3, 90 x 91 x 1, Poisson 1e4, 10 LM x CG<=50",
+            "reconstructions": k, "recon_per_s": round(1e3 * k / sum(ms), 2),
+            "latency_ms": {"p50": round(statistics.median(ms), 2), "p99": round(_pct(ms, 0.99), 2)}}
+
+
+def diff256(k: int) -> dict:
+    from . import autograd as AG
+    n, na, nd, S = 256, 360, 182, 5
+    g = P.geometry(n, na, nd, n_sub=S)
+    pairs = [synth.lattice_phantom(n, 17, radius=5.0, seed=1200 + i) for i in range(k)]
+    out = {"config": "differentiation: 256x256, 17x17 rods r=5, 360 x 182 x 5", "pairs": k}
+    for name, dt in (("f32_kahan", torch.float32), ("f64", torch.float64)):
+        L = torch.tensor(np.stack([p.lam for p in pairs]), dtype=dt, device="cuda", requires_grad=True)
+        M = torch.tensor(np.stack([p.mu for p in pairs]), dtype=dt, device="cuda", requires_grad=True)
+        y = torch.zeros((k, na, nd), dtype=dt, device="cuda")
+        AG.data_loss(L[:1], M[:1], y[:1], g).backward()  # warm-up
+        L.grad = None
+        M.grad = None
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        AG.data_loss(L, M, y, g).backward()
+        b.record()
+        torch.cuda.synchronize()
+        out[f"{name}_pairs_per_s"] = round(1e3 * k / a.elapsed_time(b), 2)
+    # what recomputing the attenuation prefixes saves: storing exp(-E_j) and the prefix
+    # sum per in-grid sample (8 bytes in FP32) for every ray of one pair
+    samples = _in_grid_samples(n, na, nd, S)
+    out["recompute_saves_bytes_per_pair"] = 8 * samples
+    return out
+
+
+def _in_grid_samples(n, na, nd, S) -> int:
+    """In-grid samples of all sub-rays of one pass (host count from the geometry)."""
+    nbk = 2 if nd == 182 else 1
+    nb = nd // nbk
+    r = n / math.sqrt(2.0)
+    p = 2 * r / nb
+    T = math.ceil(2 * r)
+    c = 0.5 * (n - 1)
+    t = -r + (np.arange(T) + 0.5)
+    u = np.array([(k - (S - 1) / 2) * 2 * p / (S + 1) for k in range(S)])
+    tot = 0
+    for a in range(na):
+        for b in range(nbk):
+            psi = 2 * math.pi * a / na + b * math.pi
+            ct, st = math.cos(psi), math.sin(psi)
+            s = (((np.arange(nb) - 0.5 * (nb - 1) + 0.5 * b) * p)[:, None] + u[None, :]).ravel()
+            fx = np.floor(-s[:, None] * st + t[None, :] * ct + c)
+            fy = np.floor(s[:, None] * ct + t[None, :] * st + c)
+            tot += int(((fx >= -1) & (fx <= n - 1) & (fy >= -1) & (fy <= n - 1)).sum())
+    return tot
+
+
+def stress512(k: int) -> dict:
+    n, na, nd, S = 512, 720, 182, 9
+    g = P.geometry(n, na, nd, n_sub=S)
+    precs = (("f32", P.PGET_F32), ("f32_kahan", P.PGET_F32_KAHAN), ("f64", P.PGET_F64))
+    res = {name: [] for name, _ in precs}
+    ms = {name: [] for name, _ in precs}
+    per = []
+    with P.Context(0) as ctx:
+        for i in range(k):
+            ph = synth.lattice_phantom(n, 17, radius=10.0, seed=1500 + i, mu_rod=(0.05, 0.12))
+            lam64 = torch.tensor(ph.lam, device="cuda")
+            mu64 = torch.tensor(ph.mu, device="cuda")
+            yc = P.pget_forward(ctx, g, P.PGET_F64, lam64, mu64)
+            y64 = torch.tensor(synth.poisson_noise(yc.cpu().numpy(), 1e6, 2500 + i), device="cuda")
+            r64 = (yc - y64).contiguous()
+            ops = {}
+            for name, prec in precs:
+                dt = P.dtype_of(prec)
+                lam, mu, r = lam64.to(dt), mu64.to(dt), r64.to(dt)
+                sino = P.pget_forward(ctx, g, prec, lam, mu)
+                gl, gm = P.pget_vjp(ctx, g, prec, lam, mu, r)
+                ops[name] = (sino, torch.cat([gl.ravel(), gm.ravel()]))
+                p = P.default_params(max_iters=10, cg_max_iters=30, cg_rel_tol=1e-6 if dt == torch.float32 else 1e-10,
+                                     precision=prec)
+                y = y64.to(dt)
+                if i == 0:
+                    _timed_solve(ctx, g, p, y)  # warm-up per precision
+                t, l_, m_, rep = _timed_solve(ctx, g, p, y)
+                ms[name].append(t)
+                res[name].append(torch.cat([l_.ravel(), m_.ravel()]))
+            item = {"seed": 1500 + i}
+            for name in ("f32", "f32_kahan"):
+                item[name] = {"sinogram": _rel(ops[name][0], ops["f64"][0]),
+                              "gradient": _rel(ops[name][1], ops["f64"][1]),
+                              "reconstruction": _rel(res[name][-1], res["f64"][-1])}
+            per.append(item)
+    return {"config": "precision stress: 512x512, 17x17 rods r=10, rod mu ~ U(0.05,0.12), 720 x 182 x 9, "
+                      "Poisson 1e6, 10 LM x CG<=30",
+            "reconstructions": k,
+            "recon_per_s": {name: round(1e3 * len(v) / sum(v), 3) for name, v in ms.items()},
+            "rel_l2_vs_f64_gpu": per}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", required=True, choices=["plain64", "diff256", "stress512"])
+    ap.add_argument("--count", type=int, default=0)
+    a = ap.parse_args()
+    build.build()
+    fn, k0 = {"plain64": (plain64, 16), "diff256": (diff256, 32), "stress512": (stress512, 4)}[a.config]
+    print(json.dumps(fn(a.count or k0)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
