@@ -113,6 +113,8 @@ def lib():
         L.og_geom_info.argtypes = [gp, C.POINTER(C.c_int32), dp, dp, C.POINTER(C.c_int32)]
         L.og_num_threads.restype = C.c_int
         L.og_set_vjp_chunks.argtypes = [C.c_int]
+        L.og_lm_trial.argtypes = [gp, C.POINTER(Params), dp, dp, dp, C.c_double, dp, C.POINTER(Trial)]
+        L.og_check_proposal.argtypes = [gp, C.POINTER(Params), dp, dp, dp, dp, dp, dp, C.POINTER(Check)]
         _lib = L
     return _lib
 
@@ -232,6 +234,42 @@ def report_dict(rep: Report) -> dict:
         "acc": list(rep.acc[:k]),
         "cg_iters": list(rep.cg_iters[:k]),
     }
+
+
+class Trial(C.Structure):
+    _fields_ = [("f", C.c_double), ("pred", C.c_double), ("ared", C.c_double), ("rho", C.c_double),
+                ("nu_next", C.c_double), ("nu0", C.c_double), ("accept", C.c_int32), ("cg_iters", C.c_int32)]
+
+
+class Check(C.Structure):
+    _fields_ = [("f", C.c_double), ("pred_step", C.c_double), ("pred_prop", C.c_double),
+                ("ared_prop", C.c_double), ("rho_prop", C.c_double), ("accept", C.c_int32), ("pad", C.c_int32)]
+
+
+def _fields(st) -> dict:
+    return {k: getattr(st, k) for k, _ in st._fields_ if k != "pad"}
+
+
+def lm_trial(g: Geom, pr: Params, y, lam, mu, nu=0.0):
+    """One LM trial at the feasible point (lam, mu) with damping nu (<= 0: nu_0 at that
+    point): returns the stacked step s_k = (s_lambda, s_mu) and the trial's scalars."""
+    y, lam, mu = map(_f64, (y, lam, mu))
+    s = np.zeros((2,) + lam.shape)
+    t = Trial()
+    if lib().og_lm_trial(C.byref(g), C.byref(pr), _p(y), _p(lam), _p(mu), float(nu), _p(s), C.byref(t)):
+        raise ValueError("invalid geometry")
+    return s, _fields(t)
+
+
+def check_proposal(g: Geom, pr: Params, y, lam, mu, s_step, prop_lam, prop_mu) -> dict:
+    """The safeguard of Alg. 2 for the proposal (prop_lam, prop_mu) at (lam, mu) with the
+    LM step s_step (stacked, as returned by lm_trial)."""
+    y, lam, mu, s_step, pl, pm = map(_f64, (y, lam, mu, s_step, prop_lam, prop_mu))
+    c = Check()
+    if lib().og_check_proposal(C.byref(g), C.byref(pr), _p(y), _p(lam), _p(mu), _p(s_step), _p(pl), _p(pm),
+                               C.byref(c)):
+        raise ValueError("invalid geometry")
+    return _fields(c)
 
 
 def initial_guess(g: Geom, y, mu_init=0.01, lambda_max=2.0, mu_max=0.2):

@@ -28,6 +28,10 @@
  *   og_lm        -- the trust-region LM iteration of Sec. 2.2: step from Eq. (9),
  *                   projection onto the box of Eq. (6), model m_k of Eq. (8), agreement
  *                   ratio rho of Eq. (12), acceptance rho > eta with eta in (0, 1/4).
+ *   og_lm_trial  -- one trial of that iteration at a given point and damping, returning
+ *                   the step s_k without moving the iterate (the LMA(u_k) of Alg. 2).
+ *   og_check_proposal -- the safeguard of Prop. conv_check / Alg. 2 (Sec. 3.1): accept a
+ *                   proposal u~ iff rho(s~) > eta and m_k(s~) <= m_k(s_k).
  *
  * Pins: every function above is checked by tests/test_oracle_*.py against closed
  * forms, hand-computed values, finite differences, the adjoint identity, dense
@@ -645,6 +649,156 @@ int og_lm(const og_geom* gin, const og_params* pr, const double* y, double* lam,
     free(ut);
     free(tmp);
     free(Hs);
+    return 0;
+}
+
+/* ------------------------------------------------- safeguarded acceleration */
+
+typedef struct {
+    double f, pred, ared, rho, nu_next, nu0;
+    int32_t accept, cg_iters;
+} og_trial;
+
+typedef struct {
+    double f, pred_step, pred_prop, ared_prop, rho_prop;
+    int32_t accept, pad;
+} og_check;
+
+/* m_k(0) - m_k(s) at u for the stacked step s (Eq. (8) with the prior's frozen-weight
+ * Hessian): -<s, grad> - |J s|^2 / 2 - s^T H s / 2. */
+static double og_model_decrease(const og_geom* g, const og_params* pr, const double* lam,
+                                const double* mu, const double* grad, const double* Wl,
+                                const double* Wm, const double* s, double* Js, double* Hs) {
+    int n = g->n, np = n * n, m = g->n_angles * g->n_det;
+    og_jvp(g, lam, mu, s, s + np, Js);
+    double sHs = 0.0;
+    og_reg_apply(n, pr->alpha_lambda, Wl, s, Hs);
+    sHs += og_dot(np, s, Hs);
+    og_reg_apply(n, pr->alpha_mu, Wm, s + np, Hs);
+    sHs += og_dot(np, s + np, Hs);
+    return -og_dot(2 * np, s, grad) - 0.5 * og_dot(m, Js, Js) - 0.5 * sHs;
+}
+
+/* One trust-region trial of the LM iteration at the feasible point u = (lam, mu) with
+ * damping nu (nu <= 0: nu_0 = nu0_scale |J g|^2 / |g|^2 at u, as at the start of og_lm):
+ * the step s = P_box(u + delta) - u of Eq. (9), its model decrease, the actual decrease,
+ * rho of Eq. (12), the acceptance rho > eta and the next damping (before clamping).
+ * u is not changed: this is the "s_k = LMA(u_k)" of Alg. 2, whose caller decides. */
+int og_lm_trial(const og_geom* gin, const og_params* pr, const double* y, const double* lam,
+                const double* mu, double nu, double* s, og_trial* out) {
+    og_ctx o;
+    if (og_setup(gin, &o)) return 1;
+    const og_geom* g = &o.g;
+    int n = g->n, np = n * n, m = g->n_angles * g->n_det;
+    memset(out, 0, sizeof *out);
+    double* r = malloc(sizeof(double) * m);
+    double* rt = malloc(sizeof(double) * m);
+    double* Js = malloc(sizeof(double) * m);
+    double* Wl = malloc(sizeof(double) * np);
+    double* Wm = malloc(sizeof(double) * np);
+    double* grad = malloc(sizeof(double) * 2 * np);
+    double* rhs = malloc(sizeof(double) * 2 * np);
+    double* delta = malloc(sizeof(double) * 2 * np);
+    double* ut = malloc(sizeof(double) * 2 * np);
+    double* tmp = malloc(sizeof(double) * np);
+    double f = og_objective(g, pr, lam, mu, y, r);
+    og_reg_weights(n, pr->tv_eps, lam, Wl);
+    og_reg_weights(n, pr->tv_eps, mu, Wm);
+    og_gradient(g, pr, lam, mu, r, Wl, Wm, grad, tmp);
+    if (!(nu > 0.0)) {
+        double gg = og_dot(2 * np, grad, grad);
+        nu = 1.0;
+        if (gg > 0.0) {
+            og_jvp(g, lam, mu, grad, grad + np, Js);
+            nu = pr->nu0_scale * og_dot(m, Js, Js) / gg;
+        }
+        if (!(nu > 0.0)) nu = 1.0;
+        out->nu0 = nu;
+    }
+    for (int i = 0; i < 2 * np; ++i) rhs[i] = -grad[i];
+    out->cg_iters = og_cg(g, pr, lam, mu, Wl, Wm, nu, rhs, delta);
+    for (int i = 0; i < np; ++i) {
+        ut[i] = og_clamp(lam[i] + delta[i], 0.0, pr->lambda_max);
+        ut[np + i] = og_clamp(mu[i] + delta[np + i], 0.0, pr->mu_max);
+        s[i] = ut[i] - lam[i];
+        s[np + i] = ut[np + i] - mu[i];
+    }
+    double pred = og_model_decrease(g, pr, lam, mu, grad, Wl, Wm, s, Js, tmp);
+    double ft = og_objective(g, pr, ut, ut + np, y, rt);
+    double ared = f - ft;
+    double rho = (pred > 0.0 && isfinite(ft)) ? ared / pred : -INFINITY;
+    out->f = f;
+    out->pred = pred;
+    out->ared = ared;
+    out->rho = rho;
+    out->accept = rho > pr->eta;
+    out->nu_next = rho < pr->rho_lo ? nu * pr->nu_up : (rho > pr->rho_hi ? nu * pr->nu_down : nu);
+    free(r);
+    free(rt);
+    free(Js);
+    free(Wl);
+    free(Wm);
+    free(grad);
+    free(rhs);
+    free(delta);
+    free(ut);
+    free(tmp);
+    return 0;
+}
+
+/* The convergence check of Prop. conv_check / Alg. 2 for a proposal u~ = (pl, pm) made
+ * at the feasible point u with the LM step s_k: with s~ = P_box(u~) - u (the proposal
+ * projected onto the constraint box, as the LM step is),
+ *   accept u~ iff rho(s~) > eta and m_k(s~) <= m_k(s_k),
+ * m_k(s~) <= m_k(s_k) being m_k(0) - m_k(s~) >= m_k(0) - m_k(s_k); rho as in Eq. (12)
+ * (-inf when the model predicts no decrease). */
+int og_check_proposal(const og_geom* gin, const og_params* pr, const double* y, const double* lam,
+                      const double* mu, const double* s_step, const double* pl, const double* pm,
+                      og_check* out) {
+    og_ctx o;
+    if (og_setup(gin, &o)) return 1;
+    const og_geom* g = &o.g;
+    int n = g->n, np = n * n, m = g->n_angles * g->n_det;
+    memset(out, 0, sizeof *out);
+    double* r = malloc(sizeof(double) * m);
+    double* rt = malloc(sizeof(double) * m);
+    double* Js = malloc(sizeof(double) * m);
+    double* Wl = malloc(sizeof(double) * np);
+    double* Wm = malloc(sizeof(double) * np);
+    double* grad = malloc(sizeof(double) * 2 * np);
+    double* ut = malloc(sizeof(double) * 2 * np);
+    double* sp = malloc(sizeof(double) * 2 * np);
+    double* tmp = malloc(sizeof(double) * np);
+    double f = og_objective(g, pr, lam, mu, y, r);
+    og_reg_weights(n, pr->tv_eps, lam, Wl);
+    og_reg_weights(n, pr->tv_eps, mu, Wm);
+    og_gradient(g, pr, lam, mu, r, Wl, Wm, grad, tmp);
+    for (int i = 0; i < np; ++i) {
+        ut[i] = og_clamp(pl[i], 0.0, pr->lambda_max);
+        ut[np + i] = og_clamp(pm[i], 0.0, pr->mu_max);
+        sp[i] = ut[i] - lam[i];
+        sp[np + i] = ut[np + i] - mu[i];
+    }
+    double pred_s = og_model_decrease(g, pr, lam, mu, grad, Wl, Wm, s_step, Js, tmp);
+    double pred_p = og_model_decrease(g, pr, lam, mu, grad, Wl, Wm, sp, Js, tmp);
+    double fp = og_objective(g, pr, ut, ut + np, y, rt);
+    double ared = f - fp;
+    double rho = (pred_p > 0.0 && isfinite(fp)) ? ared / pred_p : -INFINITY;
+    out->f = f;
+    out->pred_step = pred_s;
+    out->pred_prop = pred_p;
+    out->ared_prop = ared;
+    out->rho_prop = rho;
+    out->accept = rho > pr->eta && pred_p >= pred_s;
+    free(r);
+    free(rt);
+    free(Js);
+    free(Wl);
+    free(Wm);
+    free(grad);
+    free(ut);
+    free(sp);
+    free(tmp);
     return 0;
 }
 
