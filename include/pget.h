@@ -172,6 +172,56 @@ pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_p
                           const void* y, void* lam_io, void* mu_io, pget_lm_report* rep,
                           void* stream);
 
+/* ---- safeguarded acceleration (Prop. conv_check and Alg. 2, Sec. 3.1) ----
+ *
+ * Alg. 2 lets a learned operator G propose u~ = G(u_k, s_k) after every LM step s_k and
+ * keeps u~ only if it passes the paper's convergence check.  The two calls below are
+ * the library side of that loop; the proposal itself comes from the caller (any model). */
+
+/* Scalars of one trust-region trial (host memory). */
+typedef struct {
+    double f;        /* f(u) = 1/2 |A(u) - y|^2 + R(u)                                 */
+    double pred;     /* m_k(0) - m_k(s_k), Eq. (8)                                        */
+    double ared;     /* f(u) - f(u + s_k)                                                  */
+    double rho;      /* Eq. (12); -inf when pred <= 0 or f(u + s_k) is not finite          */
+    double nu_next;  /* nu after the schedule (x nu_up if rho < rho_lo, x nu_down if
+                        rho > rho_hi), not clamped: the caller clamps with its own nu_0   */
+    double nu0;      /* the damping used when nu <= 0 was passed, else 0                  */
+    int32_t accept;  /* rho > eta                                                          */
+    int32_t cg_iters;
+} pget_trial_report;
+
+/* One trust-region trial of the LM iteration at the feasible point u = (lam, mu) with
+ * damping nu (nu <= 0: nu_0 = nu0_scale |J g|^2 / |g|^2 at u, as a solve starts): CG on
+ * Eq. (9), s_k = P_box(u + delta) - u, model and actual decrease, rho, acceptance.  u is
+ * not changed (this is the s_k = LMA(u_k) of Alg. 2).  s_out: [2][n][n] device, the step.
+ * rep: host.  Synchronises the stream. */
+pget_status pget_lm_trial(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
+                          const void* y, const void* lam, const void* mu, double nu,
+                          void* s_out, pget_trial_report* rep, void* stream);
+
+/* Result of the convergence check for one proposal (host memory). */
+typedef struct {
+    double f;          /* f(u)                                                */
+    double pred_step;  /* m_k(0) - m_k(s_k) of the LM step                    */
+    double pred_prop;  /* m_k(0) - m_k(s~) of the proposal's step             */
+    double ared_prop;  /* f(u) - f(u + s~)                                    */
+    double rho_prop;   /* rho(s~), -inf when pred_prop <= 0                   */
+    int32_t accept;    /* rho(s~) > eta and m_k(s~) <= m_k(s_k)               */
+    int32_t pad;
+} pget_check_report;
+
+/* The check of Prop. conv_check / Alg. 2 for the proposal u~ = (prop_lam, prop_mu) at the
+ * feasible point u with the LM step s_step ([2][n][n], as pget_lm_trial returns it):
+ * s~ = P_box(u~) - u (the proposal is projected onto the constraint box like the LM
+ * step), then accept iff rho(s~) > p->eta and m_k(s~) <= m_k(s_k).  The caller then sets
+ * u_{k+1} = P_box(u~) when accepted, else u + s_k if the trial accepted, else u.  All
+ * arrays device [n][n] (s_step [2][n][n]); rep: host.  Synchronises the stream. */
+pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
+                                const void* y, const void* lam, const void* mu,
+                                const void* s_step, const void* prop_lam, const void* prop_mu,
+                                pget_check_report* rep, void* stream);
+
 /* As pget_lm_solve with HOST buffers (pinned or pageable): copies y_host to the device,
  * computes the initial guess (mu_init 0.01) when init_guess != 0 (else takes
  * lam_host / mu_host as the initial guess), solves, and copies the result back. */

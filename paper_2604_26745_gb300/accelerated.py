@@ -1,0 +1,51 @@
+"""Accelerated iteration scheme with checks (Alg. 2, Sec. 3.1) on the library's LM.
+
+Every iteration computes the LM step s_k at u_k (pget_lm_trial), lets a proposal operator
+G suggest u~ = G(u_k, s_k), and keeps u~ only if it passes the convergence check of
+Prop. conv_check (pget_proposal_check): rho(s~) > eta and m_k(s~) <= m_k(s_k).
+Otherwise the plain LM outcome stands: u_k + s_k if the trial was accepted, else u_k.
+The damping follows the LM trial's own schedule (the paper leaves it open after an
+accepted proposal; the LM step's rho drives it here, clamped as in a plain solve).
+
+G is any callable or torch.nn.Module taking (u, s, k) with u, s stacked [2, n, n] CUDA
+tensors (lambda, mu) and k the iteration, returning a proposal of the same shape, or None
+to skip the check in that iteration.  No trained model ships with the library; the
+tests drive the scheme with synthetic proposals.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import pget as P
+
+
+def accelerated_solve(ctx: P.Context, g: P.pget_geometry, p: P.pget_lm_params, y: torch.Tensor,
+                      lam: torch.Tensor, mu: torch.Tensor, G=None, iters: int | None = None):
+    """Run Alg. 2 from (lam, mu) (projected onto the box first); returns (lam, mu, history)
+    with one dict per iteration (trial scalars, check scalars, which update was taken)."""
+    iters = p.max_iters if iters is None else iters
+    lam = lam.clamp(0.0, p.lambda_max).contiguous()
+    mu = mu.clamp(0.0, p.mu_max).contiguous()
+    nu, nu0 = 0.0, None
+    s = lam.new_empty((2,) + tuple(lam.shape))
+    history = []
+    for k in range(iters):
+        s, tr = P.pget_lm_trial(ctx, g, p, y, lam, mu, nu, s_out=s)
+        if nu0 is None:
+            nu0 = nu = tr["nu0"]
+        took, chk = ("step" if tr["accept"] else "none"), None
+        if G is not None:
+            prop = G(torch.stack([lam, mu]), s, k)
+            if prop is not None:
+                pl, pm = prop[0].contiguous(), prop[1].contiguous()
+                chk = P.pget_proposal_check(ctx, g, p, y, lam, mu, s, pl, pm)
+                if chk["accept"]:
+                    lam = pl.clamp(0.0, p.lambda_max).contiguous()
+                    mu = pm.clamp(0.0, p.mu_max).contiguous()
+                    took = "proposal"
+        if took == "step":
+            lam = (lam + s[0]).clamp(0.0, p.lambda_max).contiguous()
+            mu = (mu + s[1]).clamp(0.0, p.mu_max).contiguous()
+        nu = min(max(tr["nu_next"], p.nu_min * nu0), p.nu_max * nu0)
+        history.append({"k": k, "trial": tr, "check": chk, "took": took, "nu": nu})
+    return lam, mu, history

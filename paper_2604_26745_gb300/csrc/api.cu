@@ -1,6 +1,8 @@
 // api.cu -- the C ABI of libpget.so: context, workspace, and the drivers of the
 // forward / JVP / VJP operators, the CG solve of Eq. (9) and the LM iteration (Sec. 2.2).
+#include <algorithm>
 #include <cmath>
+#include <initializer_list>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -917,6 +919,167 @@ static pget_status cg_impl(Workspace& w, const pget_lm_params& p, const void* la
     return PGET_OK;
 }
 
+// FP64 block partials (kRedBlocks each) -> sums, finished on the host in a fixed order
+static pget_status host_sums(Workspace& w, std::initializer_list<const double*> parts, double* out,
+                             cudaStream_t st) {
+    std::vector<double> h(parts.size() * kRedBlocks);
+    size_t k = 0;
+    for (const double* p : parts)
+        CK(cudaMemcpyAsync(h.data() + kRedBlocks * k++, p, sizeof(double) * kRedBlocks, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t j = 0; j < parts.size(); ++j) {
+        double a = 0.0;
+        for (int b = 0; b < kRedBlocks; ++b) a += h[j * kRedBlocks + b];
+        out[j] = a;
+    }
+    return PGET_OK;
+}
+
+// Objective f(u) = 1/2 |A(u) - y|^2 + R_lambda + R_mu at the packed point pk (u planar in
+// uvec); leaves the residual A(u) - y in r and the ray totals in U.
+template <typename T>
+static pget_status objective_at(Workspace& w, const pget_lm_params& p, void* const pk[2], const void* uvec,
+                                void* U, void* r, double* f, cudaStream_t st) {
+    const T* u = (const T*)uvec;
+    CK(op_forward(w, pk, U, w.Jp, nullptr, st));
+    sub_dot<T>((const T*)w.Jp, (const T*)w.yb, (T*)r, w.M, w.dpart[0], nullptr, st);
+    reg_value<T>(u, w.g.n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st);
+    reg_value<T>(u + w.nn, w.g.n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st);
+    double v[3];
+    pget_status s = host_sums(w, {w.dpart[0], w.dpart[1], w.dpart[2]}, v, st);
+    if (s != PGET_OK) return s;
+    *f = 0.5 * v[0] + v[1] + v[2];
+    return PGET_OK;
+}
+
+// m_k(0) - m_k(s) at the packed iterate for the planar step s (gradient in w.gr, prior
+// weights in Wl, Wm): -<s, g> - |J s|^2 / 2 - s^T H s / 2 (Eq. (8)).
+template <typename T>
+static pget_status model_decrease(Workspace& w, const pget_lm_params& p, const void* s, double* pred,
+                                  cudaStream_t st) {
+    lm_model<T>((const T*)s, (const T*)w.gr, (const T*)w.Wl, (const T*)w.Wm, w.g.n, p.alpha_lambda, p.alpha_mu,
+                w.dpart[0], w.dpart[1], st);
+    pack_vec<T>(w, s, w.pk_p, nullptr, st);
+    CK(op_jvp(w, w.pk_u, w.pk_p, w.Jp, nullptr, st));
+    dot<T>((const T*)w.Jp, (const T*)w.Jp, w.M, w.dpart[2], nullptr, st);
+    double v[3];
+    pget_status e = host_sums(w, {w.dpart[0], w.dpart[1], w.dpart[2]}, v, st);
+    if (e != PGET_OK) return e;
+    *pred = -v[0] - 0.5 * v[2] - 0.5 * v[1];
+    return PGET_OK;
+}
+
+// Shared start of the trial and the check: y and u into the workspace, f(u), prior
+// weights and the gradient g = J^T r + alpha grad^T W grad u at u.
+template <typename T>
+static pget_status at_point(Workspace& w, const pget_lm_params& p, const void* y, const void* lam, const void* mu,
+                            double* f, cudaStream_t st) {
+    const size_t nn = w.nn, e = w.elt;
+    CK(cudaMemcpyAsync(w.yb, y, e * w.M, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(w.u, lam, e * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync((char*)w.u + e * nn, mu, e * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    pack_vec<T>(w, w.u, w.pk_u, nullptr, st);
+    pget_status s = objective_at<T>(w, p, w.pk_u, w.u, w.U, w.r, f, st);
+    if (s != PGET_OK) return s;
+    const T* u = (const T*)w.u;
+    reg_weights<T>(u, w.g.n, p.tv_eps, (T*)w.Wl, nullptr, st);
+    reg_weights<T>(u + nn, w.g.n, p.tv_eps, (T*)w.Wm, nullptr, st);
+    RedArgs<T> ga;
+    ga.out = (T*)w.gr;
+    ga.v = u;
+    ga.Wl = (const T*)w.Wl;
+    ga.Wm = (const T*)w.Wm;
+    ga.alpha_l = p.alpha_lambda;
+    ga.alpha_m = p.alpha_mu;
+    ga.nu = 0.0;
+    CK(op_vjp<T>(w, w.pk_u, w.U, w.r, ga, nullptr, st));
+    return PGET_OK;
+}
+
+// One trust-region trial at u with damping nu (Alg. 2: s_k = LMA(u_k)); u is not moved.
+template <typename T>
+static pget_status trial_impl(Workspace& w, const pget_lm_params& p, const void* y, const void* lam,
+                              const void* mu, double nu, void* s_out, pget_trial_report* rep, cudaStream_t st) {
+    const size_t nn = w.nn;
+    memset(rep, 0, sizeof *rep);
+    double f = 0.0;
+    pget_status s = at_point<T>(w, p, y, lam, mu, &f, st);
+    if (s != PGET_OK) return s;
+    if (!(nu > 0.0)) {  // nu_0 = nu0_scale |J g|^2 / |g|^2, as at the start of a solve
+        dot<T>((const T*)w.gr, (const T*)w.gr, 2 * nn, w.dpart[0], nullptr, st);
+        pack_vec<T>(w, w.gr, w.pk_p, nullptr, st);
+        CK(op_jvp(w, w.pk_u, w.pk_p, w.Jp, nullptr, st));
+        dot<T>((const T*)w.Jp, (const T*)w.Jp, w.M, w.dpart[1], nullptr, st);
+        double v[2];
+        s = host_sums(w, {w.dpart[0], w.dpart[1]}, v, st);
+        if (s != PGET_OK) return s;
+        nu = v[0] > 0.0 ? p.nu0_scale * v[1] / v[0] : 1.0;
+        if (!(nu > 0.0)) nu = 1.0;
+        rep->nu0 = nu;
+    }
+    s = run_cg<T>(w, w.gr, -1.0, nu, nullptr, p, st);
+    if (s != PGET_OK) return s;
+    lm_step<T>((const T*)w.u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, p.lambda_max, p.mu_max, st);
+    double pred = 0.0, ft = 0.0;
+    s = model_decrease<T>(w, p, w.s, &pred, st);
+    if (s != PGET_OK) return s;
+    pack_vec<T>(w, w.ut, w.pk_ut, nullptr, st);
+    s = objective_at<T>(w, p, w.pk_ut, w.ut, w.Ut, w.rt, &ft, st);
+    if (s != PGET_OK) return s;
+    CgState cg;
+    CK(cudaMemcpyAsync(&cg, &w.lm->cg, sizeof cg, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s_out, w.s, w.elt * 2 * nn, cudaMemcpyDeviceToDevice, st));
+    s = check_err(w, st);
+    if (s != PGET_OK) return s;
+    const double ared = f - ft;
+    const double rho = (pred > 0.0 && std::isfinite(ft)) ? ared / pred : -INFINITY;
+    rep->f = f;
+    rep->pred = pred;
+    rep->ared = ared;
+    rep->rho = rho;
+    rep->accept = rho > p.eta;
+    rep->nu_next = rho < p.rho_lo ? nu * p.nu_up : (rho > p.rho_hi ? nu * p.nu_down : nu);
+    rep->cg_iters = cg.iters;
+    return PGET_OK;
+}
+
+// The safeguard of Prop. conv_check / Alg. 2 for the proposal (pl, pm) at u with the LM
+// step s_step: s~ = P_box(u~) - u; accept iff rho(s~) > eta and m_k(s~) <= m_k(s_k).
+template <typename T>
+static pget_status check_impl(Workspace& w, const pget_lm_params& p, const void* y, const void* lam,
+                              const void* mu, const void* s_step, const void* pl, const void* pm,
+                              pget_check_report* rep, cudaStream_t st) {
+    const size_t nn = w.nn, e = w.elt;
+    memset(rep, 0, sizeof *rep);
+    double f = 0.0, pred_s = 0.0, pred_p = 0.0, fp = 0.0;
+    pget_status s = at_point<T>(w, p, y, lam, mu, &f, st);
+    if (s != PGET_OK) return s;
+    CK(cudaMemcpyAsync(w.s, s_step, e * 2 * nn, cudaMemcpyDeviceToDevice, st));
+    s = model_decrease<T>(w, p, w.s, &pred_s, st);
+    if (s != PGET_OK) return s;
+    CK(cudaMemcpyAsync(w.ut, pl, e * nn, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync((char*)w.ut + e * nn, pm, e * nn, cudaMemcpyDeviceToDevice, st));
+    clamp_box<T>((T*)w.ut, nn, p.lambda_max, p.mu_max, st);
+    sub_dot<T>((const T*)w.ut, (const T*)w.u, (T*)w.s, 2 * nn, w.dpart[3], nullptr, st);
+    s = model_decrease<T>(w, p, w.s, &pred_p, st);
+    if (s != PGET_OK) return s;
+    pack_vec<T>(w, w.ut, w.pk_ut, nullptr, st);
+    s = objective_at<T>(w, p, w.pk_ut, w.ut, w.Ut, w.rt, &fp, st);
+    if (s != PGET_OK) return s;
+    s = check_err(w, st);
+    if (s != PGET_OK) return s;
+    const double ared = f - fp;
+    const double rho = (pred_p > 0.0 && std::isfinite(fp)) ? ared / pred_p : -INFINITY;
+    rep->f = f;
+    rep->pred_step = pred_s;
+    rep->pred_prop = pred_p;
+    rep->ared_prop = ared;
+    rep->rho_prop = rho;
+    rep->accept = rho > p.eta && pred_p >= pred_s;
+    return PGET_OK;
+}
+
 template <typename T>
 static pget_status init_impl(Workspace& w, const pget_lm_params& p, double mu_init, const void* y, void* lam,
                              void* mu, cudaStream_t st) {
@@ -1151,6 +1314,39 @@ pget_status pget_initial_guess(pget_ctx* ctx, const pget_geometry* g, const pget
     cudaStream_t st = (cudaStream_t)stream;
     return w->f64 ? init_impl<double>(*w, *p, mu_init, y, lam, mu, st)
                   : init_impl<float>(*w, *p, mu_init, y, lam, mu, st);
+}
+
+pget_status pget_lm_trial(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
+                          const void* lam, const void* mu, double nu, void* s_out, pget_trial_report* rep,
+                          void* stream) {
+    if (!ctx || !y || !lam || !mu || !s_out || !rep) return fail(PGET_EINVAL, "null argument");
+    pget_status s = check_params(p);
+    if (s != PGET_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    s = get_workspace(ctx, g, p->precision, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    return w->f64 ? trial_impl<double>(*w, *p, y, lam, mu, nu, s_out, rep, st)
+                  : trial_impl<float>(*w, *p, y, lam, mu, nu, s_out, rep, st);
+}
+
+pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
+                                const void* lam, const void* mu, const void* s_step, const void* prop_lam,
+                                const void* prop_mu, pget_check_report* rep, void* stream) {
+    if (!ctx || !y || !lam || !mu || !s_step || !prop_lam || !prop_mu || !rep)
+        return fail(PGET_EINVAL, "null argument");
+    pget_status s = check_params(p);
+    if (s != PGET_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    s = get_workspace(ctx, g, p->precision, &w);
+    if (s != PGET_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    return w->f64 ? check_impl<double>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st)
+                  : check_impl<float>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st);
 }
 
 pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,

@@ -66,6 +66,20 @@ class pget_kernel_stat(C.Structure):
 
 # exported symbols and their argument types
 _vp = C.c_void_p
+class pget_trial_report(C.Structure):
+    _fields_ = [("f", C.c_double), ("pred", C.c_double), ("ared", C.c_double), ("rho", C.c_double),
+                ("nu_next", C.c_double), ("nu0", C.c_double), ("accept", C.c_int32), ("cg_iters", C.c_int32)]
+
+
+class pget_check_report(C.Structure):
+    _fields_ = [("f", C.c_double), ("pred_step", C.c_double), ("pred_prop", C.c_double),
+                ("ared_prop", C.c_double), ("rho_prop", C.c_double), ("accept", C.c_int32), ("pad", C.c_int32)]
+
+
+def _fields(st) -> dict:
+    return {k: getattr(st, k) for k, _ in st._fields_ if k != "pad"}
+
+
 _SIGS = {
     "pget_create": ([C.POINTER(_vp), C.c_int, C.c_size_t], C.c_int),
     "pget_destroy": ([_vp], C.c_int),
@@ -81,6 +95,10 @@ _SIGS = {
                             _vp, _vp, _vp, _vp], C.c_int),
     "pget_lm_solve": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp,
                        C.POINTER(pget_lm_report), _vp], C.c_int),
+    "pget_lm_trial": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp, C.c_double,
+                       _vp, C.POINTER(pget_trial_report), _vp], C.c_int),
+    "pget_proposal_check": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp, _vp,
+                             _vp, _vp, C.POINTER(pget_check_report), _vp], C.c_int),
     "pget_lm_solve_host": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
                             _vp, C.c_int32, C.POINTER(pget_lm_report), _vp], C.c_int),
     "pget_submit": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp,
@@ -243,6 +261,28 @@ def pget_initial_guess(ctx: Context, g: pget_geometry, p: pget_lm_params, y, mu_
     _check(load().pget_initial_guess(ctx.h, C.byref(g), C.byref(p), float(mu_init), _ptr(y),
                                      _ptr(lam), _ptr(mu), _stream(stream)), ctx.h)
     return lam, mu
+
+
+def pget_lm_trial(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam, mu, nu: float = 0.0, s_out=None,
+                  stream=None):
+    """One LM trial at (lam, mu) with damping nu (<= 0: nu_0 there); returns (s, report) with
+    s the stacked step [2, n, n] (a new tensor unless s_out is given).  u is not changed."""
+    if s_out is None:
+        s_out = lam.new_empty((2,) + tuple(lam.shape))
+    rep = pget_trial_report()
+    _check(load().pget_lm_trial(ctx.h, C.byref(g), C.byref(p), _ptr(y), _ptr(lam), _ptr(mu), float(nu),
+                                _ptr(s_out), C.byref(rep), _stream(stream)), ctx.h)
+    return s_out, _fields(rep)
+
+
+def pget_proposal_check(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam, mu, s_step, prop_lam,
+                        prop_mu, stream=None) -> dict:
+    """The convergence check of Alg. 2 for the proposal (prop_lam, prop_mu)."""
+    rep = pget_check_report()
+    _check(load().pget_proposal_check(ctx.h, C.byref(g), C.byref(p), _ptr(y), _ptr(lam), _ptr(mu),
+                                      _ptr(s_step), _ptr(prop_lam), _ptr(prop_mu), C.byref(rep),
+                                      _stream(stream)), ctx.h)
+    return _fields(rep)
 
 
 def pget_lm_solve(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam, mu, stream=None):

@@ -51,8 +51,9 @@ def test_struct_sizes_match_header(lib):
 #include <stdio.h>
 #include "pget.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\n", sizeof(pget_geometry), sizeof(pget_lm_params),
-         sizeof(pget_lm_report), sizeof(pget_kernel_stat));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(pget_geometry), sizeof(pget_lm_params),
+         sizeof(pget_lm_report), sizeof(pget_kernel_stat), sizeof(pget_trial_report),
+         sizeof(pget_check_report));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -63,7 +64,8 @@ int main(void) {
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     sizes = [int(x) for x in out]
     assert sizes == [ctypes.sizeof(pget.pget_geometry), ctypes.sizeof(pget.pget_lm_params),
-                     ctypes.sizeof(pget.pget_lm_report), ctypes.sizeof(pget.pget_kernel_stat)]
+                     ctypes.sizeof(pget.pget_lm_report), ctypes.sizeof(pget.pget_kernel_stat),
+                     ctypes.sizeof(pget.pget_trial_report), ctypes.sizeof(pget.pget_check_report)]
 
 
 def test_no_gpu_calls_fail_cleanly(lib):

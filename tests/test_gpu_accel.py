@@ -1,0 +1,111 @@
+"""Safeguarded acceleration (Prop. conv_check, Alg. 2) on the GPU against the oracle.
+
+- pget_lm_trial equals the oracle's trial (step, model and actual decrease, rho,
+  acceptance, nu_0) in FP64 to rounding and in FP32-Kahan to single precision (CG <= 6
+  steps: the stable regime where the iteration is a smooth function of its input);
+- pget_proposal_check equals the oracle's check on the same step for the truth, a random
+  perturbation, half the LM step and the LM step itself (same decisions, FP64 values to
+  rounding);
+- the driver of Alg. 2: without proposals it reproduces pget_lm_solve; proposing the
+  truth near the solution is accepted in the first iteration; random proposals are never
+  accepted and leave the plain LM iterates unchanged.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_26745_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N, NA, ND, S = 24, 30, 182, 3
+
+
+def _setup(O, P, torch, seed=21, noise=1e4):
+    ph = synth.lattice_phantom(N, 3, radius=2.0, seed=seed)
+    go = O.geom(N, NA, ND, n_sub=S)
+    y = O.forward(go, ph.lam, ph.mu)
+    if noise:
+        y = synth.poisson_noise(y, noise, seed + 1)
+    return ph, go, P.geometry(N, NA, ND, n_sub=S), y
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+@pytest.mark.parametrize("seed", [21, 25])  # first trial rejected (no model decrease) / accepted
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 2e-4)])
+def test_trial_matches_oracle(O, P, torch, prec, tol, seed):
+    ph, go, g, y = _setup(O, P, torch, seed=seed)
+    pr = O.default_params(cg_max_iters=6)
+    l0, m0 = O.initial_guess(go, y)
+    so, to = O.lm_trial(go, pr, y, l0, m0)
+    dt = P.dtype_of(prec)
+    p = P.default_params(cg_max_iters=6, cg_rel_tol=1e-10, precision=prec)
+    t = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+    with P.Context(0) as c:
+        s, tr = P.pget_lm_trial(c, g, p, t(y), t(l0), t(m0), 0.0)
+    assert _rel(s.double().cpu().numpy(), so) <= tol
+    for k in ("f", "pred", "ared", "rho", "nu0"):
+        if np.isfinite(to[k]):
+            assert abs(tr[k] - to[k]) <= tol * max(1.0, abs(to[k])), (k, tr[k], to[k])
+        else:
+            assert tr[k] == to[k], k
+    assert tr["accept"] == to["accept"] and tr["cg_iters"] == to["cg_iters"]
+
+
+def test_check_matches_oracle(O, P, torch):
+    ph, go, g, y = _setup(O, P, torch, seed=23, noise=None)
+    pr = O.default_params(cg_max_iters=6)
+    rs = np.random.default_rng(5)
+    lk = np.clip(ph.lam + 0.05 * rs.standard_normal(ph.lam.shape), 0, pr.lambda_max)
+    mk = np.clip(ph.mu + 0.005 * rs.standard_normal(ph.mu.shape), 0, pr.mu_max)
+    so, to = O.lm_trial(go, pr, y, lk, mk, 1e2)
+    props = {"truth": (ph.lam, ph.mu),
+             "noise": (lk + rs.uniform(-1, 1, lk.shape), mk + rs.uniform(-0.1, 0.1, mk.shape)),
+             "half": (lk + 0.5 * so[0], mk + 0.5 * so[1]),
+             "step": (lk + so[0], mk + so[1])}
+    p = P.default_params(cg_max_iters=6, cg_rel_tol=1e-10, precision=0)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    seen = set()
+    with P.Context(0) as c:
+        for name, (pl, pm) in props.items():
+            co = O.check_proposal(go, pr, y, lk, mk, so, pl, pm)
+            cg = P.pget_proposal_check(c, g, p, t(y), t(lk), t(mk), t(so), t(pl), t(pm))
+            assert cg["accept"] == co["accept"], name
+            for k in ("f", "pred_step", "pred_prop", "ared_prop"):
+                assert abs(cg[k] - co[k]) <= 1e-9 * max(1.0, abs(co[k])), (name, k)
+            if np.isfinite(co["rho_prop"]):
+                assert abs(cg["rho_prop"] - co["rho_prop"]) <= 1e-8, name
+            else:
+                assert cg["rho_prop"] == co["rho_prop"]
+            seen.add((name, bool(co["accept"])))
+    assert ("truth", True) in seen and ("noise", False) in seen
+
+
+def test_driver(O, P, torch):
+    from paper_2604_26745_gb300.accelerated import accelerated_solve
+    ph, go, g, y = _setup(O, P, torch, seed=25, noise=None)
+    p = P.default_params(max_iters=3, cg_max_iters=6, cg_rel_tol=1e-10, precision=0)
+    yd = torch.tensor(y, device="cuda")
+    with P.Context(0) as c:
+        l0, m0 = P.pget_initial_guess(c, g, p, yd)
+        # no proposals: the plain LM solve
+        la, ma, h = accelerated_solve(c, g, p, yd, l0.clone(), m0.clone(), None)
+        lb, mb = l0.clone(), m0.clone()
+        rep = P.pget_lm_solve(c, g, p, yd, lb, mb)
+        assert [x["took"] == "step" for x in h] == [bool(a) for a in rep["acc"]]
+        assert float((la - lb).abs().max()) <= 1e-12 and float((ma - mb).abs().max()) <= 1e-12
+        # the truth, proposed near the solution, is taken at once
+        truth = torch.stack([torch.tensor(ph.lam, device="cuda"), torch.tensor(ph.mu, device="cuda")])
+        gen1 = torch.Generator("cuda").manual_seed(1)
+        near = truth + 0.02 * torch.randn(truth.shape, generator=gen1, device="cuda", dtype=truth.dtype)
+        lt, mt, ht = accelerated_solve(c, g, p, yd, near[0].clone(), near[1].clone(),
+                                       lambda u, s, k: truth if k == 0 else None)
+        assert ht[0]["took"] == "proposal"
+        # random proposals are never taken and do not change the LM iterates
+        gen = torch.Generator("cuda").manual_seed(2)
+        junk = lambda u, s, k: u + torch.rand(u.shape, generator=gen, device="cuda", dtype=u.dtype)
+        lj, mj, hj = accelerated_solve(c, g, p, yd, l0.clone(), m0.clone(), junk)
+        assert all(x["took"] != "proposal" for x in hj)
+        assert torch.equal(lj, la) and torch.equal(mj, ma)
