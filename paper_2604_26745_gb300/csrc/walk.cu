@@ -268,8 +268,10 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
             ts = tid - wa;
             in_win = (unsigned)ts < (unsigned)wn;
             __syncthreads();  // the gather of chunk ck - 1 has read every stencil
-            if (tid < wn)
-                for (int rr = 0; rr < nrows; ++rr) C0[rr * nth + tid] = kNoRow;
+            // column ts belongs to the ray of thread wa + ts: the thread that writes it during
+            // the walk also clears it, so no barrier is needed between the two
+            if (in_win)
+                for (int rr = 0; rr < nrows; ++rr) C0[rr * nth + ts] = kNoRow;
             cur_row = INT_MIN;  // the stencil rows of this chunk start empty
         }
         if constexpr (TMA) {
