@@ -83,6 +83,41 @@ def test_vjp_deterministic(ctx, P, torch):
     assert torch.equal(a1[0], a2[0]) and torch.equal(a1[1], a2[1])
 
 
+@pytest.mark.parametrize("geo", [(128, 360, 5), (96, 90, 7)])
+def test_walks_independent_of_chunk_height(P, torch, monkeypatch, geo):
+    """The chunk height is a tuning choice (shared-memory budget): forward and JVP must be
+    bitwise the same at every height (each ray sums in the same order), the adjoint the
+    same up to rounding (carried rows split the per-pixel sums differently), and every
+    operator bitwise reproducible at a fixed height.  A stencil column written by one
+    thread and cleared by another would break the last two."""
+    n, na, S = geo
+    ph = synth.lattice_phantom(n, 9, radius=3.0, seed=41)
+    g = P.geometry(n, na, 182, n_sub=S)
+    t = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+    lam, mu = t(ph.lam), t(ph.mu)
+    rs = np.random.default_rng(42)
+    dl, dm = t(rs.standard_normal((n, n))), t(0.01 * rs.standard_normal((n, n)))
+    r = t(rs.standard_normal((na, 182)))
+    ref = None
+    for kb in (72, 40, 100):
+        for k in ("FWD", "JVP", "VJP"):
+            monkeypatch.setenv(f"PGET_SMEM_KB_{k}", str(kb))
+        with P.Context(0) as c:
+            runs = []
+            for _ in range(3):
+                gl, gm = P.pget_vjp(c, g, P.PGET_F32_KAHAN, lam, mu, r)
+                runs.append((P.pget_forward(c, g, P.PGET_F32_KAHAN, lam, mu),
+                             P.pget_jvp(c, g, P.PGET_F32_KAHAN, lam, mu, dl, dm), gl, gm))
+        for rr in runs[1:]:
+            assert all(torch.equal(a, b) for a, b in zip(rr, runs[0])), kb
+        if ref is None:
+            ref = runs[0]
+            continue
+        assert torch.equal(runs[0][0], ref[0]) and torch.equal(runs[0][1], ref[1]), kb
+        for a, b in zip(runs[0][2:], ref[2:]):
+            assert float((a - b).abs().max() / b.abs().max()) <= 1e-6, kb
+
+
 @pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("eps", [1e-3, -1.0])
 def test_prior_parity(ctx, O, P, torch, prec, eps):
