@@ -271,7 +271,11 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
             // column ts belongs to the ray of thread wa + ts: the thread that writes it during
             // the walk also clears it, so no barrier is needed between the two
             if (in_win)
-                for (int rr = 0; rr < nrows; ++rr) C0[rr * nth + ts] = kNoRow;
+                for (int rr = 0; rr < nrows; ++rr) {
+                    C0[rr * nth + ts] = kNoRow;
+#pragma unroll
+                    for (int k = 0; k < SW; ++k) ST[(rr * SW + k) * nth + ts] = mk2(T(0), T(0));
+                }
             cur_row = INT_MIN;  // the stencil rows of this chunk start empty
         }
         if constexpr (TMA) {
@@ -319,17 +323,15 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                         const T gl = rho * h * at;
                         const T gm = -rho * h * h * Qh;
                         const int rl = iy0 - row_lo;  // lower row of the cell; upper is rl + 1
-                        if (iy0 != cur_row && in_win) {
+                        if (iy0 != cur_row && in_win) {  // stencil rows start zeroed (chunk top)
                             if (iy0 + 1 != cur_row) {
                                 c0_hi = ix0 - base;
                                 C0[(rl + 1) * nth + ts] = (short)c0_hi;
-                                for (int k = 0; k < SW; ++k) ST[((rl + 1) * SW + k) * nth + ts] = mk2(T(0), T(0));
                             } else {
                                 c0_hi = c0_lo;
                             }
                             c0_lo = ix0 - base;
                             C0[rl * nth + ts] = (short)c0_lo;
-                            for (int k = 0; k < SW; ++k) ST[(rl * SW + k) * nth + ts] = mk2(T(0), T(0));
                             cur_row = iy0;
                         }
                         const int ol = ix0 - c0_lo, oh = ix0 - c0_hi;
