@@ -58,6 +58,9 @@ class Params(C.Structure):
         ("rho_hi", C.c_double),
         ("nu_min", C.c_double),
         ("nu_max", C.c_double),
+        ("alpha_decay_iters", C.c_int32),
+        ("pad", C.c_int32),
+        ("alpha_decay", C.c_double),
     ]
 
 
@@ -191,7 +194,8 @@ def reg_apply(W, v, alpha) -> np.ndarray:
 def default_params(**kw) -> Params:
     d = dict(alpha_lambda=1e-2, alpha_mu=1e-2, tv_eps=1e-3, lambda_max=2.0, mu_max=0.2,
              max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10, nu0_scale=1e-3, nu_up=4.0,
-             nu_down=0.5, eta=1e-3, rho_lo=0.25, rho_hi=0.75, nu_min=1e-12, nu_max=1e12)
+             nu_down=0.5, eta=1e-3, rho_lo=0.25, rho_hi=0.75, nu_min=1e-12, nu_max=1e12,
+             alpha_decay=1.0, alpha_decay_iters=0)
     d.update(kw)
     return Params(**d)
 

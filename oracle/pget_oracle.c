@@ -27,7 +27,8 @@
  *                   (J^T J + alpha grad^T W grad + nu I) delta = rhs.
  *   og_lm        -- the trust-region LM iteration of Sec. 2.2: step from Eq. (9),
  *                   projection onto the box of Eq. (6), model m_k of Eq. (8), agreement
- *                   ratio rho of Eq. (12), acceptance rho > eta with eta in (0, 1/4).
+ *                   ratio rho of Eq. (12), acceptance rho > eta with eta in (0, 1/4);
+ *                   optionally with the continuation alpha^(k) = alpha / 5^k of Sec. 3.1.
  *   og_lm_trial  -- one trial of that iteration at a given point and damping, returning
  *                   the step s_k without moving the iterate (the LMA(u_k) of Alg. 2).
  *   og_check_proposal -- the safeguard of Prop. conv_check / Alg. 2 (Sec. 3.1): accept a
@@ -435,7 +436,23 @@ typedef struct {
     int32_t max_iters, cg_max_iters;
     double cg_rel_tol;
     double nu0_scale, nu_up, nu_down, eta, rho_lo, rho_hi, nu_min, nu_max;
+    int32_t alpha_decay_iters, pad;
+    double alpha_decay;
 } og_params;
+
+/* Prior weights of LM iteration k under the continuation of Sec. 3.1 (alpha^(k) =
+ * alpha / decay^k, the decrease halted after alpha_decay_iters iterations); decay <= 1
+ * or no iterations: fixed alpha. */
+static og_params og_params_at(const og_params* pr, int k) {
+    og_params q = *pr;
+    if (pr->alpha_decay > 1.0 && pr->alpha_decay_iters > 0) {
+        int e = k < pr->alpha_decay_iters ? k : pr->alpha_decay_iters;
+        double sc = pow(pr->alpha_decay, -(double)e);
+        q.alpha_lambda *= sc;
+        q.alpha_mu *= sc;
+    }
+    return q;
+}
 
 static double og_dot(int m, const double* a, const double* b) {
     double s = 0.0;
@@ -585,7 +602,17 @@ int og_lm(const og_geom* gin, const og_params* pr, const double* y, double* lam,
     rep->nu0 = nu0;
 
     int k;
-    for (k = 0; k < pr->max_iters; ++k) {
+    const og_params* pr0 = pr;
+    og_params prk = og_params_at(pr0, 0);
+    for (k = 0; k < pr0->max_iters; ++k) {
+        /* continuation: a new alpha changes f and its gradient at the current iterate */
+        og_params next = og_params_at(pr0, k);
+        if (k > 0 && (next.alpha_lambda != prk.alpha_lambda || next.alpha_mu != prk.alpha_mu)) {
+            prk = next;
+            f = og_objective(g, &prk, lam, mu, y, r);
+            og_gradient(g, &prk, lam, mu, r, Wl, Wm, grad, tmp);
+        }
+        pr = &prk;
         for (int i = 0; i < 2 * np; ++i) rhs[i] = -grad[i];
         int it = og_cg(g, pr, lam, mu, Wl, Wm, nu, rhs, delta);
         rep->cg_iters_total += it;
@@ -634,6 +661,7 @@ int og_lm(const og_geom* gin, const og_params* pr, const double* y, double* lam,
             rep->cg_iters[k] = it;
         }
     }
+    pr = pr0;
     rep->iters_run = k;
     rep->f_final = f;
     rep->nu_final = nu;

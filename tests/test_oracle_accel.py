@@ -116,3 +116,49 @@ def test_proposal_outside_the_box_is_projected(O):
     a = O.check_proposal(g, pr, y, l0, m0, s, pl, pm)
     b = O.check_proposal(g, pr, y, l0, m0, s, np.clip(pl, 0, pr.lambda_max), np.clip(pm, 0, pr.mu_max))
     assert a == b
+
+
+def _chain_trials(O, g, y, l0, m0, alpha, decay, K, iters, cg):
+    """The LM with continuation rebuilt from single (pinned) trials: iteration k uses
+    alpha / decay^min(k, K) with the damping carried over."""
+    lam, mu = np.clip(l0, 0, 2.0), np.clip(m0, 0, 0.2)
+    nu, nu0, out = 0.0, None, []
+    for k in range(iters):
+        sc = decay ** -min(k, K)
+        pk = O.default_params(cg_max_iters=cg, alpha_lambda=alpha * sc, alpha_mu=alpha * sc)
+        s, t = O.lm_trial(g, pk, y, lam, mu, nu)
+        if nu0 is None:
+            nu0 = nu = t["nu0"]
+        if t["accept"]:
+            lam, mu = lam + s[0], mu + s[1]
+        nu = min(max(t["nu_next"], 1e-12 * nu0), 1e12 * nu0)
+        out.append((t, nu))
+    return lam, mu, out
+
+
+def test_alpha_continuation_is_a_chain_of_trials(O):
+    """Sec. 3.1: alpha^(k) = alpha / 5^k, halted after K iterations; each iteration's f and
+    gradient use alpha^(k).  The LM with continuation equals the chain of single trials
+    with those weights, iteration by iteration (pred, ared, rho, acceptance, damping)."""
+    g, ph, y = _case(O, seed=9, noise=1e4)
+    l0, m0 = O.initial_guess(g, y)
+    for K in (2, 4):
+        pr = O.default_params(max_iters=6, cg_max_iters=6, alpha_decay=5.0, alpha_decay_iters=K)
+        lam, mu, rep = O.lm(g, pr, y, l0, m0)
+        lc, mc, chain = _chain_trials(O, g, y, l0, m0, 1e-2, 5.0, K, 6, 6)
+        for k, (t, nu) in enumerate(chain):
+            for key in ("pred", "ared", "rho"):
+                assert abs(t[key] - rep[key][k]) <= 1e-9 * max(1.0, abs(rep[key][k])), (K, k, key)
+            assert t["accept"] == rep["acc"][k] and abs(nu - rep["nu"][k]) <= 1e-12 * rep["nu"][k]
+        assert np.abs(lc - lam).max() <= 1e-12 and np.abs(mc - mu).max() <= 1e-12
+        assert sum(rep["acc"]) >= 3  # the chain exercises accepted steps
+
+
+def test_alpha_continuation_off_is_the_plain_lm(O):
+    g, ph, y = _case(O, seed=10, noise=1e4)
+    l0, m0 = O.initial_guess(g, y)
+    base = O.lm(g, O.default_params(max_iters=4, cg_max_iters=6), y, l0, m0)
+    for dec, K in ((1.0, 5), (5.0, 0), (0.0, 3)):
+        got = O.lm(g, O.default_params(max_iters=4, cg_max_iters=6, alpha_decay=dec, alpha_decay_iters=K),
+                   y, l0, m0)
+        assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1]) and got[2] == base[2]
