@@ -88,6 +88,10 @@ typedef struct {
     double rho_lo, rho_hi;           /* (0.25, 0.75)                                              */
     double nu_min, nu_max;           /* nu clamped to [nu_min nu_0, nu_max nu_0] (1e-12, 1e12)   */
     int32_t precision;               /* pget_precision                                           */
+    int32_t alpha_decay_iters;       /* continuation (Sec. 3.1): iteration k uses the prior       */
+    double alpha_decay;              /* weights alpha / alpha_decay^min(k, alpha_decay_iters);   */
+                                     /* f and its gradient are re-evaluated when they change.    */
+                                     /* alpha_decay <= 1 or 0 iterations: fixed alpha (1.0, 0)   */
 } pget_lm_params;
 
 #define PGET_TRACE 256

@@ -5,7 +5,9 @@ G suggest u~ = G(u_k, s_k), and keeps u~ only if it passes the convergence check
 Prop. conv_check (pget_proposal_check): rho(s~) > eta and m_k(s~) <= m_k(s_k).
 Otherwise the plain LM outcome stands: u_k + s_k if the trial was accepted, else u_k.
 The damping follows the LM trial's own schedule (the paper leaves it open after an
-accepted proposal; the LM step's rho drives it here, clamped as in a plain solve).
+accepted proposal; the LM step's rho drives it here, clamped as in a plain solve), and
+the prior weights follow the continuation alpha / alpha_decay^min(k, alpha_decay_iters)
+of Sec. 3.1 when p asks for it, as pget_lm_solve does.
 
 G is any callable or torch.nn.Module taking (u, s, k) with u, s stacked [2, n, n] CUDA
 tensors (lambda, mu) and k the iteration, returning a proposal of the same shape, or None
@@ -19,6 +21,16 @@ import torch
 from . import pget as P
 
 
+def params_at(p: P.pget_lm_params, k: int) -> P.pget_lm_params:
+    """The parameters of LM iteration k under the continuation (fixed when off)."""
+    q = P.pget_lm_params.from_buffer_copy(p)
+    if p.alpha_decay > 1.0 and p.alpha_decay_iters > 0:
+        sc = p.alpha_decay ** -min(k, p.alpha_decay_iters)
+        q.alpha_lambda = p.alpha_lambda * sc
+        q.alpha_mu = p.alpha_mu * sc
+    return q
+
+
 def accelerated_solve(ctx: P.Context, g: P.pget_geometry, p: P.pget_lm_params, y: torch.Tensor,
                       lam: torch.Tensor, mu: torch.Tensor, G=None, iters: int | None = None):
     """Run Alg. 2 from (lam, mu) (projected onto the box first); returns (lam, mu, history)
@@ -30,7 +42,8 @@ def accelerated_solve(ctx: P.Context, g: P.pget_geometry, p: P.pget_lm_params, y
     s = lam.new_empty((2,) + tuple(lam.shape))
     history = []
     for k in range(iters):
-        s, tr = P.pget_lm_trial(ctx, g, p, y, lam, mu, nu, s_out=s)
+        pk = params_at(p, k)
+        s, tr = P.pget_lm_trial(ctx, g, pk, y, lam, mu, nu, s_out=s)
         if nu0 is None:
             nu0 = nu = tr["nu0"]
         took, chk = ("step" if tr["accept"] else "none"), None
@@ -38,7 +51,7 @@ def accelerated_solve(ctx: P.Context, g: P.pget_geometry, p: P.pget_lm_params, y
             prop = G(torch.stack([lam, mu]), s, k)
             if prop is not None:
                 pl, pm = prop[0].contiguous(), prop[1].contiguous()
-                chk = P.pget_proposal_check(ctx, g, p, y, lam, mu, s, pl, pm)
+                chk = P.pget_proposal_check(ctx, g, pk, y, lam, mu, s, pl, pm)
                 if chk["accept"]:
                     lam = pl.clamp(0.0, p.lambda_max).contiguous()
                     mu = pm.clamp(0.0, p.mu_max).contiguous()

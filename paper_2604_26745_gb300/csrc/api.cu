@@ -618,7 +618,21 @@ pget_status check_params(const pget_lm_params* p) {
     if (!(p->nu_up >= 1) || !(p->nu_down > 0 && p->nu_down <= 1)) return fail(PGET_EINVAL, "bad nu_up / nu_down");
     if (p->precision != PGET_F64 && p->precision != PGET_F32 && p->precision != PGET_F32_KAHAN)
         return fail(PGET_EINVAL, "unknown precision %d", p->precision);
+    if (!(p->alpha_decay == 0.0 || p->alpha_decay >= 1.0) || p->alpha_decay_iters < 0)
+        return fail(PGET_EINVAL, "alpha_decay must be 0 or >= 1 and alpha_decay_iters >= 0");
     return PGET_OK;
+}
+
+// Prior weights of LM iteration k under the continuation of Sec. 3.1:
+// alpha / alpha_decay^min(k, alpha_decay_iters) (fixed when alpha_decay <= 1 or no iterations).
+pget_lm_params params_at(const pget_lm_params& p, int k) {
+    pget_lm_params q = p;
+    if (p.alpha_decay > 1.0 && p.alpha_decay_iters > 0) {
+        const double sc = std::pow(p.alpha_decay, -(double)std::min(k, p.alpha_decay_iters));
+        q.alpha_lambda *= sc;
+        q.alpha_mu *= sc;
+    }
+    return q;
 }
 
 // LM solve on device pointers (y, u0 planar inputs copied into the workspace)
@@ -662,19 +676,36 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
     LmParamsDev pd;
     params_dev(p, &pd);
     const int* no_grad = &L->no_grad;
+    pget_lm_params pk = params_at(p, 0);
     for (int k = 0; k < p.max_iters; ++k) {
+        // continuation: new prior weights change f and its gradient at the current iterate
+        const pget_lm_params nk = params_at(p, k);
+        const bool refresh = k > 0 && (nk.alpha_lambda != pk.alpha_lambda || nk.alpha_mu != pk.alpha_mu);
+        pk = nk;
+        ga.alpha_l = pk.alpha_lambda;
+        ga.alpha_m = pk.alpha_mu;
+        if (refresh) {
+            dot<T>((const T*)w.r, (const T*)w.r, M, w.dpart[0], nullptr, st);
+            finish_sum(w.dpart[0], &L->rtrt, nullptr, st);
+            reg_value<T>(u, n, pk.alpha_lambda, pk.tv_eps, w.dpart[1], nullptr, st);
+            finish_sum(w.dpart[1], &L->Rl, nullptr, st);
+            reg_value<T>(u + nn, n, pk.alpha_mu, pk.tv_eps, w.dpart[2], nullptr, st);
+            finish_sum(w.dpart[2], &L->Rm, nullptr, st);
+            lm_refresh_f(L, st);
+        }
+        const int* skip_grad = refresh ? nullptr : no_grad;
         // gradient and prior weights at a newly accepted iterate
-        reg_weights<T>(u, n, p.tv_eps, (T*)w.Wl, no_grad, st);
-        reg_weights<T>(u + nn, n, p.tv_eps, (T*)w.Wm, no_grad, st);
-        CK(op_vjp<T>(w, w.pk_u, w.U, w.r, ga, no_grad, st));
+        reg_weights<T>(u, n, p.tv_eps, (T*)w.Wl, skip_grad, st);
+        reg_weights<T>(u + nn, n, p.tv_eps, (T*)w.Wm, skip_grad, st);
+        CK(op_vjp<T>(w, w.pk_u, w.U, w.r, ga, skip_grad, st));
         // step from the damped normal equations, rhs = -grad
-        pget_status s = run_cg<T>(w, w.gr, -1.0, 0.0, &L->nu, p, st);
+        pget_status s = run_cg<T>(w, w.gr, -1.0, 0.0, &L->nu, pk, st);
         if (s != PGET_OK) return s;
         lm_step<T>(u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, p.lambda_max, p.mu_max, st);
         pack_vec<T>(w, w.ut, w.pk_ut, nullptr, st);
         pack_vec<T>(w, w.s, w.pk_p, nullptr, st);
-        lm_model<T>((const T*)w.s, (const T*)w.gr, (const T*)w.Wl, (const T*)w.Wm, n, p.alpha_lambda,
-                    p.alpha_mu, w.dpart[0], w.dpart[1], st);
+        lm_model<T>((const T*)w.s, (const T*)w.gr, (const T*)w.Wl, (const T*)w.Wm, n, pk.alpha_lambda,
+                    pk.alpha_mu, w.dpart[0], w.dpart[1], st);
         finish_sum(w.dpart[0], &L->sg, nullptr, st);
         finish_sum(w.dpart[1], &L->sHs, nullptr, st);
         CK(op_jvp(w, w.pk_u, w.pk_p, w.Jp, nullptr, st));
@@ -684,9 +715,9 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
         sub_dot<T>((const T*)w.rt, (const T*)w.yb, (T*)w.rt, M, w.dpart[3], nullptr, st);
         finish_sum(w.dpart[3], &L->rtrt, nullptr, st);
         const T* ut = (const T*)w.ut;
-        reg_value<T>(ut, n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st);
+        reg_value<T>(ut, n, pk.alpha_lambda, pk.tv_eps, w.dpart[1], nullptr, st);
         finish_sum(w.dpart[1], &L->Rl, nullptr, st);
-        reg_value<T>(ut + nn, n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st);
+        reg_value<T>(ut + nn, n, pk.alpha_mu, pk.tv_eps, w.dpart[2], nullptr, st);
         finish_sum(w.dpart[2], &L->Rm, nullptr, st);
         lm_decide(L, pd, st);
         const int* acc = &L->accept;
@@ -1165,6 +1196,8 @@ void pget_default_params(pget_lm_params* o) {
     o->nu_min = 1e-12;
     o->nu_max = 1e12;
     o->precision = PGET_F32_KAHAN;
+    o->alpha_decay = 1.0;
+    o->alpha_decay_iters = 0;
 }
 
 pget_status pget_create(pget_ctx** ctx, int device, size_t budget) {

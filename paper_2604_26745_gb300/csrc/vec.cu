@@ -577,6 +577,16 @@ __global__ void lm_init_f_kernel(LmState* L, double nu0_scale) {
 }
 void lm_init_f(LmState* L, double nu0_scale, cudaStream_t st) { lm_init_f_kernel<<<1, 32, 0, st>>>(L, nu0_scale); }
 
+// f at the current iterate from its data term and prior values (after new prior weights)
+__global__ void lm_refresh_f_kernel(LmState* L) {
+    if (threadIdx.x || blockIdx.x) return;
+    L->f = 0.5 * L->rtrt + L->Rl + L->Rm;
+}
+void lm_refresh_f(LmState* L, cudaStream_t st) {
+    lm_refresh_f_kernel<<<1, 32, 0, st>>>(L);
+    note_launch();
+}
+
 // conditional copy (accepted trial becomes the iterate)
 template <typename T>
 __global__ void copy_if_kernel(T* __restrict__ dst, const T* __restrict__ src, size_t m, const int* flag) {

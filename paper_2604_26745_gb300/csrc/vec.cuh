@@ -82,6 +82,7 @@ void lm_model(const T* s, const T* g, const T* Wl, const T* Wm, int n, double al
               double* pb, cudaStream_t st);
 void lm_decide(LmState* L, const LmParamsDev& P, cudaStream_t st);
 void lm_init_f(LmState* L, double nu0_scale, cudaStream_t st);
+void lm_refresh_f(LmState* L, cudaStream_t st);
 template <typename T>
 void copy_if(T* dst, const T* src, size_t m, const int* flag, cudaStream_t st);
 template <typename T>

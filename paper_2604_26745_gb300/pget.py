@@ -37,7 +37,8 @@ class pget_lm_params(C.Structure):
                 ("cg_max_iters", C.c_int32), ("cg_rel_tol", C.c_double), ("nu0_scale", C.c_double),
                 ("nu_up", C.c_double), ("nu_down", C.c_double), ("eta", C.c_double),
                 ("rho_lo", C.c_double), ("rho_hi", C.c_double), ("nu_min", C.c_double),
-                ("nu_max", C.c_double), ("precision", C.c_int32)]
+                ("nu_max", C.c_double), ("precision", C.c_int32), ("alpha_decay_iters", C.c_int32),
+                ("alpha_decay", C.c_double)]
 
 
 class pget_lm_report(C.Structure):

@@ -109,3 +109,41 @@ def test_driver(O, P, torch):
         lj, mj, hj = accelerated_solve(c, g, p, yd, l0.clone(), m0.clone(), junk)
         assert all(x["took"] != "proposal" for x in hj)
         assert torch.equal(lj, la) and torch.equal(mj, ma)
+
+
+def test_alpha_continuation_matches_oracle(O, P, torch):
+    """Sec. 3.1's alpha / 5^k (halted after K iterations) in pget_lm_solve against the
+    oracle LM with the same continuation (FP64, CG <= 6: the stable regime), and the Alg. 2
+    driver without proposals against pget_lm_solve."""
+    from paper_2604_26745_gb300.accelerated import accelerated_solve
+    ph, go, g, y = _setup(O, P, torch, seed=27)
+    pr = O.default_params(max_iters=5, cg_max_iters=6, alpha_decay=5.0, alpha_decay_iters=3)
+    l0, m0 = O.initial_guess(go, y)
+    lo, mo, ro = O.lm(go, pr, y, l0, m0)
+    p = P.default_params(max_iters=5, cg_max_iters=6, cg_rel_tol=1e-10, precision=0, alpha_decay=5.0,
+                         alpha_decay_iters=3)
+    t = lambda a: torch.tensor(a, device="cuda")
+    with P.Context(0) as c:
+        lam, mu = t(l0), t(m0)
+        rep = P.pget_lm_solve(c, g, p, t(y), lam, mu)
+        la, ma, h = accelerated_solve(c, g, p, t(y), t(l0), t(m0), None)
+    assert rep["acc"] == ro["acc"] and sum(ro["acc"]) >= 3
+    assert _rel(lam.cpu().numpy(), lo) <= 1e-10 and _rel(mu.cpu().numpy(), mo) <= 1e-10
+    for k in range(5):
+        assert abs(rep["f"][k] - ro["f"][k]) <= 1e-10 * abs(ro["f"][k])
+    assert [x["took"] == "step" for x in h] == [bool(a) for a in rep["acc"]]
+    assert float((la - lam).abs().max()) <= 1e-12 and float((ma - mu).abs().max()) <= 1e-12
+    # continuation off reproduces the fixed-alpha solve bitwise
+    with P.Context(0) as c:
+        outs = []
+        for dec, K in ((1.0, 3), (5.0, 0)):
+            pp = P.default_params(max_iters=3, cg_max_iters=6, cg_rel_tol=1e-10, precision=0,
+                                  alpha_decay=dec, alpha_decay_iters=K)
+            lam, mu = t(l0), t(m0)
+            P.pget_lm_solve(c, g, pp, t(y), lam, mu)
+            outs.append((lam, mu))
+        lam, mu = t(l0), t(m0)
+        P.pget_lm_solve(c, g, P.default_params(max_iters=3, cg_max_iters=6, cg_rel_tol=1e-10, precision=0),
+                        t(y), lam, mu)
+    for a, b in outs:
+        assert torch.equal(a, lam) and torch.equal(b, mu)
