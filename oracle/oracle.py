@@ -61,6 +61,10 @@ class Params(C.Structure):
         ("alpha_decay_iters", C.c_int32),
         ("pad", C.c_int32),
         ("alpha_decay", C.c_double),
+        ("geo_alpha_lambda", C.c_double),
+        ("geo_alpha_mu", C.c_double),
+        ("geo_mu_water", C.c_double),
+        ("geo_mask", C.c_void_p),
     ]
 
 
@@ -192,12 +196,21 @@ def reg_apply(W, v, alpha) -> np.ndarray:
 
 
 def default_params(**kw) -> Params:
+    """Parameters; geo_mask (an [n, n] array) switches on the geometry priors of Eq. (6)
+    with weights geo_alpha_lambda, geo_alpha_mu and water attenuation geo_mu_water."""
     d = dict(alpha_lambda=1e-2, alpha_mu=1e-2, tv_eps=1e-3, lambda_max=2.0, mu_max=0.2,
              max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10, nu0_scale=1e-3, nu_up=4.0,
              nu_down=0.5, eta=1e-3, rho_lo=0.25, rho_hi=0.75, nu_min=1e-12, nu_max=1e12,
-             alpha_decay=1.0, alpha_decay_iters=0)
+             alpha_decay=1.0, alpha_decay_iters=0, geo_alpha_lambda=0.0, geo_alpha_mu=0.0,
+             geo_mu_water=0.0)
+    mask = kw.pop("geo_mask", None)
     d.update(kw)
-    return Params(**d)
+    pr = Params(**d)
+    if mask is not None:
+        m = _f64(mask)
+        pr.geo_mask = m.ctypes.data
+        pr._keep = m  # the array must live as long as the parameters
+    return pr
 
 
 def cg(g: Geom, pr: Params, lam, mu, Wl, Wm, nu, b):

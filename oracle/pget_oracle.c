@@ -22,7 +22,9 @@
  *                   convergence proposition, Sec. 3.1), written as a scatter loop.
  *   og_reg_*     -- the regulariser that replaces the P1/P2 terms of Eq. (6):
  *                   alpha * sum sqrt(|grad u|^2 + eps^2) (smoothed TV), its gradient
- *                   alpha grad^T W grad u and the frozen-weight Hessian alpha grad^T W grad.
+ *                   alpha grad^T W grad u and the frozen-weight Hessian alpha grad^T W grad;
+ *                   optionally with the geometry priors of Eq. (6) themselves,
+ *                   alpha_1 |P1 lambda|^2 + alpha_2 |P2 mu|^2 (og_geo_*).
  *   og_cg        -- conjugate gradients on the damped normal equations of Eq. (9):
  *                   (J^T J + alpha grad^T W grad + nu I) delta = rhs.
  *   og_lm        -- the trust-region LM iteration of Sec. 2.2: step from Eq. (9),
@@ -438,7 +440,59 @@ typedef struct {
     double nu0_scale, nu_up, nu_down, eta, rho_lo, rho_hi, nu_min, nu_max;
     int32_t alpha_decay_iters, pad;
     double alpha_decay;
+    double geo_alpha_lambda, geo_alpha_mu, geo_mu_water;
+    const double* geo_mask;  /* [n][n] potential rod locations in [0, 1], or NULL */
 } og_params;
+
+/* Geometry priors of Eq. (6): alpha_1 |P1 lambda|^2 + alpha_2 |P2 mu|^2 with the
+ * projections P1 lambda = (1 - M) lambda and P2 mu = (1 - M)(mu - mu_water), M the mask of
+ * the potential rod locations (values outside them are penalised; water keeps its
+ * attenuation).  Quadratic: gradient 2 alpha (1 - M)^2 (u - c), Hessian 2 alpha (1 - M)^2. */
+static double og_geo_value(int n, const og_params* pr, const double* lam, const double* mu) {
+    if (!pr->geo_mask) return 0.0;
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < n * n; ++i) {
+        double om = 1.0 - pr->geo_mask[i];
+        double pl = om * lam[i], pm = om * (mu[i] - pr->geo_mu_water);
+        a += pl * pl;
+        b += pm * pm;
+    }
+    return pr->geo_alpha_lambda * a + pr->geo_alpha_mu * b;
+}
+
+/* grad += gradient of the geometry priors at (lam, mu) (stacked [lambda; mu]) */
+static void og_geo_grad_add(int n, const og_params* pr, const double* lam, const double* mu, double* grad) {
+    if (!pr->geo_mask) return;
+    int np = n * n;
+    for (int i = 0; i < np; ++i) {
+        double om2 = (1.0 - pr->geo_mask[i]) * (1.0 - pr->geo_mask[i]);
+        grad[i] += 2.0 * pr->geo_alpha_lambda * om2 * lam[i];
+        grad[np + i] += 2.0 * pr->geo_alpha_mu * om2 * (mu[i] - pr->geo_mu_water);
+    }
+}
+
+/* out += Hessian of the geometry priors times the stacked vector v */
+static void og_geo_hess_add(int n, const og_params* pr, const double* v, double* out) {
+    if (!pr->geo_mask) return;
+    int np = n * n;
+    for (int i = 0; i < np; ++i) {
+        double om2 = (1.0 - pr->geo_mask[i]) * (1.0 - pr->geo_mask[i]);
+        out[i] += 2.0 * pr->geo_alpha_lambda * om2 * v[i];
+        out[np + i] += 2.0 * pr->geo_alpha_mu * om2 * v[np + i];
+    }
+}
+
+/* s^T (Hessian of the geometry priors) s */
+static double og_geo_quad(int n, const og_params* pr, const double* s) {
+    if (!pr->geo_mask) return 0.0;
+    int np = n * n;
+    double q = 0.0;
+    for (int i = 0; i < np; ++i) {
+        double om2 = (1.0 - pr->geo_mask[i]) * (1.0 - pr->geo_mask[i]);
+        q += 2.0 * om2 * (pr->geo_alpha_lambda * s[i] * s[i] + pr->geo_alpha_mu * s[np + i] * s[np + i]);
+    }
+    return q;
+}
 
 /* Prior weights of LM iteration k under the continuation of Sec. 3.1 (alpha^(k) =
  * alpha / decay^k, the decrease halted after alpha_decay_iters iterations); decay <= 1
@@ -471,6 +525,7 @@ static void og_normal_apply(const og_geom* g, const og_params* pr, const double*
     for (int i = 0; i < np; ++i) out[i] += tmp_img[i] + nu * v[i];
     og_reg_apply(n, pr->alpha_mu, Wm, v + np, tmp_img);
     for (int i = 0; i < np; ++i) out[np + i] += tmp_img[i] + nu * v[np + i];
+    og_geo_hess_add(n, pr, v, out);
 }
 
 /* Plain CG from x = 0 on (J^T J + H + nu I) x = b, the normal equations of Eq. (9).
@@ -536,7 +591,7 @@ static double og_objective(const og_geom* g, const og_params* pr, const double* 
     og_forward(g, lam, mu, r);
     for (int i = 0; i < m; ++i) r[i] -= y[i];
     return 0.5 * og_dot(m, r, r) + og_reg_value(g->n, pr->alpha_lambda, pr->tv_eps, lam) +
-           og_reg_value(g->n, pr->alpha_mu, pr->tv_eps, mu);
+           og_reg_value(g->n, pr->alpha_mu, pr->tv_eps, mu) + og_geo_value(g->n, pr, lam, mu);
 }
 
 /* Gradient of the objective at u: grad = J^T r + alpha grad^T W grad u. */
@@ -549,6 +604,7 @@ static void og_gradient(const og_geom* g, const og_params* pr, const double* lam
     for (int i = 0; i < np; ++i) grad[i] += tmp[i];
     og_reg_apply(g->n, pr->alpha_mu, Wm, mu, tmp);
     for (int i = 0; i < np; ++i) grad[np + i] += tmp[i];
+    og_geo_grad_add(g->n, pr, lam, mu, grad);
 }
 
 static double og_clamp(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -630,6 +686,7 @@ int og_lm(const og_geom* gin, const og_params* pr, const double* y, double* lam,
         sHs += og_dot(np, s, Hs);
         og_reg_apply(n, pr->alpha_mu, Wm, s + np, Hs);
         sHs += og_dot(np, s + np, Hs);
+        sHs += og_geo_quad(n, pr, s);
         double pred = -og_dot(2 * np, s, grad) - 0.5 * og_dot(m, Js, Js) - 0.5 * sHs;
         /* actual decrease */
         double ft = og_objective(g, pr, ut, ut + np, y, rt);
@@ -704,6 +761,7 @@ static double og_model_decrease(const og_geom* g, const og_params* pr, const dou
     sHs += og_dot(np, s, Hs);
     og_reg_apply(n, pr->alpha_mu, Wm, s + np, Hs);
     sHs += og_dot(np, s + np, Hs);
+    sHs += og_geo_quad(n, pr, s);
     return -og_dot(2 * np, s, grad) - 0.5 * og_dot(m, Js, Js) - 0.5 * sHs;
 }
 
