@@ -92,6 +92,13 @@ typedef struct {
     double alpha_decay;              /* weights alpha / alpha_decay^min(k, alpha_decay_iters);   */
                                      /* f and its gradient are re-evaluated when they change.    */
                                      /* alpha_decay <= 1 or 0 iterations: fixed alpha (1.0, 0)   */
+    /* geometry priors of Eq. (6), added to R: geo_alpha_lambda |(1 - M) lambda|^2 +
+     * geo_alpha_mu |(1 - M)(mu - geo_mu_water)|^2 with M = geo_mask, the [n][n] mask of the
+     * potential rod locations in [0, 1] (device memory, element type of the precision;
+     * caller-owned, must stay valid for the call).  NULL: no geometry prior (default).
+     * The continuation above scales these weights too. */
+    double geo_alpha_lambda, geo_alpha_mu, geo_mu_water;
+    const void* geo_mask;
 } pget_lm_params;
 
 #define PGET_TRACE 256

@@ -504,6 +504,8 @@ static og_params og_params_at(const og_params* pr, int k) {
         double sc = pow(pr->alpha_decay, -(double)e);
         q.alpha_lambda *= sc;
         q.alpha_mu *= sc;
+        q.geo_alpha_lambda *= sc;
+        q.geo_alpha_mu *= sc;
     }
     return q;
 }

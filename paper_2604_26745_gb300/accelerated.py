@@ -28,6 +28,8 @@ def params_at(p: P.pget_lm_params, k: int) -> P.pget_lm_params:
         sc = p.alpha_decay ** -min(k, p.alpha_decay_iters)
         q.alpha_lambda = p.alpha_lambda * sc
         q.alpha_mu = p.alpha_mu * sc
+        q.geo_alpha_lambda = p.geo_alpha_lambda * sc
+        q.geo_alpha_mu = p.geo_alpha_mu * sc
     return q
 
 

@@ -552,6 +552,17 @@ void pack_pair(const Workspace& w, const void* lam, const void* mu, void* const 
     pack<T>((const T*)lam, (const T*)mu, w.g.n, w.P, attenuation_scale(w.g), pk[0], pk[1], nullptr, st);
 }
 
+// Geometry priors of Eq. (6) in a fused reduction: the Hessian term (gradient = false) or
+// the gradient 2 alpha (1 - M)^2 (u - c) (gradient = true, c = mu_water on the mu field).
+template <typename T>
+void set_geo(RedArgs<T>& a, const pget_lm_params& p, bool gradient) {
+    a.gmask = (const T*)p.geo_mask;
+    a.geo_l = p.geo_alpha_lambda;
+    a.geo_m = p.geo_alpha_mu;
+    a.geo_cm = p.geo_mu_water;
+    a.geo_offset = gradient ? 1 : 0;
+}
+
 // CG on (J^T J + H + nu I) x = scale_b * b, H and U at the packed iterate pk_u
 template <typename T>
 pget_status run_cg(Workspace& w, const void* b, double scale_b, double nu, const double* nu_dev,
@@ -571,6 +582,7 @@ pget_status run_cg(Workspace& w, const void* b, double scale_b, double nu, const
         ra.Wm = (const T*)w.Wm;
         ra.alpha_l = p.alpha_lambda;
         ra.alpha_m = p.alpha_mu;
+        set_geo(ra, p, false);
         ra.nu = nu;
         ra.nu_dev = nu_dev;
         ra.dotv = (const T*)w.p;
@@ -620,6 +632,8 @@ pget_status check_params(const pget_lm_params* p) {
         return fail(PGET_EINVAL, "unknown precision %d", p->precision);
     if (!(p->alpha_decay == 0.0 || p->alpha_decay >= 1.0) || p->alpha_decay_iters < 0)
         return fail(PGET_EINVAL, "alpha_decay must be 0 or >= 1 and alpha_decay_iters >= 0");
+    if (p->geo_mask && (!(p->geo_alpha_lambda >= 0) || !(p->geo_alpha_mu >= 0) || !std::isfinite(p->geo_mu_water)))
+        return fail(PGET_EINVAL, "geometry prior weights must be >= 0");
     return PGET_OK;
 }
 
@@ -631,6 +645,8 @@ pget_lm_params params_at(const pget_lm_params& p, int k) {
         const double sc = std::pow(p.alpha_decay, -(double)std::min(k, p.alpha_decay_iters));
         q.alpha_lambda *= sc;
         q.alpha_mu *= sc;
+        q.geo_alpha_lambda *= sc;
+        q.geo_alpha_mu *= sc;
     }
     return q;
 }
@@ -651,9 +667,9 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
     CK(op_forward(w, w.pk_u, w.U, w.Jp, nullptr, st));
     sub_dot<T>((const T*)w.Jp, (const T*)w.yb, (T*)w.r, M, w.dpart[0], nullptr, st);
     finish_sum(w.dpart[0], &L->rtrt, nullptr, st);
-    reg_value<T>(u, n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st);
+    reg_value<T>(u, n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st, (const T*)p.geo_mask, p.geo_alpha_lambda, 0.0);
     finish_sum(w.dpart[1], &L->Rl, nullptr, st);
-    reg_value<T>(u + nn, n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st);
+    reg_value<T>(u + nn, n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st, (const T*)p.geo_mask, p.geo_alpha_mu, p.geo_mu_water);
     finish_sum(w.dpart[2], &L->Rm, nullptr, st);
     reg_weights<T>(u, n, p.tv_eps, (T*)w.Wl, nullptr, st);
     reg_weights<T>(u + nn, n, p.tv_eps, (T*)w.Wm, nullptr, st);
@@ -664,6 +680,7 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
     ga.Wm = (const T*)w.Wm;
     ga.alpha_l = p.alpha_lambda;
     ga.alpha_m = p.alpha_mu;
+    set_geo(ga, p, true);
     ga.nu = 0.0;
     CK(op_vjp<T>(w, w.pk_u, w.U, w.r, ga, nullptr, st));
     dot<T>((const T*)w.gr, (const T*)w.gr, 2 * nn, w.dpart[0], nullptr, st);
@@ -684,12 +701,13 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
         pk = nk;
         ga.alpha_l = pk.alpha_lambda;
         ga.alpha_m = pk.alpha_mu;
+        set_geo(ga, pk, true);
         if (refresh) {
             dot<T>((const T*)w.r, (const T*)w.r, M, w.dpart[0], nullptr, st);
             finish_sum(w.dpart[0], &L->rtrt, nullptr, st);
-            reg_value<T>(u, n, pk.alpha_lambda, pk.tv_eps, w.dpart[1], nullptr, st);
+            reg_value<T>(u, n, pk.alpha_lambda, pk.tv_eps, w.dpart[1], nullptr, st, (const T*)pk.geo_mask, pk.geo_alpha_lambda, 0.0);
             finish_sum(w.dpart[1], &L->Rl, nullptr, st);
-            reg_value<T>(u + nn, n, pk.alpha_mu, pk.tv_eps, w.dpart[2], nullptr, st);
+            reg_value<T>(u + nn, n, pk.alpha_mu, pk.tv_eps, w.dpart[2], nullptr, st, (const T*)pk.geo_mask, pk.geo_alpha_mu, pk.geo_mu_water);
             finish_sum(w.dpart[2], &L->Rm, nullptr, st);
             lm_refresh_f(L, st);
         }
@@ -705,7 +723,7 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
         pack_vec<T>(w, w.ut, w.pk_ut, nullptr, st);
         pack_vec<T>(w, w.s, w.pk_p, nullptr, st);
         lm_model<T>((const T*)w.s, (const T*)w.gr, (const T*)w.Wl, (const T*)w.Wm, n, pk.alpha_lambda,
-                    pk.alpha_mu, w.dpart[0], w.dpart[1], st);
+                    pk.alpha_mu, w.dpart[0], w.dpart[1], st, (const T*)pk.geo_mask, pk.geo_alpha_lambda, pk.geo_alpha_mu);
         finish_sum(w.dpart[0], &L->sg, nullptr, st);
         finish_sum(w.dpart[1], &L->sHs, nullptr, st);
         CK(op_jvp(w, w.pk_u, w.pk_p, w.Jp, nullptr, st));
@@ -715,9 +733,9 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
         sub_dot<T>((const T*)w.rt, (const T*)w.yb, (T*)w.rt, M, w.dpart[3], nullptr, st);
         finish_sum(w.dpart[3], &L->rtrt, nullptr, st);
         const T* ut = (const T*)w.ut;
-        reg_value<T>(ut, n, pk.alpha_lambda, pk.tv_eps, w.dpart[1], nullptr, st);
+        reg_value<T>(ut, n, pk.alpha_lambda, pk.tv_eps, w.dpart[1], nullptr, st, (const T*)pk.geo_mask, pk.geo_alpha_lambda, 0.0);
         finish_sum(w.dpart[1], &L->Rl, nullptr, st);
-        reg_value<T>(ut + nn, n, pk.alpha_mu, pk.tv_eps, w.dpart[2], nullptr, st);
+        reg_value<T>(ut + nn, n, pk.alpha_mu, pk.tv_eps, w.dpart[2], nullptr, st, (const T*)pk.geo_mask, pk.geo_alpha_mu, pk.geo_mu_water);
         finish_sum(w.dpart[2], &L->Rm, nullptr, st);
         lm_decide(L, pd, st);
         const int* acc = &L->accept;
@@ -974,8 +992,8 @@ static pget_status objective_at(Workspace& w, const pget_lm_params& p, void* con
     const T* u = (const T*)uvec;
     CK(op_forward(w, pk, U, w.Jp, nullptr, st));
     sub_dot<T>((const T*)w.Jp, (const T*)w.yb, (T*)r, w.M, w.dpart[0], nullptr, st);
-    reg_value<T>(u, w.g.n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st);
-    reg_value<T>(u + w.nn, w.g.n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st);
+    reg_value<T>(u, w.g.n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st, (const T*)p.geo_mask, p.geo_alpha_lambda, 0.0);
+    reg_value<T>(u + w.nn, w.g.n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st, (const T*)p.geo_mask, p.geo_alpha_mu, p.geo_mu_water);
     double v[3];
     pget_status s = host_sums(w, {w.dpart[0], w.dpart[1], w.dpart[2]}, v, st);
     if (s != PGET_OK) return s;
@@ -989,7 +1007,7 @@ template <typename T>
 static pget_status model_decrease(Workspace& w, const pget_lm_params& p, const void* s, double* pred,
                                   cudaStream_t st) {
     lm_model<T>((const T*)s, (const T*)w.gr, (const T*)w.Wl, (const T*)w.Wm, w.g.n, p.alpha_lambda, p.alpha_mu,
-                w.dpart[0], w.dpart[1], st);
+                w.dpart[0], w.dpart[1], st, (const T*)p.geo_mask, p.geo_alpha_lambda, p.geo_alpha_mu);
     pack_vec<T>(w, s, w.pk_p, nullptr, st);
     CK(op_jvp(w, w.pk_u, w.pk_p, w.Jp, nullptr, st));
     dot<T>((const T*)w.Jp, (const T*)w.Jp, w.M, w.dpart[2], nullptr, st);
@@ -1023,6 +1041,7 @@ static pget_status at_point(Workspace& w, const pget_lm_params& p, const void* y
     ga.Wm = (const T*)w.Wm;
     ga.alpha_l = p.alpha_lambda;
     ga.alpha_m = p.alpha_mu;
+    set_geo(ga, p, true);
     ga.nu = 0.0;
     CK(op_vjp<T>(w, w.pk_u, w.U, w.r, ga, nullptr, st));
     return PGET_OK;
@@ -1198,6 +1217,10 @@ void pget_default_params(pget_lm_params* o) {
     o->precision = PGET_F32_KAHAN;
     o->alpha_decay = 1.0;
     o->alpha_decay_iters = 0;
+    o->geo_alpha_lambda = 0.0;
+    o->geo_alpha_mu = 0.0;
+    o->geo_mu_water = 0.0;
+    o->geo_mask = nullptr;
 }
 
 pget_status pget_create(pget_ctx** ctx, int device, size_t budget) {

@@ -136,28 +136,36 @@ __device__ __forceinline__ double block_sum(double v) {
 // R(u) = alpha sum sqrt(|grad u|^2 + eps^2)  or  alpha/2 sum |grad u|^2 ; per-block partials
 template <typename T>
 __global__ void reg_value_kernel(const T* __restrict__ u, int n, double alpha, double eps,
-                                 double* __restrict__ part, const int* skip) {
+                                 double* __restrict__ part, const int* skip, const T* __restrict__ gmask,
+                                 double galpha, double gc) {
     if (skip && *skip) return;
-    double acc = 0.0;
+    double acc = 0.0, gacc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n * n; i += gridDim.x * blockDim.x) {
         const int iy = i / n, ix = i - iy * n;
         T gx, gy;
         grad_at(u, n, ix, iy, &gx, &gy);
         double s2 = (double)gx * gx + (double)gy * gy;
         acc += eps > 0 ? sqrt(s2 + eps * eps) : 0.5 * s2;
+        if (gmask) {  // geometry prior of Eq. (6)
+            const double pv = (1.0 - (double)gmask[i]) * ((double)u[i] - gc);
+            gacc += pv * pv;
+        }
     }
-    double s = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = alpha * s;
+    double s = alpha * block_sum(acc);
+    if (gmask) s += galpha * block_sum(gacc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 template <typename T>
 void reg_value(const T* u, int n, double alpha, double eps, double* part, const int* skip,
-               cudaStream_t st) {
-    reg_value_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, n, alpha, eps, part, skip);
+               cudaStream_t st, const T* gmask, double galpha, double gc) {
+    reg_value_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, n, alpha, eps, part, skip, gmask, galpha, gc);
     note_launch();
 }
-template void reg_value<float>(const float*, int, double, double, double*, const int*, cudaStream_t);
-template void reg_value<double>(const double*, int, double, double, double*, const int*, cudaStream_t);
+template void reg_value<float>(const float*, int, double, double, double*, const int*, cudaStream_t,
+                               const float*, double, double);
+template void reg_value<double>(const double*, int, double, double, double*, const int*, cudaStream_t,
+                                const double*, double, double);
 
 // ------------------------------------------------------------------------ dots
 template <typename T>
@@ -277,6 +285,11 @@ __global__ void reduce_groups_kernel(RedArgs<T> a) {
             const int iy = (int)(i / a.n), ix = (int)(i - (size_t)iy * a.n);
             const T* vf = a.v + f * nn;
             val += reg_at(vf, f ? a.Wm : a.Wl, (T)(f ? a.alpha_m : a.alpha_l), a.n, ix, iy);
+            if (a.gmask) {  // geometry prior of Eq. (6): 2 alpha (1 - M)^2 (v - c)
+                const T om = T(1) - a.gmask[i];
+                const T c = (a.geo_offset && f) ? (T)a.geo_cm : T(0);
+                val += (T)(2.0 * (f ? a.geo_m : a.geo_l)) * om * om * (vf[i] - c);
+            }
             val += (T)nu * vf[i];
         }
         a.out[e] = val;
@@ -500,7 +513,8 @@ template void lm_step<double>(const double*, const double*, double*, double*, si
 template <typename T>
 __global__ void lm_model_kernel(const T* __restrict__ s, const T* __restrict__ g, const T* __restrict__ Wl,
                                 const T* __restrict__ Wm, int n, double al, double am,
-                                double* __restrict__ part_a, double* __restrict__ part_b) {
+                                double* __restrict__ part_a, double* __restrict__ part_b,
+                                const T* __restrict__ gmask, double geo_l, double geo_m) {
     const size_t nn = (size_t)n * n;
     double a = 0.0, b = 0.0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * nn; e += (size_t)gridDim.x * blockDim.x) {
@@ -511,6 +525,10 @@ __global__ void lm_model_kernel(const T* __restrict__ s, const T* __restrict__ g
         T hs = reg_at(sf, f ? Wm : Wl, (T)(f ? am : al), n, ix, iy);
         a += (double)s[e] * (double)g[e];
         b += (double)sf[i] * (double)hs;
+        if (gmask) {  // s^T (2 alpha (1 - M)^2) s of the geometry prior
+            const double om = 1.0 - (double)gmask[i];
+            b += 2.0 * (f ? geo_m : geo_l) * om * om * (double)sf[i] * (double)sf[i];
+        }
     }
     double sa = block_sum(a);
     double sb = block_sum(b);
@@ -521,12 +539,14 @@ __global__ void lm_model_kernel(const T* __restrict__ s, const T* __restrict__ g
 }
 template <typename T>
 void lm_model(const T* s, const T* g, const T* Wl, const T* Wm, int n, double al, double am, double* pa,
-              double* pb, cudaStream_t st) {
-    lm_model_kernel<T><<<kRedBlocks, 256, 0, st>>>(s, g, Wl, Wm, n, al, am, pa, pb);
+              double* pb, cudaStream_t st, const T* gmask, double geo_l, double geo_m) {
+    lm_model_kernel<T><<<kRedBlocks, 256, 0, st>>>(s, g, Wl, Wm, n, al, am, pa, pb, gmask, geo_l, geo_m);
     note_launch();
 }
-template void lm_model<float>(const float*, const float*, const float*, const float*, int, double, double, double*, double*, cudaStream_t);
-template void lm_model<double>(const double*, const double*, const double*, const double*, int, double, double, double*, double*, cudaStream_t);
+template void lm_model<float>(const float*, const float*, const float*, const float*, int, double, double, double*,
+                              double*, cudaStream_t, const float*, double, double);
+template void lm_model<double>(const double*, const double*, const double*, const double*, int, double, double,
+                               double*, double*, cudaStream_t, const double*, double, double);
 
 // One thread: predicted and actual decrease, rho (Eq. (12)), acceptance, nu update.
 __global__ void lm_decide_kernel(LmState* L, LmParamsDev P) {

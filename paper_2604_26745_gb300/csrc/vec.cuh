@@ -44,6 +44,11 @@ template <typename T> struct RedArgs {
     const T* dotv = nullptr;     // optional: per-block partials of <dotv, out>
     double* part = nullptr;
     const int* skip = nullptr;
+    // optional geometry priors (Eq. (6)): adds 2 geo (1 - M)^2 (v - c) with the mask M,
+    // weights geo_l / geo_m and c = geo_cm on the mu field when geo_offset (gradient), else 0
+    const T* gmask = nullptr;
+    double geo_l = 0, geo_m = 0, geo_cm = 0;
+    int geo_offset = 0;
 };
 
 template <typename T>
@@ -53,8 +58,10 @@ template <typename T>
 void reg_weights(const T* u, int n, double eps, T* W, const int* skip, cudaStream_t st);
 template <typename T>
 void reg_apply(const T* v, const T* W, int n, double alpha, T* out, cudaStream_t st);
+// alpha * R(u) (smoothed TV or quadratic), plus galpha |(1 - M)(u - gc)|^2 when gmask is set
 template <typename T>
-void reg_value(const T* u, int n, double alpha, double eps, double* part, const int* skip, cudaStream_t st);
+void reg_value(const T* u, int n, double alpha, double eps, double* part, const int* skip, cudaStream_t st,
+               const T* gmask = nullptr, double galpha = 0.0, double gc = 0.0);
 template <typename T>
 void dot(const T* a, const T* b, size_t m, double* part, const int* skip, cudaStream_t st);
 void finish_sum(const double* part, double* dst, const int* skip, cudaStream_t st);
@@ -79,7 +86,7 @@ template <typename T>
 void lm_step(const T* u, const T* x, T* ut, T* s, size_t nn, double lmax, double mmax, cudaStream_t st);
 template <typename T>
 void lm_model(const T* s, const T* g, const T* Wl, const T* Wm, int n, double al, double am, double* pa,
-              double* pb, cudaStream_t st);
+              double* pb, cudaStream_t st, const T* gmask = nullptr, double geo_l = 0.0, double geo_m = 0.0);
 void lm_decide(LmState* L, const LmParamsDev& P, cudaStream_t st);
 void lm_init_f(LmState* L, double nu0_scale, cudaStream_t st);
 void lm_refresh_f(LmState* L, cudaStream_t st);

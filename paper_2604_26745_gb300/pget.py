@@ -38,7 +38,8 @@ class pget_lm_params(C.Structure):
                 ("nu_up", C.c_double), ("nu_down", C.c_double), ("eta", C.c_double),
                 ("rho_lo", C.c_double), ("rho_hi", C.c_double), ("nu_min", C.c_double),
                 ("nu_max", C.c_double), ("precision", C.c_int32), ("alpha_decay_iters", C.c_int32),
-                ("alpha_decay", C.c_double)]
+                ("alpha_decay", C.c_double), ("geo_alpha_lambda", C.c_double), ("geo_alpha_mu", C.c_double),
+                ("geo_mu_water", C.c_double), ("geo_mask", C.c_void_p)]
 
 
 class pget_lm_report(C.Structure):
@@ -166,12 +167,19 @@ def geometry(n: int, n_angles: int, n_det: int, n_sub: int = 1, collimator: int 
 
 
 def default_params(**kw) -> pget_lm_params:
+    """Library defaults with overrides; geo_mask may be a CUDA tensor (kept alive with the
+    parameters) for the geometry priors."""
     p = pget_lm_params()
     load().pget_default_params(C.byref(p))
+    mask = kw.pop("geo_mask", None)
     for k, v in kw.items():
         if not hasattr(p, k):
             raise AttributeError(k)
         setattr(p, k, v)
+    if mask is not None:
+        m = mask.contiguous()
+        p.geo_mask = m.data_ptr()
+        p._keep = m
     return p
 
 
