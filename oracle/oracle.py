@@ -65,6 +65,8 @@ class Params(C.Structure):
         ("geo_alpha_mu", C.c_double),
         ("geo_mu_water", C.c_double),
         ("geo_mask", C.c_void_p),
+        ("inner_solver", C.c_int32),
+        ("pad2", C.c_int32),
     ]
 
 
@@ -115,6 +117,7 @@ def lib():
         L.og_reg_value.restype = C.c_double
         L.og_reg_apply.argtypes = [C.c_int, C.c_double, dp, dp, dp]
         L.og_cg.argtypes = [gp, C.POINTER(Params), dp, dp, dp, dp, C.c_double, dp, dp]
+        L.og_sgp.argtypes = [gp, C.POINTER(Params), dp, dp, dp, dp, C.c_double, dp, dp]
         L.og_lm.argtypes = [gp, C.POINTER(Params), dp, dp, dp, C.POINTER(Report)]
         L.og_initial_guess.argtypes = [gp, dp, C.c_double, C.c_double, C.c_double, dp, dp]
         L.og_geom_info.argtypes = [gp, C.POINTER(C.c_int32), dp, dp, C.POINTER(C.c_int32)]
@@ -221,6 +224,16 @@ def cg(g: Geom, pr: Params, lam, mu, Wl, Wm, nu, b):
     if it < 0:
         raise ValueError("invalid geometry")
     return x, it
+
+
+def sgp(g: Geom, pr: Params, lam, mu, Wl, Wm, nu, grad):
+    """Gradient projection on the box-constrained LM subproblem: returns (s, iterations)."""
+    lam, mu, Wl, Wm, grad = map(_f64, (lam, mu, Wl, Wm, grad))
+    s = np.zeros_like(grad)
+    it = lib().og_sgp(C.byref(g), C.byref(pr), _p(lam), _p(mu), _p(Wl), _p(Wm), float(nu), _p(grad), _p(s))
+    if it < 0:
+        raise ValueError("invalid geometry")
+    return s, it
 
 
 def lm(g: Geom, pr: Params, y, lam0, mu0):

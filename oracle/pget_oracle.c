@@ -27,6 +27,9 @@
  *                   alpha_1 |P1 lambda|^2 + alpha_2 |P2 mu|^2 (og_geo_*).
  *   og_cg        -- conjugate gradients on the damped normal equations of Eq. (9):
  *                   (J^T J + alpha grad^T W grad + nu I) delta = rhs.
+ *   og_sgp       -- gradient projection on the box-constrained form of Eq. (9), the
+ *                   inner solver Sec. 2.2 names (scaled gradient projection, identity
+ *                   scaling, Barzilai-Borwein lengths, exact line search).
  *   og_lm        -- the trust-region LM iteration of Sec. 2.2: step from Eq. (9),
  *                   projection onto the box of Eq. (6), model m_k of Eq. (8), agreement
  *                   ratio rho of Eq. (12), acceptance rho > eta with eta in (0, 1/4);
@@ -442,6 +445,8 @@ typedef struct {
     double alpha_decay;
     double geo_alpha_lambda, geo_alpha_mu, geo_mu_water;
     const double* geo_mask;  /* [n][n] potential rod locations in [0, 1], or NULL */
+    int32_t inner_solver;    /* 0: CG on Eq. (9) then projection; 1: gradient projection */
+    int32_t pad2;
 } og_params;
 
 /* Geometry priors of Eq. (6): alpha_1 |P1 lambda|^2 + alpha_2 |P2 mu|^2 with the
@@ -574,6 +579,68 @@ int og_cg(const og_geom* g, const og_params* pr, const double* lam, const double
     return it;
 }
 
+static double og_clamp(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Gradient projection for the box-constrained LM subproblem of Sec. 2.2 (the scaled
+ * gradient projection method the paper cites, with the identity scaling):
+ *   min_s q(s) = <g, s> + 1/2 s^T (J^T J + H + nu I) s   subject to  u + s in the box,
+ * from s = 0.  Iteration: d = P_box(u + s - alpha grad q(s)) - u - s; exact line search on
+ * [0, 1] for the quadratic q along d; alpha alternates the two Barzilai-Borwein lengths
+ * |d|^2 / <d, A d> and <d, A d> / |A d|^2, clamped to [1e-10, 1e10].  Stops after
+ * cg_max_iters iterations or when the unit-step projected gradient
+ * |P_box(u + s - grad q) - u - s| <= cg_rel_tol times its value at s = 0.
+ * Returns iterations run; s_out is feasible (u + s in the box). */
+int og_sgp(const og_geom* g, const og_params* pr, const double* lam, const double* mu,
+           const double* Wl, const double* Wm, double nu, const double* grad_f, double* s_out) {
+    og_ctx o;
+    if (og_setup(g, &o)) return -1;
+    int np = o.g.n * o.g.n, m = 2 * np;
+    double* x = s_out;
+    double* gq = malloc(sizeof(double) * m);
+    double* d = malloc(sizeof(double) * m);
+    double* Ad = malloc(sizeof(double) * m);
+    double* ty = malloc(sizeof(double) * o.g.n_angles * o.g.n_det);
+    double* ti = malloc(sizeof(double) * np);
+    memset(x, 0, sizeof(double) * m);
+    memcpy(gq, grad_f, sizeof(double) * m);
+    double alpha = 1.0, pg0 = -1.0;
+    int it = 0;
+    for (it = 0; it < pr->cg_max_iters;) {
+        /* unit-step projected gradient (stopping measure) and the projected step */
+        double pg = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double ui = i < np ? lam[i] : mu[i - np];
+            double hi = i < np ? pr->lambda_max : pr->mu_max;
+            double z1 = og_clamp(ui + x[i] - gq[i], 0.0, hi) - ui - x[i];
+            pg += z1 * z1;
+            d[i] = og_clamp(ui + x[i] - alpha * gq[i], 0.0, hi) - ui - x[i];
+        }
+        pg = sqrt(pg);
+        if (pg0 < 0.0) pg0 = pg;
+        if (pg <= pr->cg_rel_tol * pg0 || pg0 == 0.0) break;
+        double gd = og_dot(m, gq, d);
+        if (!(gd < 0.0)) break;
+        og_normal_apply(&o.g, pr, lam, mu, Wl, Wm, nu, d, Ad, ty, ti);
+        double dAd = og_dot(m, d, Ad);
+        if (!(dAd > 0.0)) break;
+        double lstep = -gd / dAd;
+        if (lstep > 1.0) lstep = 1.0;
+        for (int i = 0; i < m; ++i) {
+            x[i] += lstep * d[i];
+            gq[i] += lstep * Ad[i];
+        }
+        ++it;
+        double a_next = (it % 2) ? og_dot(m, d, d) / dAd : dAd / og_dot(m, Ad, Ad);
+        alpha = og_clamp(a_next, 1e-10, 1e10);
+    }
+    free(gq);
+    free(d);
+    free(Ad);
+    free(ty);
+    free(ti);
+    return it;
+}
+
 /* ------------------------------------------------------------------- LM */
 
 #define OG_TRACE 256
@@ -609,7 +676,6 @@ static void og_gradient(const og_geom* g, const og_params* pr, const double* lam
     og_geo_grad_add(g->n, pr, lam, mu, grad);
 }
 
-static double og_clamp(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 /* Levenberg-Marquardt trust-region iteration, Sec. 2.2 and Sec. 3.1:
  *   delta from CG on (J^T J + H + nu I) delta = -grad            (Eq. (9), nu = beta_k)
@@ -671,8 +737,13 @@ int og_lm(const og_geom* gin, const og_params* pr, const double* y, double* lam,
             og_gradient(g, &prk, lam, mu, r, Wl, Wm, grad, tmp);
         }
         pr = &prk;
-        for (int i = 0; i < 2 * np; ++i) rhs[i] = -grad[i];
-        int it = og_cg(g, pr, lam, mu, Wl, Wm, nu, rhs, delta);
+        int it;
+        if (pr->inner_solver == 1) {  /* gradient projection: delta is already feasible */
+            it = og_sgp(g, pr, lam, mu, Wl, Wm, nu, grad, delta);
+        } else {
+            for (int i = 0; i < 2 * np; ++i) rhs[i] = -grad[i];
+            it = og_cg(g, pr, lam, mu, Wl, Wm, nu, rhs, delta);
+        }
         rep->cg_iters_total += it;
         /* projected step */
         for (int i = 0; i < np; ++i) {
@@ -803,8 +874,12 @@ int og_lm_trial(const og_geom* gin, const og_params* pr, const double* y, const 
         if (!(nu > 0.0)) nu = 1.0;
         out->nu0 = nu;
     }
-    for (int i = 0; i < 2 * np; ++i) rhs[i] = -grad[i];
-    out->cg_iters = og_cg(g, pr, lam, mu, Wl, Wm, nu, rhs, delta);
+    if (pr->inner_solver == 1) {
+        out->cg_iters = og_sgp(g, pr, lam, mu, Wl, Wm, nu, grad, delta);
+    } else {
+        for (int i = 0; i < 2 * np; ++i) rhs[i] = -grad[i];
+        out->cg_iters = og_cg(g, pr, lam, mu, Wl, Wm, nu, rhs, delta);
+    }
     for (int i = 0; i < np; ++i) {
         ut[i] = og_clamp(lam[i] + delta[i], 0.0, pr->lambda_max);
         ut[np + i] = og_clamp(mu[i] + delta[np + i], 0.0, pr->mu_max);
