@@ -99,6 +99,13 @@ typedef struct {
      * The continuation above scales these weights too. */
     double geo_alpha_lambda, geo_alpha_mu, geo_mu_water;
     const void* geo_mask;
+    /* inner solver of the LM step (Sec. 2.2): 0 = CG on Eq. (9), then projection of
+     * u + delta onto the box (default); 1 = gradient projection on the box-constrained
+     * subproblem (the scaled gradient projection the paper names, identity scaling,
+     * Barzilai-Borwein lengths, exact line search), capped by cg_max_iters and stopped
+     * when the unit-step projected gradient falls below cg_rel_tol times its first value */
+    int32_t inner_solver;
+    int32_t reserved;
 } pget_lm_params;
 
 #define PGET_TRACE 256

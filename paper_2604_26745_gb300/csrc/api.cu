@@ -605,6 +605,44 @@ pget_status flags_status(int e) {
     return PGET_OK;
 }
 
+// Gradient projection on min <g, s> + 1/2 s^T (J^T J + H + nu I) s subject to u + s in the
+// box, u the unpacked iterate in w.u (packed in pk_u), g in gvec; result (feasible) in w.x.
+// One J^T J product per iteration, like a CG step; the scalars live in w.lm->cg.
+template <typename T>
+pget_status run_sgp(Workspace& w, const void* gvec, double nu, const double* nu_dev, const pget_lm_params& p,
+                    cudaStream_t st) {
+    const size_t nn = w.nn, m = 2 * nn;
+    CgState* cg = &w.lm->cg;
+    sgp_init<T>((const T*)gvec, (T*)w.res, (T*)w.x, m, p.cg_rel_tol, cg, st);
+    const int* stop = &cg->stop;
+    for (int it = 0; it < p.cg_max_iters; ++it) {
+        sgp_dir<T>((const T*)w.u, (const T*)w.x, (const T*)w.res, (T*)w.p, nn, p.lambda_max, p.mu_max, w.dpart[1],
+                   w.dpart[2], w.dpart[3], cg, st);
+        pack_vec<T>(w, w.p, w.pk_p, stop, st);
+        cudaError_t e = op_jvp(w, w.pk_u, w.pk_p, w.Jp, stop, st);
+        if (e != cudaSuccess) return fail(PGET_ECUDA, "jvp launch: %s", cudaGetErrorString(e));
+        RedArgs<T> ra;
+        ra.out = (T*)w.q;
+        ra.v = (const T*)w.p;
+        ra.Wl = (const T*)w.Wl;
+        ra.Wm = (const T*)w.Wm;
+        ra.alpha_l = p.alpha_lambda;
+        ra.alpha_m = p.alpha_mu;
+        set_geo(ra, p, false);
+        ra.nu = nu;
+        ra.nu_dev = nu_dev;
+        ra.dotv = (const T*)w.p;
+        ra.part = w.dpart[0];
+        e = op_vjp<T>(w, w.pk_u, w.U, w.Jp, ra, stop, st);
+        if (e != cudaSuccess) return fail(PGET_ECUDA, "vjp launch: %s", cudaGetErrorString(e));
+        dot<T>((const T*)w.q, (const T*)w.q, m, w.dpart[1], stop, st);
+        sgp_step(w.dpart[0], w.dpart[1], cg, st);
+        sgp_update<T>((T*)w.x, (T*)w.res, (const T*)w.p, (const T*)w.q, m, cg, st);
+    }
+    CK(cudaGetLastError());
+    return PGET_OK;
+}
+
 pget_status check_err(Workspace& w, cudaStream_t st) {
     int e = 0;
     CK(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -634,6 +672,7 @@ pget_status check_params(const pget_lm_params* p) {
         return fail(PGET_EINVAL, "alpha_decay must be 0 or >= 1 and alpha_decay_iters >= 0");
     if (p->geo_mask && (!(p->geo_alpha_lambda >= 0) || !(p->geo_alpha_mu >= 0) || !std::isfinite(p->geo_mu_water)))
         return fail(PGET_EINVAL, "geometry prior weights must be >= 0");
+    if (p->inner_solver != 0 && p->inner_solver != 1) return fail(PGET_EINVAL, "inner_solver must be 0 or 1");
     return PGET_OK;
 }
 
@@ -717,7 +756,8 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
         reg_weights<T>(u + nn, n, p.tv_eps, (T*)w.Wm, skip_grad, st);
         CK(op_vjp<T>(w, w.pk_u, w.U, w.r, ga, skip_grad, st));
         // step from the damped normal equations, rhs = -grad
-        pget_status s = run_cg<T>(w, w.gr, -1.0, 0.0, &L->nu, pk, st);
+        pget_status s = pk.inner_solver == 1 ? run_sgp<T>(w, w.gr, 0.0, &L->nu, pk, st)
+                                             : run_cg<T>(w, w.gr, -1.0, 0.0, &L->nu, pk, st);
         if (s != PGET_OK) return s;
         lm_step<T>(u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, p.lambda_max, p.mu_max, st);
         pack_vec<T>(w, w.ut, w.pk_ut, nullptr, st);
@@ -1068,7 +1108,7 @@ static pget_status trial_impl(Workspace& w, const pget_lm_params& p, const void*
         if (!(nu > 0.0)) nu = 1.0;
         rep->nu0 = nu;
     }
-    s = run_cg<T>(w, w.gr, -1.0, nu, nullptr, p, st);
+    s = p.inner_solver == 1 ? run_sgp<T>(w, w.gr, nu, nullptr, p, st) : run_cg<T>(w, w.gr, -1.0, nu, nullptr, p, st);
     if (s != PGET_OK) return s;
     lm_step<T>((const T*)w.u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, p.lambda_max, p.mu_max, st);
     double pred = 0.0, ft = 0.0;
@@ -1221,6 +1261,7 @@ void pget_default_params(pget_lm_params* o) {
     o->geo_alpha_mu = 0.0;
     o->geo_mu_water = 0.0;
     o->geo_mask = nullptr;
+    o->inner_solver = 0;
 }
 
 pget_status pget_create(pget_ctx** ctx, int device, size_t budget) {

@@ -607,6 +607,130 @@ void lm_refresh_f(LmState* L, cudaStream_t st) {
     note_launch();
 }
 
+// ------------------------------------------------------- gradient projection
+// min_s <g, s> + 1/2 s^T A s subject to u + s in the box (A = J^T J + H + nu I), from s = 0:
+// d = P_box(u + s - alpha grad q) - u - s, exact line search on [0, 1] for the quadratic,
+// alternating Barzilai-Borwein lengths; stop on the unit-step projected gradient.
+template <typename T>
+__global__ void sgp_init_kernel(const T* __restrict__ g, T* __restrict__ gq, T* __restrict__ x, size_t m, double tol,
+                                CgState* cg) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+        x[i] = T(0);
+        gq[i] = g[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cg->stop = 0;
+        cg->iters = 0;
+        cg->tol = tol;
+        cg->alpha = 1.0;
+        cg->bnorm = -1.0;
+    }
+}
+
+template <typename T>
+__global__ void sgp_dir_kernel(const T* __restrict__ u, const T* __restrict__ x, const T* __restrict__ gq,
+                               T* __restrict__ d, size_t nn, double lmax, double mmax, double* __restrict__ p_pg,
+                               double* __restrict__ p_gd, double* __restrict__ p_dd, const CgState* cg) {
+    if (cg->stop) return;
+    const T al = (T)cg->alpha;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * nn; i += (size_t)gridDim.x * blockDim.x) {
+        const T hi = (T)(i < nn ? lmax : mmax);
+        const T ui = u[i], xi = x[i], gi = gq[i];
+        T v1 = ui + xi - gi;
+        v1 = v1 < T(0) ? T(0) : (v1 > hi ? hi : v1);
+        const T z1 = (v1 - ui) - xi;
+        T v = ui + xi - al * gi;
+        v = v < T(0) ? T(0) : (v > hi ? hi : v);
+        const T di = (v - ui) - xi;
+        d[i] = di;
+        a += (double)z1 * (double)z1;
+        b += (double)gi * (double)di;
+        c += (double)di * (double)di;
+    }
+    const double sa = block_sum(a);
+    const double sb = block_sum(b);
+    const double sc = block_sum(c);
+    if (threadIdx.x == 0) {
+        p_pg[blockIdx.x] = sa;
+        p_gd[blockIdx.x] = sb;
+        p_dd[blockIdx.x] = sc;
+    }
+}
+
+__global__ void sgp_check_kernel(const double* __restrict__ p_pg, const double* __restrict__ p_gd,
+                                 const double* __restrict__ p_dd, CgState* cg) {
+    if (cg->stop) return;
+    const double pg2 = warp_sum_partials(p_pg);
+    const double gd = warp_sum_partials(p_gd);
+    const double dd = warp_sum_partials(p_dd);
+    if (threadIdx.x) return;
+    const double pg = sqrt(pg2);
+    if (cg->bnorm < 0.0) cg->bnorm = pg;
+    cg->rr = pg;
+    cg->pq = gd;
+    cg->dd = dd;
+    if (pg <= cg->tol * cg->bnorm || cg->bnorm == 0.0 || !(gd < 0.0)) cg->stop = 1;
+}
+
+__global__ void sgp_step_kernel(const double* __restrict__ p_dAd, const double* __restrict__ p_AdAd, CgState* cg) {
+    if (cg->stop) return;
+    const double dAd = warp_sum_partials(p_dAd);
+    const double AdAd = warp_sum_partials(p_AdAd);
+    if (threadIdx.x) return;
+    if (!(dAd > 0.0)) {
+        cg->stop = 1;
+        return;
+    }
+    double ls = -cg->pq / dAd;
+    if (ls > 1.0) ls = 1.0;
+    cg->beta = ls;
+    cg->iters += 1;
+    const double an = (cg->iters % 2) ? cg->dd / dAd : dAd / AdAd;
+    cg->alpha = fmin(fmax(an, 1e-10), 1e10);
+}
+
+template <typename T>
+__global__ void sgp_update_kernel(T* __restrict__ x, T* __restrict__ gq, const T* __restrict__ d,
+                                  const T* __restrict__ Ad, size_t m, const CgState* cg) {
+    if (cg->stop) return;
+    const T ls = (T)cg->beta;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+        x[i] += ls * d[i];
+        gq[i] += ls * Ad[i];
+    }
+}
+
+template <typename T>
+void sgp_init(const T* g, T* gq, T* x, size_t m, double tol, CgState* cg, cudaStream_t st) {
+    sgp_init_kernel<T><<<kRedBlocks, 256, 0, st>>>(g, gq, x, m, tol, cg);
+    note_launch();
+}
+template <typename T>
+void sgp_dir(const T* u, const T* x, const T* gq, T* d, size_t nn, double lmax, double mmax, double* p_pg,
+             double* p_gd, double* p_dd, CgState* cg, cudaStream_t st) {
+    sgp_dir_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, x, gq, d, nn, lmax, mmax, p_pg, p_gd, p_dd, cg);
+    sgp_check_kernel<<<1, 32, 0, st>>>(p_pg, p_gd, p_dd, cg);
+    note_launch(2);
+}
+void sgp_step(const double* p_dAd, const double* p_AdAd, CgState* cg, cudaStream_t st) {
+    sgp_step_kernel<<<1, 32, 0, st>>>(p_dAd, p_AdAd, cg);
+    note_launch();
+}
+template <typename T>
+void sgp_update(T* x, T* gq, const T* d, const T* Ad, size_t m, const CgState* cg, cudaStream_t st) {
+    sgp_update_kernel<T><<<kRedBlocks, 256, 0, st>>>(x, gq, d, Ad, m, cg);
+    note_launch();
+}
+template void sgp_init<float>(const float*, float*, float*, size_t, double, CgState*, cudaStream_t);
+template void sgp_init<double>(const double*, double*, double*, size_t, double, CgState*, cudaStream_t);
+template void sgp_dir<float>(const float*, const float*, const float*, float*, size_t, double, double, double*, double*,
+                             double*, CgState*, cudaStream_t);
+template void sgp_dir<double>(const double*, const double*, const double*, double*, size_t, double, double, double*,
+                              double*, double*, CgState*, cudaStream_t);
+template void sgp_update<float>(float*, float*, const float*, const float*, size_t, const CgState*, cudaStream_t);
+template void sgp_update<double>(double*, double*, const double*, const double*, size_t, const CgState*, cudaStream_t);
+
 // conditional copy (accepted trial becomes the iterate)
 template <typename T>
 __global__ void copy_if_kernel(T* __restrict__ dst, const T* __restrict__ src, size_t m, const int* flag) {

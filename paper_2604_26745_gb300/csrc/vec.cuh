@@ -11,8 +11,11 @@ namespace pget {
 
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs; fixed so reductions are deterministic
 
+// CG state; the gradient-projection solver reuses it: rr = |unit-step projected gradient|,
+// bnorm = its first value (< 0 before), pq = <grad q, d>, dd = |d|^2, alpha = step length,
+// beta = line-search step, iters and stop as for CG
 struct CgState {
-    double rr, pq, alpha, beta, bnorm, tol;
+    double rr, pq, alpha, beta, bnorm, tol, dd;
     int iters, stop;
 };
 
@@ -89,6 +92,15 @@ void lm_model(const T* s, const T* g, const T* Wl, const T* Wm, int n, double al
               double* pb, cudaStream_t st, const T* gmask = nullptr, double geo_l = 0.0, double geo_m = 0.0);
 void lm_decide(LmState* L, const LmParamsDev& P, cudaStream_t st);
 void lm_init_f(LmState* L, double nu0_scale, cudaStream_t st);
+// gradient projection on the box-constrained LM subproblem (see vec.cu)
+template <typename T>
+void sgp_init(const T* g, T* gq, T* x, size_t m, double tol, CgState* cg, cudaStream_t st);
+template <typename T>
+void sgp_dir(const T* u, const T* x, const T* gq, T* d, size_t nn, double lmax, double mmax, double* p_pg,
+             double* p_gd, double* p_dd, CgState* cg, cudaStream_t st);
+void sgp_step(const double* p_dAd, const double* p_AdAd, CgState* cg, cudaStream_t st);
+template <typename T>
+void sgp_update(T* x, T* gq, const T* d, const T* Ad, size_t m, const CgState* cg, cudaStream_t st);
 void lm_refresh_f(LmState* L, cudaStream_t st);
 template <typename T>
 void copy_if(T* dst, const T* src, size_t m, const int* flag, cudaStream_t st);

@@ -39,7 +39,8 @@ class pget_lm_params(C.Structure):
                 ("rho_lo", C.c_double), ("rho_hi", C.c_double), ("nu_min", C.c_double),
                 ("nu_max", C.c_double), ("precision", C.c_int32), ("alpha_decay_iters", C.c_int32),
                 ("alpha_decay", C.c_double), ("geo_alpha_lambda", C.c_double), ("geo_alpha_mu", C.c_double),
-                ("geo_mu_water", C.c_double), ("geo_mask", C.c_void_p)]
+                ("geo_mu_water", C.c_double), ("geo_mask", C.c_void_p), ("inner_solver", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class pget_lm_report(C.Structure):
