@@ -66,7 +66,9 @@ class Params(C.Structure):
         ("geo_mu_water", C.c_double),
         ("geo_mask", C.c_void_p),
         ("inner_solver", C.c_int32),
-        ("pad2", C.c_int32),
+        ("lin_constraint", C.c_int32),
+        ("lin_slope", C.c_double),
+        ("lin_offset", C.c_double),
     ]
 
 
@@ -125,6 +127,7 @@ def lib():
         L.og_set_vjp_chunks.argtypes = [C.c_int]
         L.og_lm_trial.argtypes = [gp, C.POINTER(Params), dp, dp, dp, C.c_double, dp, C.POINTER(Trial)]
         L.og_check_proposal.argtypes = [gp, C.POINTER(Params), dp, dp, dp, dp, dp, dp, C.POINTER(Check)]
+        L.og_project.argtypes = [C.POINTER(Params), C.c_int, dp, dp]
         _lib = L
     return _lib
 
@@ -200,7 +203,9 @@ def reg_apply(W, v, alpha) -> np.ndarray:
 
 def default_params(**kw) -> Params:
     """Parameters; geo_mask (an [n, n] array) switches on the geometry priors of Eq. (6)
-    with weights geo_alpha_lambda, geo_alpha_mu and water attenuation geo_mu_water."""
+    with weights geo_alpha_lambda, geo_alpha_mu and water attenuation geo_mu_water;
+    lin_constraint = 1 adds the per-pixel bound lambda <= lin_slope mu + lin_offset to the
+    box (Sec. 2.2)."""
     d = dict(alpha_lambda=1e-2, alpha_mu=1e-2, tv_eps=1e-3, lambda_max=2.0, mu_max=0.2,
              max_iters=10, cg_max_iters=50, cg_rel_tol=1e-10, nu0_scale=1e-3, nu_up=4.0,
              nu_down=0.5, eta=1e-3, rho_lo=0.25, rho_hi=0.75, nu_min=1e-12, nu_max=1e12,
@@ -216,6 +221,13 @@ def default_params(**kw) -> Params:
     return pr
 
 
+def project(pr: Params, lam, mu):
+    """Euclidean projection of every pixel's (lambda, mu) onto the constraint set."""
+    lam, mu = _f64(lam).copy(), _f64(mu).copy()
+    lib().og_project(C.byref(pr), lam.size, _p(lam), _p(mu))
+    return lam, mu
+
+
 def cg(g: Geom, pr: Params, lam, mu, Wl, Wm, nu, b):
     lam, mu, Wl, Wm, b = map(_f64, (lam, mu, Wl, Wm, b))
     x = np.zeros_like(b)
@@ -227,7 +239,7 @@ def cg(g: Geom, pr: Params, lam, mu, Wl, Wm, nu, b):
 
 
 def sgp(g: Geom, pr: Params, lam, mu, Wl, Wm, nu, grad):
-    """Gradient projection on the box-constrained LM subproblem: returns (s, iterations)."""
+    """Gradient projection on the constrained LM subproblem: returns (s, iterations)."""
     lam, mu, Wl, Wm, grad = map(_f64, (lam, mu, Wl, Wm, grad))
     s = np.zeros_like(grad)
     it = lib().og_sgp(C.byref(g), C.byref(pr), _p(lam), _p(mu), _p(Wl), _p(Wm), float(nu), _p(grad), _p(s))

@@ -30,8 +30,10 @@
  *   og_sgp       -- gradient projection on the box-constrained form of Eq. (9), the
  *                   inner solver Sec. 2.2 names (scaled gradient projection, identity
  *                   scaling, Barzilai-Borwein lengths, exact line search).
+ *   og_project   -- projection onto the constraint set of Eq. (6): the box, and with
+ *                   lin_constraint the per-pixel linear bound lambda <= k mu + b.
  *   og_lm        -- the trust-region LM iteration of Sec. 2.2: step from Eq. (9),
- *                   projection onto the box of Eq. (6), model m_k of Eq. (8), agreement
+ *                   projection onto the constraint set, model m_k of Eq. (8), agreement
  *                   ratio rho of Eq. (12), acceptance rho > eta with eta in (0, 1/4);
  *                   optionally with the continuation alpha^(k) = alpha / 5^k of Sec. 3.1.
  *   og_lm_trial  -- one trial of that iteration at a given point and damping, returning
@@ -446,7 +448,8 @@ typedef struct {
     double geo_alpha_lambda, geo_alpha_mu, geo_mu_water;
     const double* geo_mask;  /* [n][n] potential rod locations in [0, 1], or NULL */
     int32_t inner_solver;    /* 0: CG on Eq. (9) then projection; 1: gradient projection */
-    int32_t pad2;
+    int32_t lin_constraint;  /* 1: add the per-pixel linear bound lambda <= lin_slope mu + lin_offset */
+    double lin_slope, lin_offset;
 } og_params;
 
 /* Geometry priors of Eq. (6): alpha_1 |P1 lambda|^2 + alpha_2 |P2 mu|^2 with the
@@ -581,15 +584,46 @@ int og_cg(const og_geom* g, const og_params* pr, const double* lam, const double
 
 static double og_clamp(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* Euclidean projection of one pixel's pair (lambda, mu) onto the constraint set of
+ * Sec. 2.2: the box [0, lambda_max] x [0, mu_max] and, with lin_constraint, the linear
+ * bound lambda <= k mu + b (k = lin_slope >= 0, b = lin_offset >= 0: no strongly emitting
+ * pixel with low attenuation).  The set is a convex polygon.  If the box projection meets
+ * the linear bound it is the answer (the nearest point of a larger set, lying in the
+ * smaller one).  Otherwise the bound is active at the answer, which is then the nearest
+ * point of the segment of the line lambda = k t + b, mu = t that lies in the box:
+ * t = ((lambda - b) k + mu) / (k^2 + 1) (the foot of the perpendicular), clamped to
+ * 0 <= t <= mu_max and k t + b <= lambda_max. */
+static void og_project_px(const og_params* pr, double* l, double* m) {
+    double pl = og_clamp(*l, 0.0, pr->lambda_max), pm = og_clamp(*m, 0.0, pr->mu_max);
+    if (pr->lin_constraint && pl - pr->lin_slope * pm > pr->lin_offset) {
+        double k = pr->lin_slope, b = pr->lin_offset;
+        double t = ((*l - b) * k + *m) / (k * k + 1.0);
+        double t_hi = pr->mu_max;
+        if (k > 0.0 && (pr->lambda_max - b) / k < t_hi) t_hi = (pr->lambda_max - b) / k;
+        t = og_clamp(t, 0.0, t_hi);
+        pl = k * t + b;
+        pm = t;
+    }
+    *l = pl;
+    *m = pm;
+}
+
+/* Projection of a pair of images (in place). */
+void og_project(const og_params* pr, int np, double* lam, double* mu) {
+    for (int i = 0; i < np; ++i) og_project_px(pr, &lam[i], &mu[i]);
+}
+
 /* Gradient projection for the box-constrained LM subproblem of Sec. 2.2 (the scaled
  * gradient projection method the paper cites, with the identity scaling):
  *   min_s q(s) = <g, s> + 1/2 s^T (J^T J + H + nu I) s   subject to  u + s in the box,
- * from s = 0.  Iteration: d = P_box(u + s - alpha grad q(s)) - u - s; exact line search on
+ * from s = 0.  Iteration: d = P(u + s - alpha grad q(s)) - u - s; exact line search on
  * [0, 1] for the quadratic q along d; alpha alternates the two Barzilai-Borwein lengths
  * |d|^2 / <d, A d> and <d, A d> / |A d|^2, clamped to [1e-10, 1e10].  Stops after
  * cg_max_iters iterations or when the unit-step projected gradient
- * |P_box(u + s - grad q) - u - s| <= cg_rel_tol times its value at s = 0.
- * Returns iterations run; s_out is feasible (u + s in the box). */
+ * |P(u + s - grad q) - u - s| <= cg_rel_tol times its value at s = 0.  P is the projection
+ * onto the box.
+ * With lin_constraint P projects onto the box and the linear bound (og_project_px).
+ * Returns iterations run; s_out is feasible (u + s in the constraint set). */
 int og_sgp(const og_geom* g, const og_params* pr, const double* lam, const double* mu,
            const double* Wl, const double* Wm, double nu, const double* grad_f, double* s_out) {
     og_ctx o;
@@ -608,12 +642,16 @@ int og_sgp(const og_geom* g, const og_params* pr, const double* lam, const doubl
     for (it = 0; it < pr->cg_max_iters;) {
         /* unit-step projected gradient (stopping measure) and the projected step */
         double pg = 0.0;
-        for (int i = 0; i < m; ++i) {
-            double ui = i < np ? lam[i] : mu[i - np];
-            double hi = i < np ? pr->lambda_max : pr->mu_max;
-            double z1 = og_clamp(ui + x[i] - gq[i], 0.0, hi) - ui - x[i];
-            pg += z1 * z1;
-            d[i] = og_clamp(ui + x[i] - alpha * gq[i], 0.0, hi) - ui - x[i];
+        for (int i = 0; i < np; ++i) {
+            double z1l = lam[i] + x[i] - gq[i], z1m = mu[i] + x[np + i] - gq[np + i];
+            og_project_px(pr, &z1l, &z1m);
+            z1l -= lam[i] + x[i];
+            z1m -= mu[i] + x[np + i];
+            pg += z1l * z1l + z1m * z1m;
+            double zl = lam[i] + x[i] - alpha * gq[i], zm = mu[i] + x[np + i] - alpha * gq[np + i];
+            og_project_px(pr, &zl, &zm);
+            d[i] = zl - lam[i] - x[i];
+            d[np + i] = zm - mu[i] - x[np + i];
         }
         pg = sqrt(pg);
         if (pg0 < 0.0) pg0 = pg;
@@ -679,11 +717,12 @@ static void og_gradient(const og_geom* g, const og_params* pr, const double* lam
 
 /* Levenberg-Marquardt trust-region iteration, Sec. 2.2 and Sec. 3.1:
  *   delta from CG on (J^T J + H + nu I) delta = -grad            (Eq. (9), nu = beta_k)
- *   s = P_box(u + delta) - u                                       (constraint set of Eq. (6))
+ *   s = P_C(u + delta) - u      (constraint set of Eq. (6): the box, and the linear bound if set)
  *   m_k(0) - m_k(s) = -<s, grad> - |J s|^2 / 2 - s^T H s / 2      (Eq. (8))
  *   rho = (f(u) - f(u + s)) / (m_k(0) - m_k(s))                   (Eq. (12))
  *   accept iff rho > eta; nu <- nu_up nu if rho < rho_lo, nu <- nu nu_down if rho > rho_hi.
- * lam, mu hold the initial guess on entry (projected onto the box) and the result on exit. */
+ * lam, mu hold the initial guess on entry (projected onto the constraint set) and the result
+ * on exit. */
 int og_lm(const og_geom* gin, const og_params* pr, const double* y, double* lam, double* mu,
           og_report* rep) {
     og_ctx o;
@@ -704,10 +743,7 @@ int og_lm(const og_geom* gin, const og_params* pr, const double* y, double* lam,
     double* tmp = malloc(sizeof(double) * np);
     double* Hs = malloc(sizeof(double) * np);
 
-    for (int i = 0; i < np; ++i) {
-        lam[i] = og_clamp(lam[i], 0.0, pr->lambda_max);
-        mu[i] = og_clamp(mu[i], 0.0, pr->mu_max);
-    }
+    og_project(pr, np, lam, mu);
     double f = og_objective(g, pr, lam, mu, y, r);
     og_reg_weights(n, pr->tv_eps, lam, Wl);
     og_reg_weights(n, pr->tv_eps, mu, Wm);
@@ -747,8 +783,9 @@ int og_lm(const og_geom* gin, const og_params* pr, const double* y, double* lam,
         rep->cg_iters_total += it;
         /* projected step */
         for (int i = 0; i < np; ++i) {
-            ut[i] = og_clamp(lam[i] + delta[i], 0.0, pr->lambda_max);
-            ut[np + i] = og_clamp(mu[i] + delta[np + i], 0.0, pr->mu_max);
+            ut[i] = lam[i] + delta[i];
+            ut[np + i] = mu[i] + delta[np + i];
+            og_project_px(pr, &ut[i], &ut[np + i]);
             s[i] = ut[i] - lam[i];
             s[np + i] = ut[np + i] - mu[i];
         }
@@ -840,8 +877,9 @@ static double og_model_decrease(const og_geom* g, const og_params* pr, const dou
 
 /* One trust-region trial of the LM iteration at the feasible point u = (lam, mu) with
  * damping nu (nu <= 0: nu_0 = nu0_scale |J g|^2 / |g|^2 at u, as at the start of og_lm):
- * the step s = P_box(u + delta) - u of Eq. (9), its model decrease, the actual decrease,
- * rho of Eq. (12), the acceptance rho > eta and the next damping (before clamping).
+ * the step s = P(u + delta) - u of Eq. (9) (P: projection onto the constraint set), its
+ * model decrease, the actual decrease, rho of Eq. (12), the acceptance rho > eta and the
+ * next damping (before clamping).
  * u is not changed: this is the "s_k = LMA(u_k)" of Alg. 2, whose caller decides. */
 int og_lm_trial(const og_geom* gin, const og_params* pr, const double* y, const double* lam,
                 const double* mu, double nu, double* s, og_trial* out) {
@@ -881,8 +919,9 @@ int og_lm_trial(const og_geom* gin, const og_params* pr, const double* y, const 
         out->cg_iters = og_cg(g, pr, lam, mu, Wl, Wm, nu, rhs, delta);
     }
     for (int i = 0; i < np; ++i) {
-        ut[i] = og_clamp(lam[i] + delta[i], 0.0, pr->lambda_max);
-        ut[np + i] = og_clamp(mu[i] + delta[np + i], 0.0, pr->mu_max);
+        ut[i] = lam[i] + delta[i];
+        ut[np + i] = mu[i] + delta[np + i];
+        og_project_px(pr, &ut[i], &ut[np + i]);
         s[i] = ut[i] - lam[i];
         s[np + i] = ut[np + i] - mu[i];
     }
@@ -910,8 +949,8 @@ int og_lm_trial(const og_geom* gin, const og_params* pr, const double* y, const 
 }
 
 /* The convergence check of Prop. conv_check / Alg. 2 for a proposal u~ = (pl, pm) made
- * at the feasible point u with the LM step s_k: with s~ = P_box(u~) - u (the proposal
- * projected onto the constraint box, as the LM step is),
+ * at the feasible point u with the LM step s_k: with s~ = P(u~) - u (the proposal
+ * projected onto the constraint set, as the LM step is),
  *   accept u~ iff rho(s~) > eta and m_k(s~) <= m_k(s_k),
  * m_k(s~) <= m_k(s_k) being m_k(0) - m_k(s~) >= m_k(0) - m_k(s_k); rho as in Eq. (12)
  * (-inf when the model predicts no decrease). */
@@ -937,8 +976,9 @@ int og_check_proposal(const og_geom* gin, const og_params* pr, const double* y, 
     og_reg_weights(n, pr->tv_eps, mu, Wm);
     og_gradient(g, pr, lam, mu, r, Wl, Wm, grad, tmp);
     for (int i = 0; i < np; ++i) {
-        ut[i] = og_clamp(pl[i], 0.0, pr->lambda_max);
-        ut[np + i] = og_clamp(pm[i], 0.0, pr->mu_max);
+        ut[i] = pl[i];
+        ut[np + i] = pm[i];
+        og_project_px(pr, &ut[i], &ut[np + i]);
         sp[i] = ut[i] - lam[i];
         sp[np + i] = ut[np + i] - mu[i];
     }
