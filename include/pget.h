@@ -100,12 +100,19 @@ typedef struct {
     double geo_alpha_lambda, geo_alpha_mu, geo_mu_water;
     const void* geo_mask;
     /* inner solver of the LM step (Sec. 2.2): 0 = CG on Eq. (9), then projection of
-     * u + delta onto the box (default); 1 = gradient projection on the box-constrained
-     * subproblem (the scaled gradient projection the paper names, identity scaling,
-     * Barzilai-Borwein lengths, exact line search), capped by cg_max_iters and stopped
-     * when the unit-step projected gradient falls below cg_rel_tol times its first value */
+     * u + delta onto the constraint set (default); 1 = gradient projection on the
+     * constrained subproblem (the scaled gradient projection the paper names, identity
+     * scaling, Barzilai-Borwein lengths, exact line search), capped by cg_max_iters and
+     * stopped when the unit-step projected gradient falls below cg_rel_tol times its
+     * first value */
     int32_t inner_solver;
-    int32_t reserved;
+    /* linear bound of the constraint set (Sec. 2.2: no strongly emitting pixel of low
+     * attenuation): 1 adds lambda <= lin_slope mu + lin_offset per pixel to the box
+     * (lin_slope, lin_offset >= 0, finite); 0 = box only (default).  Every projection
+     * (start, step, gradient projection, proposals) is then the Euclidean projection of
+     * each pixel's pair (lambda, mu) onto the polygon box & bound. */
+    int32_t lin_constraint;
+    double lin_slope, lin_offset;
 } pget_lm_params;
 
 #define PGET_TRACE 256
@@ -239,6 +246,14 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
                                 const void* y, const void* lam, const void* mu,
                                 const void* s_step, const void* prop_lam, const void* prop_mu,
                                 pget_check_report* rep, void* stream);
+
+/* Projection onto the constraint set of p (Sec. 2.2): every pixel's pair (lambda, mu)
+ * is replaced, in place, by its Euclidean projection onto the box [0, lambda_max] x
+ * [0, mu_max], intersected with lambda <= lin_slope mu + lin_offset when p->lin_constraint
+ * is set.  lam, mu: [n][n] device arrays in the element type of p->precision (caller-
+ * owned).  Asynchronous on the stream; PGET_EINVAL for null pointers, n < 1 or invalid
+ * parameters. */
+pget_status pget_project(pget_ctx* ctx, const pget_lm_params* p, int32_t n, void* lam, void* mu, void* stream);
 
 /* As pget_lm_solve with HOST buffers (pinned or pageable): copies y_host to the device,
  * computes the initial guess (mu_init 0.01) when init_guess != 0 (else takes

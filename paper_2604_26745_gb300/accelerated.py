@@ -35,11 +35,12 @@ def params_at(p: P.pget_lm_params, k: int) -> P.pget_lm_params:
 
 def accelerated_solve(ctx: P.Context, g: P.pget_geometry, p: P.pget_lm_params, y: torch.Tensor,
                       lam: torch.Tensor, mu: torch.Tensor, G=None, iters: int | None = None):
-    """Run Alg. 2 from (lam, mu) (projected onto the box first); returns (lam, mu, history)
-    with one dict per iteration (trial scalars, check scalars, which update was taken)."""
+    """Run Alg. 2 from (lam, mu) (projected onto the constraint set first); returns
+    (lam, mu, history) with one dict per iteration (trial scalars, check scalars, which
+    update was taken).  Every projection runs in the library (pget_project)."""
     iters = p.max_iters if iters is None else iters
-    lam = lam.clamp(0.0, p.lambda_max).contiguous()
-    mu = mu.clamp(0.0, p.mu_max).contiguous()
+    proj = lambda a, b: P.pget_project(ctx, p, a.contiguous().clone(), b.contiguous().clone())
+    lam, mu = proj(lam, mu)
     nu, nu0 = 0.0, None
     s = lam.new_empty((2,) + tuple(lam.shape))
     history = []
@@ -55,12 +56,10 @@ def accelerated_solve(ctx: P.Context, g: P.pget_geometry, p: P.pget_lm_params, y
                 pl, pm = prop[0].contiguous(), prop[1].contiguous()
                 chk = P.pget_proposal_check(ctx, g, pk, y, lam, mu, s, pl, pm)
                 if chk["accept"]:
-                    lam = pl.clamp(0.0, p.lambda_max).contiguous()
-                    mu = pm.clamp(0.0, p.mu_max).contiguous()
+                    lam, mu = proj(pl, pm)
                     took = "proposal"
         if took == "step":
-            lam = (lam + s[0]).clamp(0.0, p.lambda_max).contiguous()
-            mu = (mu + s[1]).clamp(0.0, p.mu_max).contiguous()
+            lam, mu = proj(lam + s[0], mu + s[1])
         nu = min(max(tr["nu_next"], p.nu_min * nu0), p.nu_max * nu0)
         history.append({"k": k, "trial": tr, "check": chk, "took": took, "nu": nu})
     return lam, mu, history

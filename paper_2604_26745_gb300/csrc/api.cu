@@ -605,8 +605,14 @@ pget_status flags_status(int e) {
     return PGET_OK;
 }
 
+// the constraint set of the parameters: the box and the optional linear bound
+static Feas feas_of(const pget_lm_params& p) {
+    return make_feas(p.lambda_max, p.mu_max, p.lin_constraint, p.lin_slope, p.lin_offset);
+}
+
 // Gradient projection on min <g, s> + 1/2 s^T (J^T J + H + nu I) s subject to u + s in the
-// box, u the unpacked iterate in w.u (packed in pk_u), g in gvec; result (feasible) in w.x.
+// constraint set, u the unpacked iterate in w.u (packed in pk_u), g in gvec; result
+// (feasible) in w.x.
 // One J^T J product per iteration, like a CG step; the scalars live in w.lm->cg.
 template <typename T>
 pget_status run_sgp(Workspace& w, const void* gvec, double nu, const double* nu_dev, const pget_lm_params& p,
@@ -616,7 +622,7 @@ pget_status run_sgp(Workspace& w, const void* gvec, double nu, const double* nu_
     sgp_init<T>((const T*)gvec, (T*)w.res, (T*)w.x, m, p.cg_rel_tol, cg, st);
     const int* stop = &cg->stop;
     for (int it = 0; it < p.cg_max_iters; ++it) {
-        sgp_dir<T>((const T*)w.u, (const T*)w.x, (const T*)w.res, (T*)w.p, nn, p.lambda_max, p.mu_max, w.dpart[1],
+        sgp_dir<T>((const T*)w.u, (const T*)w.x, (const T*)w.res, (T*)w.p, nn, feas_of(p), w.dpart[1],
                    w.dpart[2], w.dpart[3], cg, st);
         pack_vec<T>(w, w.p, w.pk_p, stop, st);
         cudaError_t e = op_jvp(w, w.pk_u, w.pk_p, w.Jp, stop, st);
@@ -673,6 +679,10 @@ pget_status check_params(const pget_lm_params* p) {
     if (p->geo_mask && (!(p->geo_alpha_lambda >= 0) || !(p->geo_alpha_mu >= 0) || !std::isfinite(p->geo_mu_water)))
         return fail(PGET_EINVAL, "geometry prior weights must be >= 0");
     if (p->inner_solver != 0 && p->inner_solver != 1) return fail(PGET_EINVAL, "inner_solver must be 0 or 1");
+    if (p->lin_constraint != 0 && p->lin_constraint != 1) return fail(PGET_EINVAL, "lin_constraint must be 0 or 1");
+    if (p->lin_constraint && !(p->lin_slope >= 0.0 && std::isfinite(p->lin_slope) && p->lin_offset >= 0.0 &&
+                               std::isfinite(p->lin_offset)))
+        return fail(PGET_EINVAL, "linear bound: lin_slope and lin_offset must be finite and >= 0");
     return PGET_OK;
 }
 
@@ -699,7 +709,7 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
     const size_t nn = w.nn, M = w.M;
     const int n = w.g.n;
     LmState* L = w.lm;
-    clamp_box<T>((T*)w.u, nn, p.lambda_max, p.mu_max, st);
+    project_set<T>((T*)w.u, nn, feas_of(p), st);
     pack_vec<T>(w, w.u, w.pk_u, nullptr, st);
     T* u = (T*)w.u;
     // objective and gradient at u_0
@@ -759,7 +769,7 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
         pget_status s = pk.inner_solver == 1 ? run_sgp<T>(w, w.gr, 0.0, &L->nu, pk, st)
                                              : run_cg<T>(w, w.gr, -1.0, 0.0, &L->nu, pk, st);
         if (s != PGET_OK) return s;
-        lm_step<T>(u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, p.lambda_max, p.mu_max, st);
+        lm_step<T>(u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, feas_of(p), st);
         pack_vec<T>(w, w.ut, w.pk_ut, nullptr, st);
         pack_vec<T>(w, w.s, w.pk_p, nullptr, st);
         lm_model<T>((const T*)w.s, (const T*)w.gr, (const T*)w.Wl, (const T*)w.Wm, n, pk.alpha_lambda,
@@ -1110,7 +1120,7 @@ static pget_status trial_impl(Workspace& w, const pget_lm_params& p, const void*
     }
     s = p.inner_solver == 1 ? run_sgp<T>(w, w.gr, nu, nullptr, p, st) : run_cg<T>(w, w.gr, -1.0, nu, nullptr, p, st);
     if (s != PGET_OK) return s;
-    lm_step<T>((const T*)w.u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, p.lambda_max, p.mu_max, st);
+    lm_step<T>((const T*)w.u, (const T*)w.x, (T*)w.ut, (T*)w.s, nn, feas_of(p), st);
     double pred = 0.0, ft = 0.0;
     s = model_decrease<T>(w, p, w.s, &pred, st);
     if (s != PGET_OK) return s;
@@ -1150,7 +1160,7 @@ static pget_status check_impl(Workspace& w, const pget_lm_params& p, const void*
     if (s != PGET_OK) return s;
     CK(cudaMemcpyAsync(w.ut, pl, e * nn, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync((char*)w.ut + e * nn, pm, e * nn, cudaMemcpyDeviceToDevice, st));
-    clamp_box<T>((T*)w.ut, nn, p.lambda_max, p.mu_max, st);
+    project_set<T>((T*)w.ut, nn, feas_of(p), st);
     sub_dot<T>((const T*)w.ut, (const T*)w.u, (T*)w.s, 2 * nn, w.dpart[3], nullptr, st);
     s = model_decrease<T>(w, p, w.s, &pred_p, st);
     if (s != PGET_OK) return s;
@@ -1262,6 +1272,9 @@ void pget_default_params(pget_lm_params* o) {
     o->geo_mu_water = 0.0;
     o->geo_mask = nullptr;
     o->inner_solver = 0;
+    o->lin_constraint = 0;
+    o->lin_slope = 0.0;
+    o->lin_offset = 0.0;
 }
 
 pget_status pget_create(pget_ctx** ctx, int device, size_t budget) {
@@ -1444,6 +1457,21 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
     cudaStream_t st = (cudaStream_t)stream;
     return w->f64 ? check_impl<double>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st)
                   : check_impl<float>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st);
+}
+
+pget_status pget_project(pget_ctx* ctx, const pget_lm_params* p, int32_t n, void* lam, void* mu, void* stream) {
+    if (!ctx || !lam || !mu) return fail(PGET_EINVAL, "null argument");
+    if (n < 1) return fail(PGET_EINVAL, "n must be >= 1");
+    pget_status s = check_params(p);
+    if (s != PGET_OK) return s;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nn = (size_t)n * n;
+    if (p->precision == PGET_F64) project_pair<double>((double*)lam, (double*)mu, nn, feas_of(*p), st);
+    else project_pair<float>((float*)lam, (float*)mu, nn, feas_of(*p), st);
+    CK(cudaGetLastError());
+    return PGET_OK;
 }
 
 pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,

@@ -344,21 +344,48 @@ void sub_dot(const T* a, const T* b, T* out, size_t m, double* part, const int* 
 template void sub_dot<float>(const float*, const float*, float*, size_t, double*, const int*, cudaStream_t);
 template void sub_dot<double>(const double*, const double*, double*, size_t, double*, const int*, cudaStream_t);
 
+// Component c (0: lambda, 1: mu) of the Euclidean projection of the pixel pair (zl, zm)
+// onto the constraint set f.  The box clamp is the answer when it meets the linear bound
+// (or there is none); otherwise the bound is active and the answer is the nearest point
+// of its segment inside the box, lambda = k t + b, mu = t, with t the foot of the
+// perpendicular ((zl - b) k + zm) / (k^2 + 1) clamped to [0, t_hi].
 template <typename T>
-__global__ void clamp_kernel(T* __restrict__ u, size_t nn, double lmax, double mmax) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * nn; i += (size_t)gridDim.x * blockDim.x) {
-        const double hi = i < nn ? lmax : mmax;
-        T v = u[i];
-        u[i] = v < T(0) ? T(0) : (v > (T)hi ? (T)hi : v);
+__device__ __forceinline__ T project_comp(T zl, T zm, int c, const Feas& f) {
+    const T lh = (T)f.lmax, mh = (T)f.mmax;
+    T pl = zl < T(0) ? T(0) : (zl > lh ? lh : zl);
+    T pm = zm < T(0) ? T(0) : (zm > mh ? mh : zm);
+    const T k = (T)f.k, b = (T)f.b;
+    if (f.lin && pl - k * pm > b) {
+        T t = ((zl - b) * k + zm) / (T)f.den;
+        t = t < T(0) ? T(0) : (t > (T)f.t_hi ? (T)f.t_hi : t);
+        pl = k * t + b;
+        pm = t;
+    }
+    return c ? pm : pl;
+}
+
+// (lambda, mu) = P(lambda, mu) in place, one thread per pixel
+template <typename T>
+__global__ void project_kernel(T* __restrict__ ul, T* __restrict__ um, size_t nn, Feas f) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x) {
+        const T zl = ul[i], zm = um[i];
+        ul[i] = project_comp(zl, zm, 0, f);
+        um[i] = project_comp(zl, zm, 1, f);
     }
 }
 template <typename T>
-void clamp_box(T* u, size_t nn, double lmax, double mmax, cudaStream_t st) {
-    clamp_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, nn, lmax, mmax);
+void project_pair(T* lam, T* mu, size_t nn, const Feas& f, cudaStream_t st) {
+    project_kernel<T><<<kRedBlocks, 256, 0, st>>>(lam, mu, nn, f);
     note_launch();
 }
-template void clamp_box<float>(float*, size_t, double, double, cudaStream_t);
-template void clamp_box<double>(double*, size_t, double, double, cudaStream_t);
+template <typename T>
+void project_set(T* u, size_t nn, const Feas& f, cudaStream_t st) {
+    project_pair<T>(u, u + nn, nn, f, st);
+}
+template void project_set<float>(float*, size_t, const Feas&, cudaStream_t);
+template void project_pair<float>(float*, float*, size_t, const Feas&, cudaStream_t);
+template void project_set<double>(double*, size_t, const Feas&, cudaStream_t);
+template void project_pair<double>(double*, double*, size_t, const Feas&, cudaStream_t);
 
 template <typename T>
 __global__ void fill_kernel(T* __restrict__ u, size_t m, double v) {
@@ -489,25 +516,31 @@ template void cg_pupdate<float>(float*, const float*, size_t, const CgState*, cu
 template void cg_pupdate<double>(double*, const double*, size_t, const CgState*, cudaStream_t);
 
 // ------------------------------------------------------------- trust region
-// ut = P_box(u + x), s = ut - u
+// ut = P(u + x), s = ut - u (P: projection onto the constraint set)
 template <typename T>
 __global__ void lm_step_kernel(const T* __restrict__ u, const T* __restrict__ x, T* __restrict__ ut,
-                               T* __restrict__ s, size_t nn, double lmax, double mmax) {
+                               T* __restrict__ s, size_t nn, Feas f) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * nn; i += (size_t)gridDim.x * blockDim.x) {
-        const T hi = (T)(i < nn ? lmax : mmax);
         T v = u[i] + x[i];
-        v = v < T(0) ? T(0) : (v > hi ? hi : v);
+        if (f.lin) {  // the pair of this pixel: the other component is at i -/+ nn
+            const size_t o = i < nn ? i + nn : i - nn;
+            const T w = u[o] + x[o];
+            v = i < nn ? project_comp(v, w, 0, f) : project_comp(w, v, 1, f);
+        } else {
+            const T hi = (T)(i < nn ? f.lmax : f.mmax);
+            v = v < T(0) ? T(0) : (v > hi ? hi : v);
+        }
         ut[i] = v;
         s[i] = v - u[i];
     }
 }
 template <typename T>
-void lm_step(const T* u, const T* x, T* ut, T* s, size_t nn, double lmax, double mmax, cudaStream_t st) {
-    lm_step_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, x, ut, s, nn, lmax, mmax);
+void lm_step(const T* u, const T* x, T* ut, T* s, size_t nn, const Feas& f, cudaStream_t st) {
+    lm_step_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, x, ut, s, nn, f);
     note_launch();
 }
-template void lm_step<float>(const float*, const float*, float*, float*, size_t, double, double, cudaStream_t);
-template void lm_step<double>(const double*, const double*, double*, double*, size_t, double, double, cudaStream_t);
+template void lm_step<float>(const float*, const float*, float*, float*, size_t, const Feas&, cudaStream_t);
+template void lm_step<double>(const double*, const double*, double*, double*, size_t, const Feas&, cudaStream_t);
 
 // partials of <s, g> (part_a) and <s, H s> (part_b), H = alpha grad^T W grad per field
 template <typename T>
@@ -629,19 +662,27 @@ __global__ void sgp_init_kernel(const T* __restrict__ g, T* __restrict__ gq, T* 
 
 template <typename T>
 __global__ void sgp_dir_kernel(const T* __restrict__ u, const T* __restrict__ x, const T* __restrict__ gq,
-                               T* __restrict__ d, size_t nn, double lmax, double mmax, double* __restrict__ p_pg,
+                               T* __restrict__ d, size_t nn, Feas f, double* __restrict__ p_pg,
                                double* __restrict__ p_gd, double* __restrict__ p_dd, const CgState* cg) {
     if (cg->stop) return;
     const T al = (T)cg->alpha;
     double a = 0.0, b = 0.0, c = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * nn; i += (size_t)gridDim.x * blockDim.x) {
-        const T hi = (T)(i < nn ? lmax : mmax);
         const T ui = u[i], xi = x[i], gi = gq[i];
         T v1 = ui + xi - gi;
-        v1 = v1 < T(0) ? T(0) : (v1 > hi ? hi : v1);
-        const T z1 = (v1 - ui) - xi;
         T v = ui + xi - al * gi;
-        v = v < T(0) ? T(0) : (v > hi ? hi : v);
+        if (f.lin) {  // project the pixel's pair; the other component is at i -/+ nn
+            const size_t o = i < nn ? i + nn : i - nn;
+            const T uo = u[o], xo = x[o], go = gq[o];
+            const T w1 = uo + xo - go, w = uo + xo - al * go;
+            v1 = i < nn ? project_comp(v1, w1, 0, f) : project_comp(w1, v1, 1, f);
+            v = i < nn ? project_comp(v, w, 0, f) : project_comp(w, v, 1, f);
+        } else {
+            const T hi = (T)(i < nn ? f.lmax : f.mmax);
+            v1 = v1 < T(0) ? T(0) : (v1 > hi ? hi : v1);
+            v = v < T(0) ? T(0) : (v > hi ? hi : v);
+        }
+        const T z1 = (v1 - ui) - xi;
         const T di = (v - ui) - xi;
         d[i] = di;
         a += (double)z1 * (double)z1;
@@ -707,9 +748,9 @@ void sgp_init(const T* g, T* gq, T* x, size_t m, double tol, CgState* cg, cudaSt
     note_launch();
 }
 template <typename T>
-void sgp_dir(const T* u, const T* x, const T* gq, T* d, size_t nn, double lmax, double mmax, double* p_pg,
+void sgp_dir(const T* u, const T* x, const T* gq, T* d, size_t nn, const Feas& f, double* p_pg,
              double* p_gd, double* p_dd, CgState* cg, cudaStream_t st) {
-    sgp_dir_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, x, gq, d, nn, lmax, mmax, p_pg, p_gd, p_dd, cg);
+    sgp_dir_kernel<T><<<kRedBlocks, 256, 0, st>>>(u, x, gq, d, nn, f, p_pg, p_gd, p_dd, cg);
     sgp_check_kernel<<<1, 32, 0, st>>>(p_pg, p_gd, p_dd, cg);
     note_launch(2);
 }
@@ -724,9 +765,9 @@ void sgp_update(T* x, T* gq, const T* d, const T* Ad, size_t m, const CgState* c
 }
 template void sgp_init<float>(const float*, float*, float*, size_t, double, CgState*, cudaStream_t);
 template void sgp_init<double>(const double*, double*, double*, size_t, double, CgState*, cudaStream_t);
-template void sgp_dir<float>(const float*, const float*, const float*, float*, size_t, double, double, double*, double*,
+template void sgp_dir<float>(const float*, const float*, const float*, float*, size_t, const Feas&, double*, double*,
                              double*, CgState*, cudaStream_t);
-template void sgp_dir<double>(const double*, const double*, const double*, double*, size_t, double, double, double*,
+template void sgp_dir<double>(const double*, const double*, const double*, double*, size_t, const Feas&, double*,
                               double*, double*, CgState*, cudaStream_t);
 template void sgp_update<float>(float*, float*, const float*, const float*, size_t, const CgState*, cudaStream_t);
 template void sgp_update<double>(double*, double*, const double*, const double*, size_t, const CgState*, cudaStream_t);

@@ -19,6 +19,19 @@ struct CgState {
     int iters, stop;
 };
 
+// Constraint set of one pixel's pair (lambda, mu), Sec. 2.2: the box [0, lmax] x [0, mmax]
+// and, when lin is set, the linear bound lambda <= k mu + b (k, b >= 0).  t_hi is the
+// largest mu of the bound's segment inside the box, den = k^2 + 1.
+struct Feas {
+    double lmax, mmax, k, b, t_hi, den;
+    int lin;
+};
+inline Feas make_feas(double lmax, double mmax, int lin, double k, double b) {
+    Feas f{lmax, mmax, k, b, mmax, k * k + 1.0, lin};
+    if (k > 0.0 && (lmax - b) / k < f.t_hi) f.t_hi = (lmax - b) / k;
+    return f;
+}
+
 struct LmState {
     double f, f0, nu, nu0;
     double sg, sHs, JsJs, rtrt, Rl, Rm, gg;
@@ -73,8 +86,11 @@ void reduce_views(const T* gpart, const int* vtrans, int n, int n_views, int gro
                   const RedArgs<T>& ra, bool kahan, cudaStream_t st);
 template <typename T>
 void sub_dot(const T* a, const T* b, T* out, size_t m, double* part, const int* skip, cudaStream_t st);
+// projection onto the constraint set, in place: stacked [lambda; mu] / separate images
 template <typename T>
-void clamp_box(T* u, size_t nn, double lmax, double mmax, cudaStream_t st);
+void project_set(T* u, size_t nn, const Feas& f, cudaStream_t st);
+template <typename T>
+void project_pair(T* lam, T* mu, size_t nn, const Feas& f, cudaStream_t st);
 template <typename T>
 void fill(T* u, size_t m, double v, cudaStream_t st);
 template <typename T>
@@ -86,7 +102,7 @@ void cg_update(T* x, T* res, const T* p, const T* q, size_t m, double* part, CgS
 template <typename T>
 void cg_pupdate(T* p, const T* res, size_t m, const CgState* cg, cudaStream_t st);
 template <typename T>
-void lm_step(const T* u, const T* x, T* ut, T* s, size_t nn, double lmax, double mmax, cudaStream_t st);
+void lm_step(const T* u, const T* x, T* ut, T* s, size_t nn, const Feas& f, cudaStream_t st);
 template <typename T>
 void lm_model(const T* s, const T* g, const T* Wl, const T* Wm, int n, double al, double am, double* pa,
               double* pb, cudaStream_t st, const T* gmask = nullptr, double geo_l = 0.0, double geo_m = 0.0);
@@ -96,7 +112,7 @@ void lm_init_f(LmState* L, double nu0_scale, cudaStream_t st);
 template <typename T>
 void sgp_init(const T* g, T* gq, T* x, size_t m, double tol, CgState* cg, cudaStream_t st);
 template <typename T>
-void sgp_dir(const T* u, const T* x, const T* gq, T* d, size_t nn, double lmax, double mmax, double* p_pg,
+void sgp_dir(const T* u, const T* x, const T* gq, T* d, size_t nn, const Feas& f, double* p_pg,
              double* p_gd, double* p_dd, CgState* cg, cudaStream_t st);
 void sgp_step(const double* p_dAd, const double* p_AdAd, CgState* cg, cudaStream_t st);
 template <typename T>

@@ -371,9 +371,17 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                 const float fi = ((float)Xc - X00f) * dXrf * invR2 + ((float)Yr - Y00f) * dYrf * invR2;
                 const int ilo = max(0, (int)ceilf(fi - wI - wa)), ihi = min(wn - 1, (int)floorf(fi + wI - wa));
                 T2 acc = mk2(T(0), T(0));
-                for (int t = ilo; t <= ihi; ++t) {  // window columns of the candidate rays
-                    const int k = Xc - (int)C0[rl * nth + t];
-                    if ((unsigned)k < (unsigned)SW) acc = add2(acc, ST[(rl * SW + k) * nth + t]);
+                const short* c0r = C0 + rl * nth;
+                const T2* str = ST + (size_t)rl * SW * nth;
+                // window columns of the candidate rays, two at a time (their loads are
+                // independent); the sum keeps the order of t
+                for (int t = ilo; t <= ihi; t += 2) {
+                    const bool two = t + 1 <= ihi;
+                    const int k0 = Xc - (int)c0r[t];
+                    const int k1 = two ? Xc - (int)c0r[t + 1] : -1;
+                    const T2 v0 = (unsigned)k0 < (unsigned)SW ? str[k0 * nth + t] : mk2(T(0), T(0));
+                    const T2 v1 = (unsigned)k1 < (unsigned)SW ? str[k1 * nth + t + 1] : mk2(T(0), T(0));
+                    acc = add2(add2(acc, v0), v1);
                 }
                 if (ck > 0 && Yr == row_hi + 1) acc = add2(acc, carry_rd[Xc]);
                 if (Yr == row_lo && ck < A.nchunks - 1) {

@@ -40,7 +40,7 @@ class pget_lm_params(C.Structure):
                 ("nu_max", C.c_double), ("precision", C.c_int32), ("alpha_decay_iters", C.c_int32),
                 ("alpha_decay", C.c_double), ("geo_alpha_lambda", C.c_double), ("geo_alpha_mu", C.c_double),
                 ("geo_mu_water", C.c_double), ("geo_mask", C.c_void_p), ("inner_solver", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("lin_constraint", C.c_int32), ("lin_slope", C.c_double), ("lin_offset", C.c_double)]
 
 
 class pget_lm_report(C.Structure):
@@ -102,6 +102,7 @@ _SIGS = {
                        _vp, C.POINTER(pget_trial_report), _vp], C.c_int),
     "pget_proposal_check": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp, _vp,
                              _vp, _vp, C.POINTER(pget_check_report), _vp], C.c_int),
+    "pget_project": ([_vp, C.POINTER(pget_lm_params), C.c_int32, _vp, _vp, _vp], C.c_int),
     "pget_lm_solve_host": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
                             _vp, C.c_int32, C.POINTER(pget_lm_report), _vp], C.c_int),
     "pget_submit": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp,
@@ -293,6 +294,17 @@ def pget_proposal_check(ctx: Context, g: pget_geometry, p: pget_lm_params, y, la
                                       _ptr(s_step), _ptr(prop_lam), _ptr(prop_mu), C.byref(rep),
                                       _stream(stream)), ctx.h)
     return _fields(rep)
+
+
+def pget_project(ctx: Context, p: pget_lm_params, lam, mu, stream=None):
+    """Project (lam, mu) in place onto the constraint set of p (box and optional linear
+    bound); lam, mu: contiguous [n, n] CUDA tensors of the precision's dtype."""
+    if lam.shape != mu.shape or lam.dim() != 2 or lam.shape[0] != lam.shape[1]:
+        raise ValueError("lam and mu must be square images of one shape")
+    if not (lam.is_contiguous() and mu.is_contiguous()):
+        raise ValueError("lam and mu must be contiguous")
+    _check(load().pget_project(ctx.h, C.byref(p), int(lam.shape[0]), _ptr(lam), _ptr(mu), _stream(stream)), ctx.h)
+    return lam, mu
 
 
 def pget_lm_solve(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam, mu, stream=None):
