@@ -147,11 +147,10 @@ struct Workspace {
     int tx_extra = 0;
     long long wait_ns = 0;
     // adjoint view groups: CTA g sums views group_view[group_off[g] .. group_off[g+1]),
-    // all of one canonical orientation (gtrans[g]), into partial image g
-    int n_groups = 0;
+    // all of one canonical orientation, into partial image g
+    int n_groups = 0, n_groups0 = 0;  // CTA groups in all / in the normal frame (listed first)
     int* d_group_off = nullptr;
     int* d_group_view = nullptr;
-    int* d_gtrans = nullptr;
     void* pk_u[2] = {nullptr, nullptr};
     void* pk_ut[2] = {nullptr, nullptr};
     void* pk_p[2] = {nullptr, nullptr};
@@ -359,6 +358,7 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
         }
     }
     w->n_groups = (int)gtrans.size();
+    w->n_groups0 = (int)std::count(gtrans.begin(), gtrans.end(), 0);  // normal-frame groups come first
     const size_t e = w->elt, e2 = 2 * e;
     (void)e2;
     CK(w->alloc(&w->d_views, sizeof(ViewDev) * V));
@@ -406,8 +406,6 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     CK(cudaMemcpy(w->d_group_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_group_view, sizeof(int) * gview.size()));
     CK(cudaMemcpy(w->d_group_view, gview.data(), sizeof(int) * gview.size(), cudaMemcpyHostToDevice));
-    CK(w->alloc(&w->d_gtrans, sizeof(int) * gtrans.size()));
-    CK(cudaMemcpy(w->d_gtrans, gtrans.data(), sizeof(int) * gtrans.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->part2, e * (size_t)groups * 2 * w->nn));
     for (int k = 0; k < 4; ++k) CK(w->alloc(&w->dpart[k], sizeof(double) * kRedBlocks));
     CK(w->alloc(&w->lm, sizeof(LmState)));
@@ -536,7 +534,7 @@ cudaError_t op_vjp(Workspace& w, void* const pku[2], const void* U, const void* 
     w.prof->begin(kPRed, st);
     // the view sum is already two-level (<= ~40 terms per level): plain sums suffice;
     // the Kahan compensation of PGET_F32_KAHAN applies along rays
-    reduce_views<T>((const T*)w.gpart, w.d_gtrans, w.g.n, w.n_groups, w.groups, (T*)w.part2, ra, false, st);
+    reduce_views<T>((const T*)w.gpart, w.g.n, w.n_groups, w.n_groups0, w.groups, (T*)w.part2, ra, false, st);
     w.prof->end(st);
     return cudaGetLastError();
 }

@@ -4,6 +4,7 @@
 // Vectors u = (lambda, mu) are planar [2][n][n] (lambda block, then mu block).  Dot
 // products accumulate in double per thread, per block (fixed tree) and over blocks in
 // block order (finish kernels), so every result is deterministic.
+#include <algorithm>
 #include <cmath>
 
 #include "kernels.cuh"
@@ -209,59 +210,64 @@ void finish_sum(const double* part, double* dst, const int* skip, cudaStream_t s
 
 // ---------------------------------------------------------------- view reduction
 // Stage 1: block (tile, view group) sums the partial images of its views over a 32 x 32
-// pixel tile.  Views with a transposed canonical frame wrote [ix][iy]; they are summed
-// in that orientation and transposed once through shared memory.
+// pixel tile.  The partial images come sorted by orientation: views [0, n0) wrote the
+// normal frame, views [n0, n_views) the transposed one ([ix][iy]).  Groups [0, g0) split
+// the first range, groups [g0, groups) the second, so every block sums one orientation
+// with no per-view test (its loads stay independent across the unrolled views); a
+// transposed block turns its tile once through shared memory.
 // (float: at most 64 registers, so that four 256-thread blocks fit an SM and the
 // tiles x groups grid of about 2 x 304 blocks runs in a single wave)
 template <typename T, bool KAHAN>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 && !KAHAN ? 4 : 3) reduce_views_kernel(const T* __restrict__ gpart, const int* __restrict__ vtrans, int n,
-                                    int n_views, int groups, T* __restrict__ out2, const int* skip) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 && !KAHAN ? 4 : 3)
+    reduce_views_kernel(const T* __restrict__ gpart, int n, int n_views, int n0, int groups, int g0,
+                        T* __restrict__ out2, const int* skip) {
     using T2 = typename Vec2<T>::type;
     if (skip && *skip) return;
     __shared__ T2 tile[32][33];
     const int tiles_x = (n + 31) / 32;
     const int tl = blockIdx.x % (tiles_x * tiles_x), grp = blockIdx.x / (tiles_x * tiles_x);
     const int bx = (tl % tiles_x) * 32, by = (tl / tiles_x) * 32;
-    const int v0 = (int)((long long)n_views * grp / groups), v1 = (int)((long long)n_views * (grp + 1) / groups);
+    const bool tr = grp >= g0;
+    const int c0 = tr ? n0 : 0, cn = tr ? n_views - n0 : n0;
+    const int gi = tr ? grp - g0 : grp, gn = tr ? groups - g0 : g0;
+    const int v0 = c0 + (int)((long long)cn * gi / gn), v1 = c0 + (int)((long long)cn * (gi + 1) / gn);
     const size_t nn = (size_t)n * n;
-    Acc<T, KAHAN> an[2][4], at[2][4];
+    Acc<T, KAHAN> a[2][4];
     for (int f = 0; f < 2; ++f)
-        for (int k = 0; k < 4; ++k) {
-            an[f][k].init();
-            at[f][k].init();
-        }
+        for (int k = 0; k < 4; ++k) a[f][k].init();
     const int tx = threadIdx.x, ty = threadIdx.y;
+    const int rb = tr ? bx : by, cb = tr ? by : bx;  // stored rows and columns of the tile
     constexpr int kUnroll = sizeof(T) == 4 && !KAHAN ? 4 : 2;  // loads in flight within 64 registers
 #pragma unroll kUnroll
     for (int v = v0; v < v1; ++v) {
         const T* gp = gpart + (size_t)v * 2 * nn;
-        if (!vtrans[v]) {
-            for (int k = 0; k < 4; ++k) {
-                int iy = by + ty + 8 * k, ix = bx + tx;
-                if (iy < n && ix < n) {
-                    an[0][k].add(gp[(size_t)iy * n + ix]);
-                    an[1][k].add(gp[nn + (size_t)iy * n + ix]);
-                }
-            }
-        } else {
-            for (int k = 0; k < 4; ++k) {
-                int rr = bx + ty + 8 * k, cc = by + tx;  // stored [ix][iy]
-                if (rr < n && cc < n) {
-                    at[0][k].add(gp[(size_t)rr * n + cc]);
-                    at[1][k].add(gp[nn + (size_t)rr * n + cc]);
-                }
+        for (int k = 0; k < 4; ++k) {
+            const int r = rb + ty + 8 * k, c = cb + tx;
+            if (r < n && c < n) {
+                a[0][k].add(gp[(size_t)r * n + c]);
+                a[1][k].add(gp[nn + (size_t)r * n + c]);
             }
         }
     }
-    for (int k = 0; k < 4; ++k) tile[ty + 8 * k][tx] = mk2(at[0][k].val(), at[1][k].val());
-    __syncthreads();
     T* o = out2 + (size_t)grp * 2 * nn;
-    for (int k = 0; k < 4; ++k) {
-        int iy = by + ty + 8 * k, ix = bx + tx;
-        if (iy < n && ix < n) {
-            T2 tv = tile[tx][ty + 8 * k];
-            o[(size_t)iy * n + ix] = an[0][k].val() + tv.x;
-            o[nn + (size_t)iy * n + ix] = an[1][k].val() + tv.y;
+    if (tr) {  // uniform per block
+        for (int k = 0; k < 4; ++k) tile[ty + 8 * k][tx] = mk2(a[0][k].val(), a[1][k].val());
+        __syncthreads();
+        for (int k = 0; k < 4; ++k) {
+            const int iy = by + ty + 8 * k, ix = bx + tx;
+            if (iy < n && ix < n) {
+                const T2 tv = tile[tx][ty + 8 * k];
+                o[(size_t)iy * n + ix] = tv.x;
+                o[nn + (size_t)iy * n + ix] = tv.y;
+            }
+        }
+    } else {
+        for (int k = 0; k < 4; ++k) {
+            const int iy = by + ty + 8 * k, ix = bx + tx;
+            if (iy < n && ix < n) {
+                o[(size_t)iy * n + ix] = a[0][k].val();
+                o[nn + (size_t)iy * n + ix] = a[1][k].val();
+            }
         }
     }
 }
@@ -302,14 +308,19 @@ __global__ void reduce_groups_kernel(RedArgs<T> a) {
 }
 
 template <typename T>
-void reduce_views(const T* gpart, const int* vtrans, int n, int n_views, int groups, T* part2,
-                  const RedArgs<T>& ra, bool kahan, cudaStream_t st) {
+void reduce_views(const T* gpart, int n, int n_views, int n0, int groups, T* part2, const RedArgs<T>& ra,
+                  bool kahan, cudaStream_t st) {
     const int tiles_x = (n + 31) / 32;
+    // groups per orientation in proportion to its views, at least one for each present
+    int g0 = n0 <= 0 ? 0 : (n0 >= n_views ? groups : (int)((long long)groups * n0 / n_views));
+    if (n0 > 0 && n0 < n_views) g0 = std::min(std::max(g0, 1), groups - 1);
     dim3 block(32, 8);
     if (kahan)
-        reduce_views_kernel<T, true><<<tiles_x * tiles_x * groups, block, 0, st>>>(gpart, vtrans, n, n_views, groups, part2, ra.skip);
+        reduce_views_kernel<T, true><<<tiles_x * tiles_x * groups, block, 0, st>>>(gpart, n, n_views, n0, groups, g0,
+                                                                                   part2, ra.skip);
     else
-        reduce_views_kernel<T, false><<<tiles_x * tiles_x * groups, block, 0, st>>>(gpart, vtrans, n, n_views, groups, part2, ra.skip);
+        reduce_views_kernel<T, false><<<tiles_x * tiles_x * groups, block, 0, st>>>(gpart, n, n_views, n0, groups, g0,
+                                                                                    part2, ra.skip);
     RedArgs<T> r2 = ra;
     r2.in2 = part2;
     r2.groups = groups;
@@ -319,8 +330,8 @@ void reduce_views(const T* gpart, const int* vtrans, int n, int n_views, int gro
         reduce_groups_kernel<T, false><<<kRedBlocks, 256, 0, st>>>(r2);
     note_launch(2);
 }
-template void reduce_views<float>(const float*, const int*, int, int, int, float*, const RedArgs<float>&, bool, cudaStream_t);
-template void reduce_views<double>(const double*, const int*, int, int, int, double*, const RedArgs<double>&, bool, cudaStream_t);
+template void reduce_views<float>(const float*, int, int, int, int, float*, const RedArgs<float>&, bool, cudaStream_t);
+template void reduce_views<double>(const double*, int, int, int, int, double*, const RedArgs<double>&, bool, cudaStream_t);
 
 // ------------------------------------------------------------------ elementwise
 template <typename T>

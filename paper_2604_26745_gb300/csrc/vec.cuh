@@ -82,8 +82,8 @@ template <typename T>
 void dot(const T* a, const T* b, size_t m, double* part, const int* skip, cudaStream_t st);
 void finish_sum(const double* part, double* dst, const int* skip, cudaStream_t st);
 template <typename T>
-void reduce_views(const T* gpart, const int* vtrans, int n, int n_views, int groups, T* part2,
-                  const RedArgs<T>& ra, bool kahan, cudaStream_t st);
+void reduce_views(const T* gpart, int n, int n_views, int n0, int groups, T* part2, const RedArgs<T>& ra,
+                  bool kahan, cudaStream_t st);
 template <typename T>
 void sub_dot(const T* a, const T* b, T* out, size_t m, double* part, const int* skip, cudaStream_t st);
 // projection onto the constraint set, in place: stacked [lambda; mu] / separate images
