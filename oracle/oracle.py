@@ -37,6 +37,8 @@ class Geom(C.Structure):
         ("fov_radius", C.c_double),
         ("det_pitch", C.c_double),
         ("interleave", C.c_int32),
+        ("depth_w", C.c_void_p),
+        ("depth_c", C.c_void_p),
     ]
 
 
@@ -142,9 +144,23 @@ def _f64(a) -> np.ndarray:
 
 
 def geom(n, n_angles, n_det, n_sub=1, collimator=1, n_banks=0, step=0.0, fov_radius=0.0,
-         det_pitch=0.0, interleave=1) -> Geom:
-    return Geom(n, n_angles, n_det, n_banks, n_sub, collimator, step, fov_radius, det_pitch,
-                interleave)
+         det_pitch=0.0, interleave=1, depth_w=None, depth_c=None) -> Geom:
+    """Geometry; depth_w, depth_c (arrays of length T, the samples per ray) are the depth
+    factors of Eq. (5): the emission weight and the attenuation factor of sample j."""
+    g = Geom(n, n_angles, n_det, n_banks, n_sub, collimator, step, fov_radius, det_pitch, interleave)
+    keep = []
+    for name, tab in (("depth_w", depth_w), ("depth_c", depth_c)):
+        if tab is not None:
+            a = _f64(tab)
+            setattr(g, name, a.ctypes.data)
+            keep.append(a)
+    g._keep = keep  # the tables must live as long as the geometry
+    if keep:
+        T = geom_info(g)["T"]
+        for a in keep:
+            if a.shape != (T,):
+                raise ValueError(f"depth tables need {T} entries (one per ray sample)")
+    return g
 
 
 def geom_info(g: Geom):

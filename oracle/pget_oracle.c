@@ -67,6 +67,12 @@ typedef struct {
     double fov_radius;   /* r_Omega (0: n / sqrt 2)                                   */
     double det_pitch;    /* p (0: 2 r_Omega / detectors per bank)                     */
     int32_t interleave;  /* 1: bank B shifted by p/2 (default); 0: no shift (test aid) */
+    /* depth factors of Eq. (5) over the sample index j of every ray (length T, or NULL
+     * for all ones): depth_w[j] scales the emission of sample j (the part of the
+     * detector response r_{m,n} that varies with the distance to the detector), depth_c[j]
+     * its attenuation exponent (the vertical-opening correction c_{m,n} >= 1) */
+    const double* depth_w;
+    const double* depth_c;
 } og_geom;
 
 typedef struct {
@@ -170,8 +176,13 @@ static double og_sample(const double* img, const int idx[4], const double wt[4])
 
 /* ------------------------------------------------------------- forward model */
 
-/* Ray sum of Eq. (1) on one ray: q = h sum_j lambda_j exp(-E_j),
- * E_j = h (mu_j / 2 + sum_{i > j} mu_i), i > j being nearer the detector. */
+/* depth factors of sample j (1 without tables) */
+static double og_dw(const og_ctx* o, int j) { return o->g.depth_w ? o->g.depth_w[j] : 1.0; }
+static double og_dc(const og_ctx* o, int j) { return o->g.depth_c ? o->g.depth_c[j] : 1.0; }
+
+/* Ray sum of Eq. (1) on one ray: q = h sum_j w_j lambda_j exp(-c_j E_j),
+ * E_j = h (mu_j / 2 + sum_{i > j} mu_i), i > j being nearer the detector, with the depth
+ * factors w_j, c_j of Eq. (5) (1 by default). */
 static double og_ray_sum(const og_ctx* o, const og_ray* ry, const double* lam, const double* mu) {
     double h = o->h, S = 0.0, q = 0.0;
     for (int j = o->T - 1; j >= 0; --j) {
@@ -182,7 +193,7 @@ static double og_ray_sum(const og_ctx* o, const og_ray* ry, const double* lam, c
         if (!og_bilinear(o, fx, fy, idx, wt)) continue;
         double l = og_sample(lam, idx, wt), m = og_sample(mu, idx, wt);
         double E = h * (S + 0.5 * m);
-        q += h * l * exp(-E);
+        q += h * og_dw(o, j) * l * exp(-og_dc(o, j) * E);
         S += m;
     }
     return q;
@@ -215,7 +226,7 @@ int og_forward(const og_geom* gin, const double* lam, const double* mu, double* 
 /* ------------------------------------------------------------------ JVP */
 
 /* Derivative of og_ray_sum along (dl, dm), Eq. (2):
- * q' = h sum_j exp(-E_j) (dl_j - lambda_j dE_j), dE_j = h (dm_j / 2 + sum_{i > j} dm_i). */
+ * q' = h sum_j w_j exp(-c_j E_j) (dl_j - lambda_j c_j dE_j), dE_j = h (dm_j / 2 + sum_{i > j} dm_i). */
 static double og_ray_jvp(const og_ctx* o, const og_ray* ry, const double* lam, const double* mu,
                          const double* dl, const double* dm) {
     double h = o->h, S = 0.0, dS = 0.0, q = 0.0;
@@ -229,7 +240,8 @@ static double og_ray_jvp(const og_ctx* o, const og_ray* ry, const double* lam, c
         double a = og_sample(dl, idx, wt), b = og_sample(dm, idx, wt);
         double E = h * (S + 0.5 * m);
         double dE = h * (dS + 0.5 * b);
-        q += h * exp(-E) * (a - l * dE);
+        double c = og_dc(o, j);
+        q += h * og_dw(o, j) * exp(-c * E) * (a - l * c * dE);
         S += m;
         dS += b;
     }
@@ -264,8 +276,8 @@ int og_jvp(const og_geom* gin, const double* lam, const double* mu, const double
 /* ------------------------------------------------------------------ VJP */
 
 /* Adjoint of og_ray_jvp for one ray with residual weight rho, scattered into gl, gm:
- *   d q / d lambda_j = h exp(-E_j)
- *   d q / d mu_i     = -h Q_i,  Q_i = sum_{j < i} h lambda_j exp(-E_j) + h lambda_i exp(-E_i) / 2
+ *   d q / d lambda_j = h w_j exp(-c_j E_j)
+ *   d q / d mu_i     = -h Q_i,  Q_i = sum_{j < i} c_j t_j + c_i t_i / 2,  t_j = h w_j lambda_j exp(-c_j E_j)
  * (j < i: farther from the detector), each spread to pixels by the bilinear weights. */
 static void og_ray_vjp(const og_ctx* o, const og_ray* ry, const double* lam, const double* mu,
                        double rho, double* gl, double* gm, double* ex, double* lv) {
@@ -283,7 +295,7 @@ static void og_ray_vjp(const og_ctx* o, const og_ray* ry, const double* lam, con
             continue;
         }
         double l = og_sample(lam, idx, wt), m = og_sample(mu, idx, wt);
-        ex[j] = exp(-h * (S + 0.5 * m));
+        ex[j] = og_dw(o, j) * exp(-og_dc(o, j) * h * (S + 0.5 * m));  /* w_j exp(-c_j E_j) */
         lv[j] = l;
         S += m;
     }
@@ -295,8 +307,9 @@ static void og_ray_vjp(const og_ctx* o, const og_ray* ry, const double* lam, con
         double wt[4];
         og_point(o, ry, j, &fx, &fy);
         if (!og_bilinear(o, fx, fy, idx, wt)) continue;
+        double c = og_dc(o, j);
         double term = h * lv[j] * ex[j];
-        double Q = P + 0.5 * term;
+        double Q = P + 0.5 * c * term;
         double vl = rho * h * ex[j];
         double vm = -rho * h * Q;
         for (int q = 0; q < 4; ++q) {
@@ -304,7 +317,7 @@ static void og_ray_vjp(const og_ctx* o, const og_ray* ry, const double* lam, con
             gl[idx[q]] += wt[q] * vl;
             gm[idx[q]] += wt[q] * vm;
         }
-        P += term;
+        P += c * term;
     }
 }
 
