@@ -69,6 +69,14 @@ typedef struct {
     double step;          /* ray sample spacing h in pixels (<= 0: 1)                     */
     double fov_radius;    /* r (<= 0: n / sqrt 2, the circumscribed disk of the grid)     */
     double det_pitch;     /* p (<= 0: 2 r / nb)                                           */
+    /* Depth factors of Eq. (5) (optional; NULL: all ones): HOST arrays of T entries, T the
+     * samples per ray (pget_geometry_info), copied when a call first uses the geometry.
+     * Sample j of every sub-ray contributes h w_j lambda_j exp(-c_j E_j): depth_w[j] = w_j
+     * >= 0 is the distance-dependent part of the detector response r_{m,n}, depth_c[j] =
+     * c_j >= 0 the vertical-opening correction c_{m,n} of its attenuation (>= 1 in the
+     * paper).  Not supported by pget_forward_noalloc. */
+    const double* depth_w;
+    const double* depth_c;
 } pget_geometry;
 
 /* Levenberg-Marquardt parameters (Sec. 2.2, Eq. (6)-(9), Sec. 3.1).
@@ -246,6 +254,12 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
                                 const void* y, const void* lam, const void* mu,
                                 const void* s_step, const void* prop_lam, const void* prop_mu,
                                 pget_check_report* rep, void* stream);
+
+/* Derived sizes of a geometry (any output pointer may be NULL): samples per ray T (the
+ * length of the depth tables), detector banks, field-of-view radius r, detector pitch p
+ * and distinct rays per view (slots).  PGET_EINVAL for an invalid geometry. */
+pget_status pget_geometry_info(const pget_geometry* g, int32_t* n_samples, int32_t* n_banks, double* fov_radius,
+                               double* det_pitch, int32_t* max_slots);
 
 /* Projection onto the constraint set of p (Sec. 2.2): every pixel's pair (lambda, mu)
  * is replaced, in place, by its Euclidean projection onto the box [0, lambda_max] x

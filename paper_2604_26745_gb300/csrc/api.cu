@@ -149,6 +149,7 @@ struct Workspace {
     // adjoint view groups: CTA g sums views group_view[group_off[g] .. group_off[g+1]),
     // all of one canonical orientation, into partial image g
     int n_groups = 0, n_groups0 = 0;  // CTA groups in all / in the normal frame (listed first)
+    void* d_depth = nullptr;  // [T] (w_j, c_j) depth factors of Eq. (5), element type; null without
     int* d_group_off = nullptr;
     int* d_group_view = nullptr;
     void* pk_u[2] = {nullptr, nullptr};
@@ -219,6 +220,7 @@ static size_t workspace_bytes(const Geometry& g, int prec, int groups) {
     b += V * sizeof(ViewDev) + V * 4 + (size_t)g.n_det * g.n_sub * 4 + g.n_sub * 8;
     b += g.src_off.size() * 4 + g.src_det.size() * 12 + g.clip.size() * 4;
     b += V * (size_t)(g.n + 1) * 8;     // adjoint ray windows (at most n + 1 chunks per view)
+    if (g.depth) b += 2 * (size_t)g.T * elt;  // depth factors
     return b;
 }
 
@@ -377,6 +379,14 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
         return cudaMemcpy(*dst, f.data(), 4 * f.size(), cudaMemcpyHostToDevice);
     };
     CK(upload_t(&w->d_w, G.w));
+    if (G.depth) {  // interleaved (w_j, c_j) pairs
+        std::vector<double> dt(2 * (size_t)G.T);
+        for (int j = 0; j < G.T; ++j) {
+            dt[2 * j] = G.depth_w[j];
+            dt[2 * j + 1] = G.depth_c[j];
+        }
+        CK(upload_t(&w->d_depth, dt));
+    }
     CK(w->alloc(&w->d_clip, sizeof(int) * G.clip.size()));
     CK(cudaMemcpy(w->d_clip, G.clip.data(), sizeof(int) * G.clip.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_win, sizeof(int2) * w->pv.win.size()));
@@ -471,6 +481,7 @@ WalkArgs base_args(const Workspace& w) {
     a.src_det = w.d_src_det;
     a.src_w = w.d_src_w;
     a.clip = w.d_clip;
+    a.depth = w.d_depth;
     a.err = w.err;
     a.tx_extra = w.tx_extra;
     a.wait_ns = w.wait_ns;
@@ -569,8 +580,8 @@ pget_status run_cg(Workspace& w, const void* b, double scale_b, double nu, const
     CgState* cg = &w.lm->cg;
     cg_init<T>((const T*)b, (T*)w.x, (T*)w.res, (T*)w.p, m, scale_b, p.cg_rel_tol, w.dpart[0], cg, st);
     const int* stop = &cg->stop;
+    pack_vec<T>(w, w.p, w.pk_p, stop, st);  // later directions are packed by cg_dir_pack
     for (int it = 0; it < p.cg_max_iters; ++it) {
-        pack_vec<T>(w, w.p, w.pk_p, stop, st);
         cudaError_t e = op_jvp(w, w.pk_u, w.pk_p, w.Jp, stop, st);
         if (e != cudaSuccess) return fail(PGET_ECUDA, "jvp launch: %s", cudaGetErrorString(e));
         RedArgs<T> ra;
@@ -587,9 +598,9 @@ pget_status run_cg(Workspace& w, const void* b, double scale_b, double nu, const
         ra.part = w.dpart[0];
         e = op_vjp<T>(w, w.pk_u, w.U, w.Jp, ra, stop, st);
         if (e != cudaSuccess) return fail(PGET_ECUDA, "vjp launch: %s", cudaGetErrorString(e));
-        cg_finish_pq(w.dpart[0], cg, st);
-        cg_update<T>((T*)w.x, (T*)w.res, (const T*)w.p, (const T*)w.q, m, w.dpart[0], cg, st);
-        cg_pupdate<T>((T*)w.p, (const T*)w.res, m, cg, st);
+        cg_step<T>((T*)w.x, (T*)w.res, (const T*)w.p, (const T*)w.q, m, w.dpart[0], w.dpart[1], cg, st);
+        cg_dir_pack<T>((T*)w.p, (const T*)w.res, w.dpart[1], cg, w.g.n, w.P, attenuation_scale(w.g), w.pk_p[0],
+                       w.pk_p[1], st);
     }
     CK(cudaGetLastError());
     return PGET_OK;
@@ -1455,6 +1466,21 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
     cudaStream_t st = (cudaStream_t)stream;
     return w->f64 ? check_impl<double>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st)
                   : check_impl<float>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st);
+}
+
+pget_status pget_geometry_info(const pget_geometry* gin, int32_t* n_samples, int32_t* n_banks, double* fov_radius,
+                               double* det_pitch, int32_t* max_slots) {
+    if (!gin) return fail(PGET_EINVAL, "null geometry");
+    Geometry g;
+    std::string msg;
+    pget_status s = build_geometry(*gin, &g, &msg);
+    if (s != PGET_OK) return fail(s, "%s", msg.c_str());
+    if (n_samples) *n_samples = g.T;
+    if (n_banks) *n_banks = g.n_banks;
+    if (fov_radius) *fov_radius = g.r;
+    if (det_pitch) *det_pitch = g.p;
+    if (max_slots) *max_slots = g.max_slots;
+    return PGET_OK;
 }
 
 pget_status pget_project(pget_ctx* ctx, const pget_lm_params* p, int32_t n, void* lam, void* mu, void* stream) {

@@ -40,6 +40,18 @@ pget_status build_geometry(const pget_geometry& in, Geometry* G, std::string* ms
     if (Td < 1 || Td > 1 << 20) return *msg = "samples per ray out of range", PGET_EINVAL;
     g.T = (int)Td;
     g.c = 0.5 * (g.n - 1);
+    if (in.depth_w || in.depth_c) {
+        g.depth = true;
+        g.depth_w.assign(g.T, 1.0);
+        g.depth_c.assign(g.T, 1.0);
+        for (int j = 0; j < g.T; ++j) {
+            if (in.depth_w) g.depth_w[j] = in.depth_w[j];
+            if (in.depth_c) g.depth_c[j] = in.depth_c[j];
+            if (!(std::isfinite(g.depth_w[j]) && g.depth_w[j] >= 0.0 && std::isfinite(g.depth_c[j]) &&
+                  g.depth_c[j] >= 0.0))
+                return *msg = "depth tables must be finite and >= 0", PGET_EINVAL;
+        }
+    }
     const int S = g.n_sub;
 
     // sub-ray weights
@@ -174,9 +186,17 @@ pget_status build_geometry(const pget_geometry& in, Geometry* G, std::string* ms
             }
         }
     }
-    char key[256];
-    snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%.17g/%.17g/%.17g", g.n, g.n_angles, g.n_det,
-             g.n_banks, g.n_sub, g.collimator, g.h, g.r, g.p);
+    char key[320];
+    int kl = snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%.17g/%.17g/%.17g", g.n, g.n_angles, g.n_det,
+                      g.n_banks, g.n_sub, g.collimator, g.h, g.r, g.p);
+    if (g.depth) {  // the tables' contents are part of the geometry (FNV-1a over their bytes)
+        unsigned long long hsh = 1469598103934665603ull;
+        for (const std::vector<double>* tab : {&g.depth_w, &g.depth_c}) {
+            const unsigned char* b = (const unsigned char*)tab->data();
+            for (size_t i = 0; i < tab->size() * sizeof(double); ++i) hsh = (hsh ^ b[i]) * 1099511628211ull;
+        }
+        snprintf(key + kl, sizeof key - kl, "/depth:%016llx", hsh);
+    }
     g.key = key;
     *G = std::move(g);
     return PGET_OK;

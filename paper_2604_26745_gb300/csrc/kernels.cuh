@@ -148,6 +148,8 @@ struct WalkArgs {
                                //      samples in the chunk; stencil column = slot - first
     const int* group_off;      // VJP: CTA g handles views group_view[group_off[g] .. group_off[g+1])
     const int* group_view;     //      (null: CTA g handles view g)
+    const void* depth;         // [T] (w_j, c_j) pairs (element type of the path): depth factors
+                               //      of Eq. (5); null without tables
     const int* stop;           // optional: skip the launch when *stop != 0
     long long wait_ns;         // limit of one chunk-copy wait (0: 1 s)
     int tx_extra;              // test aid: bytes added to the first chunk's expected copy

@@ -54,6 +54,7 @@ using namespace pget;
 extern "C" pget_status pget_forward_noalloc(const pget_geometry* gin, int32_t precision, const void* lam,
                                             const void* mu, void* y, void* stream) {
     if (!gin || !lam || !mu || !y) return PGET_EINVAL;
+    if (gin->depth_w || gin->depth_c) return PGET_EINVAL;  // depth tables need a context workspace
     if (precision != PGET_F64 && precision != PGET_F32 && precision != PGET_F32_KAHAN) return PGET_EINVAL;
     const bool f64 = precision == PGET_F64;
     const size_t elt = f64 ? 8 : 4;

@@ -56,6 +56,10 @@ struct Geometry {
     // [-1, n-1]^2 (the kernels test every sample exactly); empty rays have jhi < jlo
     std::vector<int> clip;            // [n_views * max_slots * 2]
     int views_transposed = 0;
+    // depth factors of Eq. (5), [T] each, empty without tables: sample j contributes
+    // h w_j lambda_j exp(-c_j E_j)
+    std::vector<double> depth_w, depth_c;
+    bool depth = false;
     std::string key;                  // identifies the geometry for workspace caching
 };
 

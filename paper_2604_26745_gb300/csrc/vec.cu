@@ -443,25 +443,40 @@ __global__ void cg_finish_init_kernel(const double* __restrict__ part, CgState* 
     cg->iters = 0;
 }
 
-// after q = A p and partials of <p, q>
-__global__ void cg_finish_pq_kernel(const double* __restrict__ part, CgState* cg) {
-    if (cg->stop) return;
-    const double s = warp_sum_partials(part);
-    if (threadIdx.x) return;
-    cg->pq = s;
-    if (!(s > 0.0) || !isfinite(s)) {
-        cg->stop = 1;
-        return;
+// The kRedBlocks partials summed by warp 0 of the block in the fixed order of
+// warp_sum_partials (every block obtains the same value) and shared with the block.
+__device__ __forceinline__ double block_partials(const double* __restrict__ part) {
+    __shared__ double v;
+    if (threadIdx.y == 0 && threadIdx.x < 32) {
+        const double s = warp_sum_partials(part);
+        if (threadIdx.x == 0) v = s;
     }
-    cg->alpha = cg->rr / s;
+    __syncthreads();
+    return v;
 }
 
+// CG step fused with the finish of <p, q>: every block forms alpha = rr / <p, q> from the
+// partials part_pq itself; x += alpha p, res -= alpha q, per-block partials of |res|^2 into
+// part_rr (a separate buffer: other blocks may still be reading part_pq).  Block 0 records
+// pq, alpha and rr_prev = rr for the p update; <p, q> <= 0 or non-finite stops the solve.
 template <typename T>
-__global__ void cg_update_kernel(T* __restrict__ x, T* __restrict__ res, const T* __restrict__ p,
-                                 const T* __restrict__ q, size_t m, double* __restrict__ part,
-                                 const CgState* cg) {
+__global__ void cg_step_kernel(T* __restrict__ x, T* __restrict__ res, const T* __restrict__ p,
+                               const T* __restrict__ q, size_t m, const double* __restrict__ part_pq,
+                               double* __restrict__ part_rr, CgState* cg) {
     if (cg->stop) return;
-    const T al = (T)cg->alpha;
+    const double pq = block_partials(part_pq);
+    const double rr = cg->rr;
+    const bool bad = !(pq > 0.0) || !isfinite(pq);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cg->pq = pq;
+        if (bad) cg->stop = 1;
+        else {
+            cg->alpha = rr / pq;
+            cg->rr_prev = rr;
+        }
+    }
+    if (bad) return;
+    const T al = (T)(rr / pq);
     double acc = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
         x[i] += al * p[i];
@@ -469,31 +484,79 @@ __global__ void cg_update_kernel(T* __restrict__ x, T* __restrict__ res, const T
         res[i] = r;
         acc += (double)r * (double)r;
     }
-    double s = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    double sum = block_sum(acc);
+    if (threadIdx.x == 0) part_rr[blockIdx.x] = sum;
 }
 
-__global__ void cg_finish_rr_kernel(const double* __restrict__ part, CgState* cg) {
+// Direction update fused with the finish of |res|^2 and the packing of p for the next
+// JVP: every block forms s = |res|^2 from the partials; the iteration counts, and stops
+// (p untouched) when sqrt(s) <= tol |b| or s is not finite; otherwise
+// p = res + (s / rr_prev) p on the block's 32 x 32 tile of both fields, written planar and
+// in the two padded layouts of pack_kernel.  Block 0 records iters, rr and beta.
+template <typename T>
+__global__ void cg_dir_pack_kernel(T* __restrict__ p, const T* __restrict__ res, const double* __restrict__ part_rr,
+                                   CgState* cg, int n, int P, T mu_scale, typename Vec2<T>::type* __restrict__ out_n,
+                                   typename Vec2<T>::type* __restrict__ out_t) {
+    using T2 = typename Vec2<T>::type;
     if (cg->stop) return;
-    const double s = warp_sum_partials(part);
-    if (threadIdx.x) return;
-    cg->iters += 1;
-    if (sqrt(s) <= cg->tol * cg->bnorm || !isfinite(s)) {
-        cg->stop = 1;
+    const double s = block_partials(part_rr);
+    const double rp = cg->rr_prev;
+    const bool done = sqrt(s) <= cg->tol * cg->bnorm || !isfinite(s);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        cg->iters += 1;
         cg->rr = s;
+        if (!done) cg->beta = s / rp;
+    }
+    if (done) {
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) cg->stop = 1;
         return;
     }
-    cg->beta = s / cg->rr;
-    cg->rr = s;
+    const T be = (T)(s / rp);
+    const size_t nn = (size_t)n * n;
+    __shared__ T2 tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int iy = by + k, ix = bx + threadIdx.x;
+        if (iy < n && ix < n) {
+            const size_t i = (size_t)iy * n + ix;
+            const T pl = res[i] + be * p[i];
+            const T pm = res[nn + i] + be * p[nn + i];
+            p[i] = pl;
+            p[nn + i] = pm;
+            const T2 v = mk2(pl, mu_scale * pm);
+            out_n[(size_t)(iy + 1) * P + ix + 1] = v;
+            tile[k][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int ix = bx + k, iy = by + threadIdx.x;
+        if (iy < n && ix < n) out_t[(size_t)(ix + 1) * P + iy + 1] = tile[threadIdx.x][k];
+    }
 }
 
 template <typename T>
-__global__ void cg_pupdate_kernel(T* __restrict__ p, const T* __restrict__ res, size_t m, const CgState* cg) {
-    if (cg->stop) return;
-    const T be = (T)cg->beta;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
-        p[i] = res[i] + be * p[i];
+void cg_step(T* x, T* res, const T* p, const T* q, size_t m, const double* part_pq, double* part_rr, CgState* cg,
+             cudaStream_t st) {
+    cg_step_kernel<T><<<kRedBlocks, 256, 0, st>>>(x, res, p, q, m, part_pq, part_rr, cg);
+    note_launch();
 }
+template <typename T>
+void cg_dir_pack(T* p, const T* res, const double* part_rr, CgState* cg, int n, int P, double mu_scale, void* out_n,
+                 void* out_t, cudaStream_t st) {
+    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+    cg_dir_pack_kernel<T><<<grid, block, 0, st>>>(p, res, part_rr, cg, n, P, (T)mu_scale,
+                                                  (typename Vec2<T>::type*)out_n, (typename Vec2<T>::type*)out_t);
+    note_launch();
+}
+template void cg_step<float>(float*, float*, const float*, const float*, size_t, const double*, double*, CgState*,
+                             cudaStream_t);
+template void cg_step<double>(double*, double*, const double*, const double*, size_t, const double*, double*,
+                              CgState*, cudaStream_t);
+template void cg_dir_pack<float>(float*, const float*, const double*, CgState*, int, int, double, void*, void*,
+                                 cudaStream_t);
+template void cg_dir_pack<double>(double*, const double*, const double*, CgState*, int, int, double, void*, void*,
+                                  cudaStream_t);
 
 template <typename T>
 void cg_init(const T* b, T* x, T* res, T* p, size_t m, double scale_b, double tol, double* part, CgState* cg,
@@ -503,28 +566,8 @@ void cg_init(const T* b, T* x, T* res, T* p, size_t m, double scale_b, double to
     cg_finish_init_kernel<<<1, 32, 0, st>>>(part, cg);
     note_launch();
 }
-void cg_finish_pq(const double* part, CgState* cg, cudaStream_t st) {
-    cg_finish_pq_kernel<<<1, 32, 0, st>>>(part, cg);
-    note_launch();
-}
-template <typename T>
-void cg_update(T* x, T* res, const T* p, const T* q, size_t m, double* part, CgState* cg, cudaStream_t st) {
-    cg_update_kernel<T><<<kRedBlocks, 256, 0, st>>>(x, res, p, q, m, part, cg);
-    note_launch();
-    cg_finish_rr_kernel<<<1, 32, 0, st>>>(part, cg);
-    note_launch();
-}
-template <typename T>
-void cg_pupdate(T* p, const T* res, size_t m, const CgState* cg, cudaStream_t st) {
-    cg_pupdate_kernel<T><<<kRedBlocks, 256, 0, st>>>(p, res, m, cg);
-    note_launch();
-}
 template void cg_init<float>(const float*, float*, float*, float*, size_t, double, double, double*, CgState*, cudaStream_t);
 template void cg_init<double>(const double*, double*, double*, double*, size_t, double, double, double*, CgState*, cudaStream_t);
-template void cg_update<float>(float*, float*, const float*, const float*, size_t, double*, CgState*, cudaStream_t);
-template void cg_update<double>(double*, double*, const double*, const double*, size_t, double*, CgState*, cudaStream_t);
-template void cg_pupdate<float>(float*, const float*, size_t, const CgState*, cudaStream_t);
-template void cg_pupdate<double>(double*, const double*, size_t, const CgState*, cudaStream_t);
 
 // ------------------------------------------------------------- trust region
 // ut = P(u + x), s = ut - u (P: projection onto the constraint set)

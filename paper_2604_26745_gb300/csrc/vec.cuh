@@ -16,6 +16,7 @@ constexpr int kRedBlocks = 304;   // 2 x 152 SMs; fixed so reductions are determ
 // beta = line-search step, iters and stop as for CG
 struct CgState {
     double rr, pq, alpha, beta, bnorm, tol, dd;
+    double rr_prev;  // CG: |res|^2 of the previous step (the fused direction update divides by it)
     int iters, stop;
 };
 
@@ -96,11 +97,14 @@ void fill(T* u, size_t m, double v, cudaStream_t st);
 template <typename T>
 void cg_init(const T* b, T* x, T* res, T* p, size_t m, double scale_b, double tol, double* part, CgState* cg,
              cudaStream_t st);
-void cg_finish_pq(const double* part, CgState* cg, cudaStream_t st);
+// fused CG step (finish of <p, q>, x and res update, partials of |res|^2 into part_rr) and
+// direction update (finish of |res|^2, p update, packing of p for the next JVP)
 template <typename T>
-void cg_update(T* x, T* res, const T* p, const T* q, size_t m, double* part, CgState* cg, cudaStream_t st);
+void cg_step(T* x, T* res, const T* p, const T* q, size_t m, const double* part_pq, double* part_rr, CgState* cg,
+             cudaStream_t st);
 template <typename T>
-void cg_pupdate(T* p, const T* res, size_t m, const CgState* cg, cudaStream_t st);
+void cg_dir_pack(T* p, const T* res, const double* part_rr, CgState* cg, int n, int P, double mu_scale, void* out_n,
+                 void* out_t, cudaStream_t st);
 template <typename T>
 void lm_step(const T* u, const T* x, T* ut, T* s, size_t nn, const Feas& f, cudaStream_t st);
 template <typename T>

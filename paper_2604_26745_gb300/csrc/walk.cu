@@ -12,6 +12,9 @@
 //                                           g_mu = -rho h^2 (sum_{l<j} lambda_l e_l + lambda_j e_j / 2)
 //     with rho = sum of w_k r over the sub-rays on this slot; the far-side prefix is the
 //     ray total (from the forward pass) minus the detector-side suffix.
+// With the depth factors of Eq. (5) (DEPTH): e_j = w_j exp(-c_j E_j) in all three, dE_j
+// enters the JVP as c_j dE_j, and the adjoint prefix sums c_l lambda_l e_l (the forward
+// then stores that c-weighted total for the adjoint).
 //
 // Scatter-free adjoint.  A sample touches the four pixels of its bilinear cell: columns
 // ix0, ix0+1 of rows iy0, iy0+1.  Every ray crosses a pixel row with at most three
@@ -132,7 +135,7 @@ __device__ __forceinline__ void chunk_rows(int n, int Yc, int ck, int* row_hi, i
     *nrows = *row_hi - *row_lo + 2;
 }
 
-template <typename T, bool KAHAN, int MODE>
+template <typename T, bool KAHAN, int MODE, bool DEPTH>
 __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -199,10 +202,13 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
     int j = jr.y;
     Pos<T> pos;
     pos.init(vp, active ? tid : 0, j);
-    Acc<T, KAHAN> S, q, dS;
+    Acc<T, KAHAN> S, q, dS, qc;  // qc: forward with depth factors, sum c_j w_j lambda_j exp(-c_j E_j)
     S.init();
     q.init();
     dS.init();
+    qc.init();
+    const T2* dtab = (const T2*)A.depth;
+    (void)dtab;
     T rho = T(0), Utot = T(0);
     if constexpr (MODE == kVjp) {
         if (active) {
@@ -307,20 +313,34 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                     const T w00 = (T(1) - ax) - w01;
                     const T2 lm = bilerp2(w00, w10, w01, w11, a00, a10, a01, a11);
                     const T l = lm.x, m = lm.y;  // m is mu h log2(e)
-                    const T at = exp2_(-(S.val() + T(0.5) * m));
+                    T dw = T(1), dc = T(1);    // depth factors of sample j
+                    if constexpr (DEPTH) {
+                        const T2 t = dtab[j];
+                        dw = t.x;
+                        dc = t.y;
+                    }
+                    const T at = DEPTH ? exp2_(-(dc * (S.val() + T(0.5) * m))) : exp2_(-(S.val() + T(0.5) * m));
                     if constexpr (MODE == kFwd) {
-                        q.add(l * at);
+                        if constexpr (DEPTH) {
+                            const T wl = dw * (l * at);
+                            q.add(wl);
+                            qc.add(dc * wl);
+                        } else {
+                            q.add(l * at);
+                        }
                     } else if constexpr (MODE == kJvp) {
                         const T2 b00 = cp[o], b10 = cp[o + 1], b01 = cp[o + Ps], b11 = cp[o + Ps + 1];
                         const T2 dd = bilerp2(w00, w10, w01, w11, b00, b10, b01, b11);
                         // dE in natural units: ln 2 (dS + dm/2) with dS, dm scaled like m
                         const T dE = T(0.6931471805599453) * (dS.val() + T(0.5) * dd.y);
-                        q.add(at * (dd.x - l * dE));
+                        if constexpr (DEPTH) q.add(dw * at * (dd.x - l * (dc * dE)));
+                        else q.add(at * (dd.x - l * dE));
                         dS.add(dd.y);
                     } else {
-                        const T la = l * at;
-                        const T Qh = (Utot - q.val()) - T(0.5) * la;
-                        const T gl = rho * h * at;
+                        const T la = DEPTH ? dw * (l * at) : l * at;  // emission term of sample j
+                        const T cla = DEPTH ? dc * la : la;            // its weight in the prefix
+                        const T Qh = (Utot - q.val()) - T(0.5) * cla;
+                        const T gl = DEPTH ? rho * h * (dw * at) : rho * h * at;
                         const T gm = -rho * h * h * Qh;
                         const int rl = iy0 - row_lo;  // lower row of the cell; upper is rl + 1
                         if (iy0 != cur_row && in_win) {  // stencil rows start zeroed (chunk top)
@@ -348,7 +368,7 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
                         } else {
                             atomicOr(A.err, 2);  // geometry bound violated: report, never write out of range
                         }
-                        q.add(la);
+                        q.add(cla);
                     }
                     S.add(m);
                 }
@@ -406,7 +426,8 @@ __global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
         const T val = q.val();
         if (active) {
             sval[tid] = val;
-            if (MODE == kFwd && A.slot_val) ((T*)A.slot_val)[(size_t)v * A.max_slots + tid] = val;
+            // the adjoint's ray total: with depth factors the c-weighted one
+            if (MODE == kFwd && A.slot_val) ((T*)A.slot_val)[(size_t)v * A.max_slots + tid] = DEPTH ? qc.val() : val;
         }
         __syncthreads();
         T* y = (T*)A.y_out + (size_t)vp.angle * A.n_det + (size_t)vp.bank * A.nb;
@@ -563,19 +584,19 @@ WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, 
 
 // dynamic shared memory already permitted for each instantiation (set outside any
 // stream capture: prepare_walk runs before a CUDA graph is captured)
-template <typename T, bool K, int M>
+template <typename T, bool K, int M, bool D>
 static cudaError_t allow_smem(size_t bytes) {
     static size_t allowed = 0;
     if (bytes <= allowed) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<T, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<T, K, M, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) allowed = bytes;
     return e;
 }
 
-template <typename T, bool K, int M>
+template <typename T, bool K, int M, bool D>
 static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_views, cudaStream_t st) {
-    auto kern = walk_kernel<T, K, M>;
-    cudaError_t e = allow_smem<T, K, M>(pl.smem);
+    auto kern = walk_kernel<T, K, M, D>;
+    cudaError_t e = allow_smem<T, K, M, D>(pl.smem);
     if (e != cudaSuccess) return e;
     WalkArgs a = a0;
     a.Ps = pl.Ps;
@@ -587,8 +608,8 @@ static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_view
 
 template <typename T, bool K, int M>
 static int occ_one(const WalkPlan& pl) {
-    auto kern = walk_kernel<T, K, M>;
-    if (allow_smem<T, K, M>(pl.smem) != cudaSuccess) return 1;
+    auto kern = walk_kernel<T, K, M, false>;  // without depth tables (sizes optional view groups only)
+    if (allow_smem<T, K, M, false>(pl.smem) != cudaSuccess) return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pl.threads, pl.smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -612,11 +633,20 @@ int walk_occupancy(int mode, int precision, const WalkPlan& pl) {
 }
 
 cudaError_t prepare_walk(int mode, int precision, const WalkPlan& pl) {
-#define PGET_P(T, K)                                           \
-    switch (mode) {                                            \
-        case kFwd: return allow_smem<T, K, kFwd>(pl.smem);     \
-        case kJvp: return allow_smem<T, K, kJvp>(pl.smem);     \
-        default: return allow_smem<T, K, kVjp>(pl.smem);       \
+#define PGET_P(T, K)                                                                             \
+    switch (mode) {                                                                              \
+        case kFwd: {                                                                             \
+            cudaError_t e = allow_smem<T, K, kFwd, false>(pl.smem);                              \
+            return e != cudaSuccess ? e : allow_smem<T, K, kFwd, true>(pl.smem);                 \
+        }                                                                                        \
+        case kJvp: {                                                                             \
+            cudaError_t e = allow_smem<T, K, kJvp, false>(pl.smem);                              \
+            return e != cudaSuccess ? e : allow_smem<T, K, kJvp, true>(pl.smem);                 \
+        }                                                                                        \
+        default: {                                                                               \
+            cudaError_t e = allow_smem<T, K, kVjp, false>(pl.smem);                              \
+            return e != cudaSuccess ? e : allow_smem<T, K, kVjp, true>(pl.smem);                 \
+        }                                                                                        \
     }
     if (precision == PGET_F64) {
         PGET_P(double, false)
@@ -631,11 +661,14 @@ cudaError_t prepare_walk(int mode, int precision, const WalkPlan& pl) {
 cudaError_t launch_walk(int mode, int precision, const WalkPlan& pl, const WalkArgs& a, int n_views,
                         cudaStream_t st) {
     if (n_views <= 0) return cudaSuccess;
-#define PGET_L(T, K)                                                           \
-    switch (mode) {                                                            \
-        case kFwd: return launch_one<T, K, kFwd>(pl, a, n_views, st);          \
-        case kJvp: return launch_one<T, K, kJvp>(pl, a, n_views, st);          \
-        default: return launch_one<T, K, kVjp>(pl, a, n_views, st);            \
+#define PGET_L(T, K)                                                                                  \
+    switch (mode) {                                                                                   \
+        case kFwd: return a.depth ? launch_one<T, K, kFwd, true>(pl, a, n_views, st)                  \
+                                  : launch_one<T, K, kFwd, false>(pl, a, n_views, st);                \
+        case kJvp: return a.depth ? launch_one<T, K, kJvp, true>(pl, a, n_views, st)                  \
+                                  : launch_one<T, K, kJvp, false>(pl, a, n_views, st);                \
+        default: return a.depth ? launch_one<T, K, kVjp, true>(pl, a, n_views, st)                    \
+                                : launch_one<T, K, kVjp, false>(pl, a, n_views, st);                  \
     }
     if (precision == PGET_F64) {
         PGET_L(double, false)

@@ -28,7 +28,8 @@ class PgetError(RuntimeError):
 class pget_geometry(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_angles", C.c_int32), ("n_det", C.c_int32),
                 ("n_banks", C.c_int32), ("n_sub", C.c_int32), ("collimator", C.c_int32),
-                ("step", C.c_double), ("fov_radius", C.c_double), ("det_pitch", C.c_double)]
+                ("step", C.c_double), ("fov_radius", C.c_double), ("det_pitch", C.c_double),
+                ("depth_w", C.c_void_p), ("depth_c", C.c_void_p)]
 
 
 class pget_lm_params(C.Structure):
@@ -103,6 +104,8 @@ _SIGS = {
     "pget_proposal_check": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp, _vp,
                              _vp, _vp, C.POINTER(pget_check_report), _vp], C.c_int),
     "pget_project": ([_vp, C.POINTER(pget_lm_params), C.c_int32, _vp, _vp, _vp], C.c_int),
+    "pget_geometry_info": ([C.POINTER(pget_geometry), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)], C.c_int),
     "pget_lm_solve_host": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
                             _vp, C.c_int32, C.POINTER(pget_lm_report), _vp], C.c_int),
     "pget_submit": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp,
@@ -164,8 +167,35 @@ def _stream(stream) -> int:
 
 def geometry(n: int, n_angles: int, n_det: int, n_sub: int = 1, collimator: int = 1,
              n_banks: int = 0, step: float = 0.0, fov_radius: float = 0.0,
-             det_pitch: float = 0.0) -> pget_geometry:
-    return pget_geometry(n, n_angles, n_det, n_banks, n_sub, collimator, step, fov_radius, det_pitch)
+             det_pitch: float = 0.0, depth_w=None, depth_c=None) -> pget_geometry:
+    """Geometry; depth_w, depth_c (host sequences of T = geometry_info(...)["n_samples"]
+    entries) are the depth factors of Eq. (5): emission weight and attenuation factor of
+    sample j of every ray."""
+    g = pget_geometry(n, n_angles, n_det, n_banks, n_sub, collimator, step, fov_radius, det_pitch)
+    keep = []
+    if depth_w is not None or depth_c is not None:
+        T = geometry_info(g)["n_samples"]
+        for name, tab in (("depth_w", depth_w), ("depth_c", depth_c)):
+            if tab is None:
+                continue
+            a = (C.c_double * T)(*[float(v) for v in tab]) if len(tab) == T else None
+            if a is None:
+                raise ValueError(f"{name} needs {T} entries (one per ray sample)")
+            setattr(g, name, C.cast(a, C.c_void_p).value)
+            keep.append(a)
+    g._keep = keep  # the host tables must live as long as the geometry
+    return g
+
+
+def geometry_info(g: pget_geometry) -> dict:
+    """Derived sizes: samples per ray, banks, field-of-view radius, pitch, rays per view."""
+    T, nb, ms = C.c_int32(), C.c_int32(), C.c_int32()
+    r, p = C.c_double(), C.c_double()
+    st = load().pget_geometry_info(C.byref(g), C.byref(T), C.byref(nb), C.byref(r), C.byref(p), C.byref(ms))
+    if st != 0:
+        raise ValueError("invalid geometry")
+    return {"n_samples": T.value, "n_banks": nb.value, "fov_radius": r.value, "det_pitch": p.value,
+            "max_slots": ms.value}
 
 
 def default_params(**kw) -> pget_lm_params:
