@@ -1,0 +1,70 @@
+"""Learned proposal operator of Sec. 3.3 for the accelerated scheme (Alg. 2).
+
+The convolutional encoder-decoder of Sec. 3.3 maps the iterate u and the LM step s (both
+stacked [2, n, n]: emission, attenuation) to a proposal u~:
+
+    e = E_u(u) + E_s(s)            two encoders, 5 x 5 convolutions each followed by a
+                                   ReLU, channels 2 -> 8 -> 16 -> 32
+    d = D(e)                       decoder 32 -> 16 -> 8 (convolution + ReLU), then a
+                                   convolution 8 -> 2 without activation
+    u~ = ReLU(u + d * C(s))        d multiplied pixelwise by a 5 x 5 convolution of s
+                                   (2 -> 2, no activation), added to u by the skip
+                                   connection and projected to non-negative values
+
+Every convolution keeps the image size (padding 2).  As in Sec. 4, the inputs are scaled
+by the box bounds (lambda / lambda_max, mu / mu_max) and the output is scaled back.  No
+trained weights ship with the library (the paper's training data are not available):
+the module is the architecture, to be trained by the caller or loaded from a state dict,
+and Alg. 2's safeguard keeps any proposal it makes from harming the iteration.  Its
+convolutions run in the framework's convolution library.
+"""
+from __future__ import annotations
+
+import torch
+from torch import nn
+
+
+def _conv(cin: int, cout: int) -> nn.Conv2d:
+    return nn.Conv2d(cin, cout, kernel_size=5, padding=2)
+
+
+class ConvProposal(nn.Module):
+    """u~ = ReLU(u + D(E_u(u) + E_s(s)) * C(s)) on images scaled by the box bounds."""
+
+    WIDTHS = (2, 8, 16, 32)
+
+    def __init__(self, lambda_max: float = 2.0, mu_max: float = 0.2):
+        super().__init__()
+        w = self.WIDTHS
+        enc = lambda: nn.Sequential(*[m for a, b in zip(w[:-1], w[1:]) for m in (_conv(a, b), nn.ReLU())])
+        self.enc_u = enc()
+        self.enc_s = enc()
+        r = w[::-1]  # 32 -> 16 -> 8, then 8 -> 2 without activation
+        layers = [m for a, b in zip(r[:-2], r[1:-1]) for m in (_conv(a, b), nn.ReLU())]
+        self.dec = nn.Sequential(*layers, _conv(r[-2], r[-1]))
+        self.gate = _conv(2, 2)
+        self.register_buffer("scale", torch.tensor([lambda_max, mu_max]).view(1, 2, 1, 1))
+
+    def forward(self, u: torch.Tensor, s: torch.Tensor) -> torch.Tensor:
+        """u, s: [B, 2, n, n] (or [2, n, n]) in physical units; returns u~ of the same shape."""
+        squeeze = u.dim() == 3
+        if squeeze:
+            u, s = u.unsqueeze(0), s.unsqueeze(0)
+        sc = self.scale.to(dtype=u.dtype)
+        un, sn = u / sc, s / sc
+        d = self.dec(self.enc_u(un) + self.enc_s(sn))
+        # ReLU(u / sc + d C) sc with the scale applied to the correction only (sc > 0):
+        # the same map, and exactly u where the correction vanishes
+        out = torch.relu(u + sc * (d * self.gate(sn)))
+        return out.squeeze(0) if squeeze else out
+
+
+def as_proposal(model: nn.Module):
+    """The G(u, s, k) callable of accelerated_solve for a module taking (u, s)."""
+
+    @torch.no_grad()
+    def G(u: torch.Tensor, s: torch.Tensor, k: int) -> torch.Tensor:
+        p = next(model.parameters())
+        return model(u.to(p.dtype), s.to(p.dtype)).to(u.dtype)
+
+    return G

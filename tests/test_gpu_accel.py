@@ -147,3 +147,32 @@ def test_alpha_continuation_matches_oracle(O, P, torch):
                         t(y), lam, mu)
     for a, b in outs:
         assert torch.equal(a, lam) and torch.equal(b, mu)
+
+
+def test_driver_with_the_conv_proposal(O, P, torch):
+    """Alg. 2 with the convolutional proposal operator of Sec. 3.3 (untrained): with all
+    weights zero it proposes u itself (s~ = 0, no model decrease) and the scheme is the
+    plain LM bitwise; with random weights every proposal it takes passed the check
+    (rho(s~) > eta and m_k(s~) <= m_k(s_k))."""
+    from paper_2604_26745_gb300.accelerated import accelerated_solve
+    from paper_2604_26745_gb300.proposals import ConvProposal, as_proposal
+    ph, go, g, y = _setup(O, P, torch, seed=25)
+    p = P.default_params(max_iters=3, cg_max_iters=6, cg_rel_tol=1e-10, precision=0)
+    yd = torch.tensor(y, device="cuda")
+    with P.Context(0) as c:
+        l0, m0 = P.pget_initial_guess(c, g, p, yd)
+        lb, mb, hb = accelerated_solve(c, g, p, yd, l0.clone(), m0.clone(), None)
+        zero = ConvProposal().cuda().double()
+        for q in zero.parameters():
+            torch.nn.init.zeros_(q)
+        lz, mz, hz = accelerated_solve(c, g, p, yd, l0.clone(), m0.clone(), as_proposal(zero))
+        torch.manual_seed(0)
+        net = ConvProposal().cuda().double()
+        ln, mn, hn = accelerated_solve(c, g, p, yd, l0.clone(), m0.clone(), as_proposal(net))
+    assert all(x["took"] != "proposal" and x["check"] is not None for x in hz)
+    assert torch.equal(lz, lb) and torch.equal(mz, mb)
+    for x in hn:
+        assert x["check"] is not None
+        if x["took"] == "proposal":
+            assert x["check"]["rho_prop"] > p.eta and x["check"]["pred_prop"] >= x["check"]["pred_step"]
+    assert (ln >= 0).all() and (mn >= 0).all()
