@@ -77,3 +77,21 @@ def test_no_gpu_calls_fail_cleanly(lib):
     with pytest.raises(pget.PgetError):
         pget.Context(0)
     assert pget.pget_version().startswith("pget-gb300")
+
+
+def test_geometry_info_and_depth_table_checks(lib, O):
+    """pget_geometry_info is host-only: it reports the samples per ray T of the oracle's
+    geometry (the length of the depth tables of Eq. (5)) and rejects invalid tables."""
+    import numpy as np
+    from paper_2604_26745_gb300 import pget
+    for args in ((128, 360, 182, 5), (27, 17, 91, 3), (64, 90, 91, 1)):
+        info = pget.geometry_info(pget.geometry(*args[:3], n_sub=args[3]))
+        assert info["n_samples"] == O.geom_info(O.geom(*args[:3], n_sub=args[3]))["T"]
+    T = pget.geometry_info(pget.geometry(16, 8, 91))["n_samples"]
+    ok = pget.geometry(16, 8, 91, depth_w=np.ones(T), depth_c=np.full(T, 1.5))
+    assert pget.geometry_info(ok)["n_samples"] == T
+    for bad in (dict(depth_w=-np.ones(T)), dict(depth_c=np.full(T, np.nan)), dict(depth_c=np.full(T, np.inf))):
+        with pytest.raises(ValueError):
+            pget.geometry_info(pget.geometry(16, 8, 91, **bad))
+    with pytest.raises(ValueError):  # wrong length
+        pget.geometry(16, 8, 91, depth_w=np.ones(T + 1))
