@@ -39,9 +39,9 @@ SUB = (16, 16)
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # (profiles/walk_kernels_single128.md), valid only for the kernel source it was taken on:
 # reported while csrc/walk.cu and csrc/kernels.cuh hash to these values, null otherwise.
-TRAFFIC = {"walk_vjp": {"bytes": 3130880 + 33636608,
-                        "walk.cu": "96dd6a17e5e06cd11277ccb2a18258f0270563cf1d4ffff882499d67ff1f6c36",
-                        "kernels.cuh": "0aae84d337a6f8619a196917ff87b520935a95ab4a442496d32ac3d8b45fe936"}}
+TRAFFIC = {"walk_vjp": {"bytes": 3132160 + 33967360,
+                        "walk.cu": "c117d013251cc9759f56e1eba9a4654b360af226aab1c620d55862d2a6a33542",
+                        "kernels.cuh": "d61d8e76eb35c0c5156e12b11d7684120b0782d142fb7e1b39b698203255edec"}}
 
 
 def captured_traffic(kernel: str):
