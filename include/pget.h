@@ -287,7 +287,9 @@ pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget
  * pget_submit: y ([n_angles][n_det]) and the optional initial guess lam0, mu0 ([n][n];
  *   both NULL: the pget_initial_guess reading with mu_init 0.01) are device pointers in
  *   the element type of p->precision; they are copied into slot memory before the call
- *   returns, so the caller may free them afterwards.  Returns PGET_EAGAIN when every slot
+ *   returns, so the caller may free them afterwards; so are the geometry's depth tables.
+ *   The parameters are taken by value, except p->geo_mask, which the request reads while it
+ *   runs: keep that array valid until pget_poll reports done.  Returns PGET_EAGAIN when every slot
  *   is busy or the memory budget of the context is in use (retry after a poll),
  *   PGET_ENOMEM when the request can never fit the budget, PGET_EINVAL for bad
  *   arguments.  Up to 8 requests are in flight (environment PGET_MAX_INFLIGHT, <= 64).

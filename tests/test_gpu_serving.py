@@ -155,3 +155,50 @@ def test_tickets_and_cancel(P, torch):
         with pytest.raises(P.PgetError) as e:
             P.pget_submit(ctx, P.geometry(1, 10, 91), p, y)
         assert e.value.status == P.PGET_EINVAL
+
+
+def test_serving_with_the_method_options(P, torch):
+    """Requests that use the optional parts of the method at once (gradient-projection
+    inner solver, linear bound, geometry priors, alpha continuation, depth tables of
+    Eq. (5)), mixed with a plain request, equal the same requests solved alone, bitwise;
+    the depth tables are copied at submission (the caller's arrays are overwritten with NaN
+    right after it)."""
+    n, na, S = 40, 45, 3
+    T = P.geometry_info(P.geometry(n, na, 182, n_sub=S))["n_samples"]
+    jj = np.arange(T) / (T - 1)
+    mask = torch.tensor(np.clip(synth.lattice_phantom(n, 4, radius=3.0, seed=5, zero_frac=0.0, mu_rod=1.0,
+                                                      mu_bg=0.0).mu, 0.0, 1.0), dtype=torch.float32, device="cuda")
+    opts = [dict(), dict(inner_solver=1, lin_constraint=1, lin_slope=14.0, lin_offset=0.0),
+            dict(geo_mask=mask, geo_alpha_lambda=2.0, geo_alpha_mu=20.0, geo_mu_water=0.01, alpha_decay=5.0,
+                 alpha_decay_iters=2, lin_constraint=1, lin_slope=20.0, lin_offset=0.05)]
+    reqs = []
+    for k, o in enumerate(opts):
+        depth = dict(depth_w=list(0.7 + 0.3 * jj), depth_c=list(1.0 + 0.5 * (1.0 - jj) ** 2)) if k else {}
+        g = P.geometry(n, na, 182, n_sub=S, **depth)
+        ph = synth.lattice_phantom(n, 4, radius=2.0, seed=500 + k)
+        with P.Context(0) as c:
+            yc = P.pget_forward(c, g, P.PGET_F64, torch.tensor(ph.lam, device="cuda"), torch.tensor(ph.mu, device="cuda"))
+        y = torch.tensor(synth.poisson_noise(yc.cpu().numpy(), 1e5, 600 + k), dtype=torch.float32, device="cuda")
+        p = P.default_params(max_iters=4, cg_max_iters=8, precision=P.PGET_F32_KAHAN, **o)
+        reqs.append((g, p, y))
+    alone = []
+    with P.Context(0) as c:
+        for g, p, y in reqs:
+            lam, mu = P.pget_initial_guess(c, g, p, y)
+            rep = P.pget_lm_solve(c, g, p, y, lam, mu)
+            alone.append((lam.clone(), mu.clone(), rep["f"]))
+    with P.Context(0) as ctx:
+        tickets = []
+        for g, p, y in reqs:
+            tickets.append(P.pget_submit(ctx, g, p, y))
+            for tab in getattr(g, "_keep", []):  # the caller's tables are spoilt once submitted
+                for i in range(len(tab)):
+                    tab[i] = float("nan")
+        outs = []
+        for t, (g, p, y) in zip(tickets, reqs):
+            lam = torch.empty((g.n, g.n), device="cuda")
+            mu = torch.empty_like(lam)
+            rep = _wait(P, ctx, t, lam, mu)
+            outs.append((lam, mu, rep["f"]))
+    for (la, ma, fa), (lb, mb, fb) in zip(alone, outs):
+        assert torch.equal(la, lb) and torch.equal(ma, mb) and fa == fb
