@@ -134,7 +134,6 @@ struct Workspace {
     size_t nn = 0, M = 0, nslots = 0, img_elems = 0;
     WalkPlan pf, pj, pv;
     ViewDev* d_views = nullptr;
-    int* d_vtrans = nullptr;
     int* d_det_slot = nullptr;
     void* d_w = nullptr;        // sub-ray weights in the element type of the path
     int* d_src_off = nullptr;
@@ -365,10 +364,6 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     (void)e2;
     CK(w->alloc(&w->d_views, sizeof(ViewDev) * V));
     CK(cudaMemcpy(w->d_views, G.views.data(), sizeof(ViewDev) * V, cudaMemcpyHostToDevice));
-    std::vector<int> vt(V);
-    for (int v = 0; v < V; ++v) vt[v] = G.views[v].transposed;
-    CK(w->alloc(&w->d_vtrans, sizeof(int) * V));
-    CK(cudaMemcpy(w->d_vtrans, vt.data(), sizeof(int) * V, cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_det_slot, sizeof(int) * G.det_slot.size()));
     CK(cudaMemcpy(w->d_det_slot, G.det_slot.data(), sizeof(int) * G.det_slot.size(), cudaMemcpyHostToDevice));
     auto upload_t = [&](void** dst, const std::vector<double>& src) -> cudaError_t {
