@@ -443,6 +443,16 @@ __global__ void cg_finish_init_kernel(const double* __restrict__ part, CgState* 
     cg->iters = 0;
 }
 
+// The solve's stop flag as one value per block.  Block 0 of the fused CG kernels below
+// may set the flag while other blocks of the same launch are starting: each block reads
+// it once, so that all its threads take the same branch around the block barriers.
+__device__ __forceinline__ bool block_stopped(const CgState* cg) {
+    __shared__ int s;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s = cg->stop;
+    __syncthreads();
+    return s != 0;
+}
+
 // The kRedBlocks partials summed by warp 0 of the block in the fixed order of
 // warp_sum_partials (every block obtains the same value) and shared with the block.
 __device__ __forceinline__ double block_partials(const double* __restrict__ part) {
@@ -463,7 +473,7 @@ template <typename T>
 __global__ void cg_step_kernel(T* __restrict__ x, T* __restrict__ res, const T* __restrict__ p,
                                const T* __restrict__ q, size_t m, const double* __restrict__ part_pq,
                                double* __restrict__ part_rr, CgState* cg) {
-    if (cg->stop) return;
+    if (block_stopped(cg)) return;
     const double pq = block_partials(part_pq);
     const double rr = cg->rr;
     const bool bad = !(pq > 0.0) || !isfinite(pq);
@@ -498,7 +508,7 @@ __global__ void cg_dir_pack_kernel(T* __restrict__ p, const T* __restrict__ res,
                                    CgState* cg, int n, int P, T mu_scale, typename Vec2<T>::type* __restrict__ out_n,
                                    typename Vec2<T>::type* __restrict__ out_t) {
     using T2 = typename Vec2<T>::type;
-    if (cg->stop) return;
+    if (block_stopped(cg)) return;
     const double s = block_partials(part_rr);
     const double rp = cg->rr_prev;
     const bool done = sqrt(s) <= cg->tol * cg->bnorm || !isfinite(s);
