@@ -327,7 +327,7 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
         return kb * 1024;
     };
     w->pf = plan_walk(G, w->P, kFwd, w->f64, budget("PGET_SMEM_KB_FWD", 64));
-    w->pj = plan_walk(G, w->P, kJvp, w->f64, budget("PGET_SMEM_KB_JVP", 64));
+    w->pj = plan_walk(G, w->P, kJvp, w->f64, budget("PGET_SMEM_KB_JVP", 72));
     {
         std::vector<int2> rows;
         ray_rows(G, w->f64, &rows);
