@@ -44,6 +44,12 @@ TRAFFIC = {"walk_vjp": {"bytes": 3132160 + 33967360,
                         "kernels.cuh": "d61d8e76eb35c0c5156e12b11d7684120b0782d142fb7e1b39b698203255edec"}}
 
 
+def workload_config(world: int) -> dict:
+    """The config object of both arms' JSON lines: the workload and its sizes."""
+    return {"workload": WORKLOAD_NAME, "parallelism": f"replicas x{world}",
+            "l2": "flushed between timed steps (256 MB write)", **dict(WORKLOAD)}
+
+
 def captured_traffic(kernel: str):
     import hashlib
     t = TRAFFIC.get(kernel)
@@ -212,7 +218,7 @@ def run_reference(args, rank: int):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME},
+            "data": "synthetic", "config": workload_config(args.gpus),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"each step = 1 of {W['max_iters']} LM iterations of one reconstruction; "
                                        f"recon/s = 1 / ({W['max_iters']} x mean step time)"},
@@ -380,8 +386,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(sum(step_ms) / len(step_ms), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps (256 MB write)", **{k: v for k, v in W.items()}},
+        "config": workload_config(world),
         "latency_ms": {"p50": round(statistics.median(step_ms), 3),
                        "p99": round(sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)], 3)},
         "accuracy": {"f32_kahan_vs_f64_gpu_rel_l2": f32_vs_f64, "rel_err_vs_truth_lambda": err_l,
