@@ -6,6 +6,7 @@
 // block order (finish kernels), so every result is deterministic.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "vec.cuh"
@@ -272,6 +273,64 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 && !KAHAN ? 4 : 3)
     }
 }
 
+// Stage 1 for float images with n divisible by 4: as reduce_views_kernel, but every thread
+// sums one row segment of four pixels (16-byte loads and stores; the views in the same
+// order, so the sums are the same).
+template <bool KAHAN>
+__global__ void __launch_bounds__(256, KAHAN ? 3 : 4)
+    reduce_views4_kernel(const float* __restrict__ gpart, int n, int n_views, int n0, int groups, int g0,
+                         float* __restrict__ out2, const int* skip) {
+    if (skip && *skip) return;
+    __shared__ float2 tile[32][33];
+    const int tiles_x = (n + 31) / 32;
+    const int tl = blockIdx.x % (tiles_x * tiles_x), grp = blockIdx.x / (tiles_x * tiles_x);
+    const int bx = (tl % tiles_x) * 32, by = (tl / tiles_x) * 32;
+    const bool tr = grp >= g0;
+    const int c0 = tr ? n0 : 0, cn = tr ? n_views - n0 : n0;
+    const int gi = tr ? grp - g0 : grp, gn = tr ? groups - g0 : g0;
+    const int v0 = c0 + (int)((long long)cn * gi / gn), v1 = c0 + (int)((long long)cn * (gi + 1) / gn);
+    const size_t nn = (size_t)n * n;
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const int rr = t >> 3, cc = (t & 7) * 4;         // tile row, first of its four columns
+    const int r = (tr ? bx : by) + rr, c = (tr ? by : bx) + cc;  // stored row and column
+    Acc<float, KAHAN> a[2][4];
+    for (int f = 0; f < 2; ++f)
+        for (int k = 0; k < 4; ++k) a[f][k].init();
+    if (r < n && c < n) {  // c and n are multiples of 4: the segment lies inside the row
+        const size_t off = (size_t)r * n + c;
+#pragma unroll 4
+        for (int v = v0; v < v1; ++v) {
+            const float* gp = gpart + (size_t)v * 2 * nn + off;
+            const float4 x = *reinterpret_cast<const float4*>(gp);
+            const float4 y = *reinterpret_cast<const float4*>(gp + nn);
+            a[0][0].add(x.x);
+            a[0][1].add(x.y);
+            a[0][2].add(x.z);
+            a[0][3].add(x.w);
+            a[1][0].add(y.x);
+            a[1][1].add(y.y);
+            a[1][2].add(y.z);
+            a[1][3].add(y.w);
+        }
+    }
+    float* o = out2 + (size_t)grp * 2 * nn;
+    if (tr) {  // stored [ix][iy]: the thread holds ix = r, iy = c + k; turn the tile (uniform per block)
+        for (int k = 0; k < 4; ++k) tile[cc + k][rr] = make_float2(a[0][k].val(), a[1][k].val());
+        __syncthreads();
+        const int iy = by + rr, ix = bx + cc;
+        if (iy < n && ix < n) {
+            const float2 e0 = tile[rr][cc], e1 = tile[rr][cc + 1], e2 = tile[rr][cc + 2], e3 = tile[rr][cc + 3];
+            *reinterpret_cast<float4*>(o + (size_t)iy * n + ix) = make_float4(e0.x, e1.x, e2.x, e3.x);
+            *reinterpret_cast<float4*>(o + nn + (size_t)iy * n + ix) = make_float4(e0.y, e1.y, e2.y, e3.y);
+        }
+    } else if (r < n && c < n) {
+        *reinterpret_cast<float4*>(o + (size_t)r * n + c) =
+            make_float4(a[0][0].val(), a[0][1].val(), a[0][2].val(), a[0][3].val());
+        *reinterpret_cast<float4*>(o + nn + (size_t)r * n + c) =
+            make_float4(a[1][0].val(), a[1][1].val(), a[1][2].val(), a[1][3].val());
+    }
+}
+
 // Stage 2: out = sum over groups (+ alpha grad^T W grad v + nu v when v given);
 // per-block partial of <dotv, out> when dotv given.
 template <typename T, bool KAHAN>
@@ -315,12 +374,19 @@ void reduce_views(const T* gpart, int n, int n_views, int n0, int groups, T* par
     int g0 = n0 <= 0 ? 0 : (n0 >= n_views ? groups : (int)((long long)groups * n0 / n_views));
     if (n0 > 0 && n0 < n_views) g0 = std::min(std::max(g0, 1), groups - 1);
     dim3 block(32, 8);
-    if (kahan)
-        reduce_views_kernel<T, true><<<tiles_x * tiles_x * groups, block, 0, st>>>(gpart, n, n_views, n0, groups, g0,
-                                                                                   part2, ra.skip);
-    else
-        reduce_views_kernel<T, false><<<tiles_x * tiles_x * groups, block, 0, st>>>(gpart, n, n_views, n0, groups, g0,
-                                                                                    part2, ra.skip);
+    const int grid = tiles_x * tiles_x * groups;
+    bool vec4 = false;
+    if constexpr (std::is_same<T, float>::value) {
+        vec4 = n % 4 == 0;  // then partial images and their rows start on 16-byte boundaries
+        if (vec4 && kahan)
+            reduce_views4_kernel<true><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
+        else if (vec4)
+            reduce_views4_kernel<false><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
+    }
+    if (!vec4 && kahan)
+        reduce_views_kernel<T, true><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
+    else if (!vec4)
+        reduce_views_kernel<T, false><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
     RedArgs<T> r2 = ra;
     r2.in2 = part2;
     r2.groups = groups;
