@@ -16,7 +16,7 @@ from paper_2604_26745_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: (1e-12, 1e-12), 2: (2e-6, 2e-5), 1: (2e-5, 1e-4)}
+TOL = {0: (1e-12, 1e-12), 2: (1e-6, 2e-6), 1: (2e-6, 5e-6)}
 
 CASES = {
     # name: (n, n_angles, n_det, n_sub, collimator, n_lat)
@@ -58,7 +58,7 @@ def test_operators_with_depth_tables(ctx, O, P, torch, case, prec):
     assert rel(y.cpu().numpy(), yo) <= tol_y
     assert rel(yo, O.forward(O.geom(n, na, nd, n_sub=S, collimator=col), lam, mu)) > 1e-2  # tables matter
     dy = P.pget_jvp(ctx, gg, prec, t(lam), t(mu), t(dl), t(dm))
-    assert rel(dy.cpu().numpy(), O.jvp(go, lam, mu, dl, dm)) <= 4 * tol_y
+    assert rel(dy.cpu().numpy(), O.jvp(go, lam, mu, dl, dm)) <= tol_y
     r = np.random.default_rng(7).standard_normal((na, nd))
     gl, gm = P.pget_vjp(ctx, gg, prec, t(lam), t(mu), t(r))
     ol, om = O.vjp(go, lam, mu, r)

@@ -13,7 +13,7 @@ def rel(a, b):
     return float(np.abs(np.asarray(a, np.float64) - b).max() / np.abs(b).max())
 
 
-@pytest.mark.parametrize("prec,tol_y,tol_g", [(2, 2e-6, 2e-5), (0, 1e-12, 1e-12)])
+@pytest.mark.parametrize("prec,tol_y,tol_g", [(2, 1e-6, 2e-6), (0, 1e-12, 1e-12)])
 def test_single_request_size_operators(ctx, O, P, torch, prec, tol_y, tol_g):
     n, na, nd, S = 128, 360, 182, 5
     go = O.geom(n, na, nd, n_sub=S)
@@ -27,7 +27,7 @@ def test_single_request_size_operators(ctx, O, P, torch, prec, tol_y, tol_g):
     y = P.pget_forward(ctx, g, prec, t(ph.lam), t(ph.mu)).cpu().numpy()
     assert rel(y, O.forward(go, ph.lam, ph.mu)) <= tol_y
     dy = P.pget_jvp(ctx, g, prec, t(ph.lam), t(ph.mu), t(dl), t(dm)).cpu().numpy()
-    assert rel(dy, O.jvp(go, ph.lam, ph.mu, dl, dm)) <= 4 * tol_y
+    assert rel(dy, O.jvp(go, ph.lam, ph.mu, dl, dm)) <= tol_y
     gl, gm = P.pget_vjp(ctx, g, prec, t(ph.lam), t(ph.mu), t(r))
     ol, om = O.vjp(go, ph.lam, ph.mu, r)
     assert rel(gl.cpu().numpy(), ol) <= tol_g

@@ -3,9 +3,12 @@ through the C ABI on identical seeded inputs.
 
 Tolerances (relative, max-norm over the output unless stated):
   PGET_F64        1e-12  (same arithmetic as the oracle up to rounding order and exp)
-  PGET_F32_KAHAN  sinogram 2e-6, gradient 2e-5: float exp(-E) carries |E| 2^-24 relative
-                  error (E up to ~10 here), positions are exact (32.32 fixed point)
-  PGET_F32        sinogram 2e-5, gradient 1e-4 (uncompensated float sums of ~200 terms)
+  PGET_F32_KAHAN  sinogram and JVP 1e-6, gradient 2e-6: float exp(-E) carries |E| 2^-24
+                  relative error (E up to ~10 here), positions are exact (32.32 fixed point);
+                  measured at most 1.6e-7 / 1.2e-7 / 3.4e-7 over these cases and the full
+                  128^2 geometry
+  PGET_F32        sinogram and JVP 2e-6, gradient 5e-6 (uncompensated float sums of ~200
+                  terms; measured at most 4.3e-7)
 """
 import numpy as np
 import pytest
@@ -14,7 +17,7 @@ from paper_2604_26745_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: (1e-12, 1e-12), 2: (2e-6, 2e-5), 1: (2e-5, 1e-4)}
+TOL = {0: (1e-12, 1e-12), 2: (1e-6, 2e-6), 1: (2e-6, 5e-6)}
 
 
 def rel(a, b):
@@ -51,7 +54,7 @@ def test_forward_jvp_vjp_parity(ctx, O, P, torch, case, prec):
     y = P.pget_forward(ctx, gg, prec, t(lam), t(mu))
     assert rel(y.cpu().numpy(), O.forward(go, lam, mu)) <= tol_y
     dy = P.pget_jvp(ctx, gg, prec, t(lam), t(mu), t(dl), t(dm))
-    assert rel(dy.cpu().numpy(), O.jvp(go, lam, mu, dl, dm)) <= 4 * tol_y
+    assert rel(dy.cpu().numpy(), O.jvp(go, lam, mu, dl, dm)) <= tol_y
     r = np.random.default_rng(7).standard_normal((na, nd))
     gl, gm = P.pget_vjp(ctx, gg, prec, t(lam), t(mu), t(r))
     ol, om = O.vjp(go, lam, mu, r)
