@@ -13,6 +13,7 @@ namespace pget {
 
 constexpr int kMaxSub = 64;
 constexpr int kMaxSlots = 1024;   // rays per bank and view handled by one CTA (one per thread)
+constexpr int kWalkThreads = 896; // block bound of the walk kernels for views up to this size
 
 // ---------------------------------------------------------------- geometry
 //

@@ -135,8 +135,13 @@ __device__ __forceinline__ void chunk_rows(int n, int Yc, int ck, int* row_hi, i
     *nrows = *row_hi - *row_lo + 2;
 }
 
-template <typename T, bool KAHAN, int MODE, bool DEPTH>
-__global__ void __launch_bounds__(kMaxSlots) walk_kernel(WalkArgs A) {
+// MAXT: the largest block the instantiation launches with.  Views of at most kWalkThreads
+// rays (every configuration measured here) take the kWalkThreads instantiation, which may
+// use 72 registers per thread (3 CTAs of 288 threads still fit an SM; measured 4-12 %
+// faster than 64); larger views take the kMaxSlots one, 64 registers, so that 1024
+// threads fit.
+template <typename T, bool KAHAN, int MODE, bool DEPTH, int MAXT>
+__global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs A) {
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char sm[];
     if (A.stop && *A.stop) return;
@@ -584,18 +589,23 @@ WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, 
 
 // dynamic shared memory already permitted for each instantiation (set outside any
 // stream capture: prepare_walk runs before a CUDA graph is captured)
-template <typename T, bool K, int M, bool D>
-static cudaError_t allow_smem(size_t bytes) {
+template <typename T, bool K, int M, bool D, int X>
+static cudaError_t allow_smem_x(size_t bytes) {
     static size_t allowed = 0;
     if (bytes <= allowed) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<T, K, M, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<T, K, M, D, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) allowed = bytes;
     return e;
+}
+template <typename T, bool K, int M, bool D>
+static cudaError_t allow_smem(size_t bytes) {
+    cudaError_t e = allow_smem_x<T, K, M, D, kWalkThreads>(bytes);
+    return e != cudaSuccess ? e : allow_smem_x<T, K, M, D, kMaxSlots>(bytes);
 }
 
 template <typename T, bool K, int M, bool D>
 static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_views, cudaStream_t st) {
-    auto kern = walk_kernel<T, K, M, D>;
+    auto kern = pl.threads <= kWalkThreads ? walk_kernel<T, K, M, D, kWalkThreads> : walk_kernel<T, K, M, D, kMaxSlots>;
     cudaError_t e = allow_smem<T, K, M, D>(pl.smem);
     if (e != cudaSuccess) return e;
     WalkArgs a = a0;
@@ -608,7 +618,9 @@ static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_view
 
 template <typename T, bool K, int M>
 static int occ_one(const WalkPlan& pl) {
-    auto kern = walk_kernel<T, K, M, false>;  // without depth tables (sizes optional view groups only)
+    // without depth tables (sizes optional view groups only)
+    auto kern = pl.threads <= kWalkThreads ? walk_kernel<T, K, M, false, kWalkThreads>
+                                           : walk_kernel<T, K, M, false, kMaxSlots>;
     if (allow_smem<T, K, M, false>(pl.smem) != cudaSuccess) return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pl.threads, pl.smem) != cudaSuccess) return 1;
