@@ -39,8 +39,8 @@ SUB = (16, 16)
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
 # (profiles/walk_kernels_single128.md), valid only for the kernel source it was taken on:
 # reported while csrc/walk.cu and csrc/kernels.cuh hash to these values, null otherwise.
-TRAFFIC = {"walk_vjp": {"bytes": 3132160 + 33967360,
-                        "walk.cu": "c117d013251cc9759f56e1eba9a4654b360af226aab1c620d55862d2a6a33542",
+TRAFFIC = {"walk_vjp": {"bytes": 3129856 + 33681152,
+                        "walk.cu": "6a45b798e874435eec15c2dd113f1b5c32680afe4ab5433cf5e0accc000d6070",
                         "kernels.cuh": "d61d8e76eb35c0c5156e12b11d7684120b0782d142fb7e1b39b698203255edec"}}
 
 
