@@ -32,6 +32,9 @@
 #include <climits>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kernels.cuh"
 
@@ -135,11 +138,11 @@ __device__ __forceinline__ void chunk_rows(int n, int Yc, int ck, int* row_hi, i
     *nrows = *row_hi - *row_lo + 2;
 }
 
-// MAXT: the largest block the instantiation launches with.  Views of at most kWalkThreads
-// rays (every configuration measured here) take the kWalkThreads instantiation, which may
-// use 72 registers per thread (3 CTAs of 288 threads still fit an SM; measured 4-12 %
-// faster than 64); larger views take the kMaxSlots one, 64 registers, so that 1024
-// threads fit.
+// MAXT: the largest block the instantiation launches with.  The kWalkThreads
+// instantiation may use 72 registers per thread (measured 4-12 % faster than 64 at 3 CTAs
+// of 288 threads per SM); it runs when the view has at most kWalkThreads rays and the
+// extra registers leave as many CTAs resident per SM (see walk_choice).  Otherwise the
+// kMaxSlots instantiation runs, 64 registers, so that 1024 threads fit.
 template <typename T, bool KAHAN, int MODE, bool DEPTH, int MAXT>
 __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs A) {
     using T2 = typename Vec2<T>::type;
@@ -603,11 +606,36 @@ static cudaError_t allow_smem(size_t bytes) {
     return e != cudaSuccess ? e : allow_smem_x<T, K, M, D, kMaxSlots>(bytes);
 }
 
+// The instantiation for a plan: the 72-register one when the block fits it and it keeps
+// at least as many CTAs resident per SM as the 64-register one (with 480 threads, say,
+// 72 registers allow one CTA per SM where 64 allow two).  The occupancy query runs once per
+// (block, shared memory) and is cached: prepare_walk makes it before any stream capture.
+// Needs allow_smem first.
+template <typename T, bool K, int M, bool D>
+static void (*walk_choice(const WalkPlan& pl))(WalkArgs) {
+    if (pl.threads > kWalkThreads) return walk_kernel<T, K, M, D, kMaxSlots>;
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, bool> wide;  // (threads, smem) -> 72 registers
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(pl.threads, pl.smem);
+    auto it = wide.find(key);
+    if (it == wide.end()) {
+        int o72 = 0, o64 = 0;
+        bool ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o72, walk_kernel<T, K, M, D, kWalkThreads>,
+                                                                pl.threads, pl.smem) == cudaSuccess &&
+                  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o64, walk_kernel<T, K, M, D, kMaxSlots>,
+                                                                pl.threads, pl.smem) == cudaSuccess;
+        if (!ok) cudaGetLastError();  // a failed query is no launch error: the 64-register one runs
+        it = wide.emplace(key, ok && o72 >= o64 && o72 > 0).first;
+    }
+    return it->second ? walk_kernel<T, K, M, D, kWalkThreads> : walk_kernel<T, K, M, D, kMaxSlots>;
+}
+
 template <typename T, bool K, int M, bool D>
 static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_views, cudaStream_t st) {
-    auto kern = pl.threads <= kWalkThreads ? walk_kernel<T, K, M, D, kWalkThreads> : walk_kernel<T, K, M, D, kMaxSlots>;
     cudaError_t e = allow_smem<T, K, M, D>(pl.smem);
     if (e != cudaSuccess) return e;
+    auto kern = walk_choice<T, K, M, D>(pl);
     WalkArgs a = a0;
     a.Ps = pl.Ps;
     a.nst = pl.nst;
@@ -619,9 +647,8 @@ static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_view
 template <typename T, bool K, int M>
 static int occ_one(const WalkPlan& pl) {
     // without depth tables (sizes optional view groups only)
-    auto kern = pl.threads <= kWalkThreads ? walk_kernel<T, K, M, false, kWalkThreads>
-                                           : walk_kernel<T, K, M, false, kMaxSlots>;
     if (allow_smem<T, K, M, false>(pl.smem) != cudaSuccess) return 1;
+    auto kern = walk_choice<T, K, M, false>(pl);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pl.threads, pl.smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -644,21 +671,23 @@ int walk_occupancy(int mode, int precision, const WalkPlan& pl) {
 #undef PGET_O
 }
 
+// shared memory permitted and the register instantiation chosen for both depth variants
+template <typename T, bool K, int M>
+static cudaError_t prepare_one(const WalkPlan& pl) {
+    cudaError_t e = allow_smem<T, K, M, false>(pl.smem);
+    if (e == cudaSuccess) e = allow_smem<T, K, M, true>(pl.smem);
+    if (e != cudaSuccess) return e;
+    walk_choice<T, K, M, false>(pl);
+    walk_choice<T, K, M, true>(pl);
+    return cudaSuccess;
+}
+
 cudaError_t prepare_walk(int mode, int precision, const WalkPlan& pl) {
 #define PGET_P(T, K)                                                                             \
     switch (mode) {                                                                              \
-        case kFwd: {                                                                             \
-            cudaError_t e = allow_smem<T, K, kFwd, false>(pl.smem);                              \
-            return e != cudaSuccess ? e : allow_smem<T, K, kFwd, true>(pl.smem);                 \
-        }                                                                                        \
-        case kJvp: {                                                                             \
-            cudaError_t e = allow_smem<T, K, kJvp, false>(pl.smem);                              \
-            return e != cudaSuccess ? e : allow_smem<T, K, kJvp, true>(pl.smem);                 \
-        }                                                                                        \
-        default: {                                                                               \
-            cudaError_t e = allow_smem<T, K, kVjp, false>(pl.smem);                              \
-            return e != cudaSuccess ? e : allow_smem<T, K, kVjp, true>(pl.smem);                 \
-        }                                                                                        \
+        case kFwd: return prepare_one<T, K, kFwd>(pl);                                           \
+        case kJvp: return prepare_one<T, K, kJvp>(pl);                                           \
+        default: return prepare_one<T, K, kVjp>(pl);                                             \
     }
     if (precision == PGET_F64) {
         PGET_P(double, false)
