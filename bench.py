@@ -37,29 +37,44 @@ METRIC = "recon/s"
 SUB = (16, 16)
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
-# (profiles/walk_kernels_single128.md), valid only for the kernel source it was taken on:
-# reported while csrc/walk.cu and csrc/kernels.cuh hash to these values, null otherwise.
+# (profiles/walk_kernels_single128.md), valid only for the kernel code it was taken on:
+# reported while the device code of csrc/walk.cu (the part before its host section) and
+# csrc/kernels.cuh, without comments, blank lines and includes, hash to these values; null
+# otherwise.
 TRAFFIC = {"walk_vjp": {"bytes": 3129856 + 33681152,
-                        "walk.cu": "6a45b798e874435eec15c2dd113f1b5c32680afe4ab5433cf5e0accc000d6070",
-                        "kernels.cuh": "d61d8e76eb35c0c5156e12b11d7684120b0782d142fb7e1b39b698203255edec"}}
+                        "walk.cu": "df841f95780a2129242265ff8a2ea1e8948b49d19c248221ad3dcd9ddf012590",
+                        "kernels.cuh": "bbef9417fb4bd7ebda756e9ee1a3066b6323e3f91ff72f90f1d475b7587588d7"}}
+
+
+def _device_code_hash(path: str, split: str | None = None) -> str:
+    import hashlib
+    import re
+    with open(path) as fh:
+        src = fh.read()
+    if split:
+        src = src.split(split)[0]
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    lines = [ln.strip() for ln in src.split("\n") if ln.strip() and not ln.strip().startswith("#include")]
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
+def captured_traffic(kernel: str):
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    csrc = os.path.join(ROOT, "paper_2604_26745_gb300", "csrc")
+    if _device_code_hash(os.path.join(csrc, "walk.cu"), "static int smem_pitch(") != t["walk.cu"]:
+        return None
+    if _device_code_hash(os.path.join(csrc, "kernels.cuh")) != t["kernels.cuh"]:
+        return None
+    return t["bytes"]
 
 
 def workload_config(world: int) -> dict:
     """The config object of both arms' JSON lines: the workload and its sizes."""
     return {"workload": WORKLOAD_NAME, "parallelism": f"replicas x{world}",
             "l2": "flushed between timed steps (256 MB write)", **dict(WORKLOAD)}
-
-
-def captured_traffic(kernel: str):
-    import hashlib
-    t = TRAFFIC.get(kernel)
-    if not t:
-        return None
-    for f in ("walk.cu", "kernels.cuh"):
-        with open(os.path.join(ROOT, "paper_2604_26745_gb300", "csrc", f), "rb") as fh:
-            if hashlib.sha256(fh.read()).hexdigest() != t[f]:
-                return None
-    return t["bytes"]
 
 
 def _args():
