@@ -196,7 +196,8 @@ pget_status pget_initial_guess(pget_ctx* ctx, const pget_geometry* g, const pget
                                double mu_init, const void* y, void* lam, void* mu, void* stream);
 
 /* Levenberg-Marquardt trust-region solve (Sec. 2.2 and 3.1): each iteration runs CG on
- * Eq. (9), projects u + delta onto the box, takes s = P(u + delta) - u, evaluates the
+ * Eq. (9) (or gradient projection, inner_solver), takes s = P(u + delta) - u with P the
+ * projection onto the constraint set (the box, and the linear bound if set), evaluates the
  * model decrease of Eq. (8) and rho of Eq. (12), accepts iff rho > eta and updates nu.
  * All state stays on the device; one host synchronisation per iteration reads the
  * FP64 scalars into the report.  lam_io, mu_io: initial guess in, result out.
@@ -226,7 +227,8 @@ typedef struct {
 
 /* One trust-region trial of the LM iteration at the feasible point u = (lam, mu) with
  * damping nu (nu <= 0: nu_0 = nu0_scale |J g|^2 / |g|^2 at u, as a solve starts): CG on
- * Eq. (9), s_k = P_box(u + delta) - u, model and actual decrease, rho, acceptance.  u is
+ * Eq. (9), s_k = P(u + delta) - u (P: projection onto the constraint set), model and actual
+ * decrease, rho, acceptance.  u is
  * not changed (this is the s_k = LMA(u_k) of Alg. 2).  s_out: [2][n][n] device, the step.
  * rep: host.  Synchronises the stream. */
 pget_status pget_lm_trial(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
@@ -246,9 +248,10 @@ typedef struct {
 
 /* The check of Prop. conv_check / Alg. 2 for the proposal u~ = (prop_lam, prop_mu) at the
  * feasible point u with the LM step s_step ([2][n][n], as pget_lm_trial returns it):
- * s~ = P_box(u~) - u (the proposal is projected onto the constraint box like the LM
- * step), then accept iff rho(s~) > p->eta and m_k(s~) <= m_k(s_k).  The caller then sets
- * u_{k+1} = P_box(u~) when accepted, else u + s_k if the trial accepted, else u.  All
+ * s~ = P(u~) - u (the proposal is projected onto the constraint set like the LM step),
+ * then accept iff rho(s~) > p->eta and m_k(s~) <= m_k(s_k).  The caller then sets
+ * u_{k+1} = P(u~) when accepted (pget_project), else u + s_k if the trial accepted, else
+ * u.  All
  * arrays device [n][n] (s_step [2][n][n]); rep: host.  Synchronises the stream. */
 pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
                                 const void* y, const void* lam, const void* mu,

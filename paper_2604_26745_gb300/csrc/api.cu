@@ -1149,7 +1149,8 @@ static pget_status trial_impl(Workspace& w, const pget_lm_params& p, const void*
 }
 
 // The safeguard of Prop. conv_check / Alg. 2 for the proposal (pl, pm) at u with the LM
-// step s_step: s~ = P_box(u~) - u; accept iff rho(s~) > eta and m_k(s~) <= m_k(s_k).
+// step s_step: s~ = P(u~) - u (P: projection onto the constraint set); accept iff
+// rho(s~) > eta and m_k(s~) <= m_k(s_k).
 template <typename T>
 static pget_status check_impl(Workspace& w, const pget_lm_params& p, const void* y, const void* lam,
                               const void* mu, const void* s_step, const void* pl, const void* pm,

@@ -771,8 +771,9 @@ void lm_refresh_f(LmState* L, cudaStream_t st) {
 }
 
 // ------------------------------------------------------- gradient projection
-// min_s <g, s> + 1/2 s^T A s subject to u + s in the box (A = J^T J + H + nu I), from s = 0:
-// d = P_box(u + s - alpha grad q) - u - s, exact line search on [0, 1] for the quadratic,
+// min_s <g, s> + 1/2 s^T A s subject to u + s in the constraint set (A = J^T J + H + nu I),
+// from s = 0: d = P(u + s - alpha grad q) - u - s with P the projection onto the set (box,
+// and the linear bound if set), exact line search on [0, 1] for the quadratic,
 // alternating Barzilai-Borwein lengths; stop on the unit-step projected gradient.
 template <typename T>
 __global__ void sgp_init_kernel(const T* __restrict__ g, T* __restrict__ gq, T* __restrict__ x, size_t m, double tol,

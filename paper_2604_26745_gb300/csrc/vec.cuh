@@ -112,7 +112,7 @@ void lm_model(const T* s, const T* g, const T* Wl, const T* Wm, int n, double al
               double* pb, cudaStream_t st, const T* gmask = nullptr, double geo_l = 0.0, double geo_m = 0.0);
 void lm_decide(LmState* L, const LmParamsDev& P, cudaStream_t st);
 void lm_init_f(LmState* L, double nu0_scale, cudaStream_t st);
-// gradient projection on the box-constrained LM subproblem (see vec.cu)
+// gradient projection on the constrained LM subproblem (see vec.cu)
 template <typename T>
 void sgp_init(const T* g, T* gq, T* x, size_t m, double tol, CgState* cg, cudaStream_t st);
 template <typename T>
