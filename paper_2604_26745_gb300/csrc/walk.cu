@@ -591,10 +591,13 @@ WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, 
 }
 
 // dynamic shared memory already permitted for each instantiation (set outside any
-// stream capture: prepare_walk runs before a CUDA graph is captured)
+// stream capture: prepare_walk runs before a CUDA graph is captured); guarded, as contexts
+// may be driven from several host threads
 template <typename T, bool K, int M, bool D, int X>
 static cudaError_t allow_smem_x(size_t bytes) {
+    static std::mutex mu;
     static size_t allowed = 0;
+    std::lock_guard<std::mutex> lk(mu);
     if (bytes <= allowed) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(walk_kernel<T, K, M, D, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) allowed = bytes;
