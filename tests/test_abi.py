@@ -95,3 +95,57 @@ def test_geometry_info_and_depth_table_checks(lib, O):
             pget.geometry_info(pget.geometry(16, 8, 91, **bad))
     with pytest.raises(ValueError):  # wrong length
         pget.geometry(16, 8, 91, depth_w=np.ones(T + 1))
+
+
+def test_plain_c_program_links_and_runs(lib, O):
+    """A C program linked against libpget.so (no Python) uses the host-only calls:
+    pget_geometry_info gives the oracle's derived sizes, an invalid geometry returns
+    PGET_EINVAL, pget_default_params fills the documented defaults, and without a GPU
+    pget_create returns an error status with a message and leaves *ctx NULL."""
+    import subprocess
+    import tempfile
+    import torch
+    L, path = lib
+    prog = r'''
+#include <stdio.h>
+#include <string.h>
+#include "pget.h"
+int main(void) {
+  pget_geometry g;
+  memset(&g, 0, sizeof g);
+  g.n = 128; g.n_angles = 360; g.n_det = 182; g.n_sub = 5; g.collimator = 1;
+  int32_t T = 0, nb = 0, slots = 0;
+  double r = 0, p = 0;
+  int s = pget_geometry_info(&g, &T, &nb, &r, &p, &slots);
+  pget_geometry bad = g;
+  bad.n = 1;
+  int sbad = pget_geometry_info(&bad, NULL, NULL, NULL, NULL, NULL);
+  pget_lm_params prm;
+  pget_default_params(&prm);
+  pget_ctx* ctx = (pget_ctx*)&g;
+  int sc = pget_create(&ctx, 0, 0);
+  const char* msg = pget_last_error(NULL);
+  printf("%d %d %d %.17g %.17g %d %d %.17g %.17g %d %d %d\n", s, T, nb, r, p, slots, sbad,
+         prm.lambda_max, prm.mu_max, sc, ctx == NULL, msg && msg[0] != 0);
+  if (sc == PGET_OK) pget_destroy(ctx);
+  printf("%s\n", pget_version());
+  return 0;
+}'''
+    d = os.path.dirname(path)
+    with tempfile.TemporaryDirectory() as td:
+        c = os.path.join(td, "use.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(td, "use")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe, "-L", d, "-lpget",
+                        f"-Wl,-rpath,{d}"], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=120, check=True).stdout.split("\n")
+    f = out[0].split()
+    info = O.geom_info(O.geom(128, 360, 182, n_sub=5))
+    assert int(f[0]) == 0 and int(f[1]) == info["T"] and int(f[2]) == info["n_banks"] == 2
+    assert abs(float(f[3]) - info["radius"]) <= 1e-12 and abs(float(f[4]) - info["pitch"]) <= 1e-12
+    assert 91 <= int(f[5]) <= 1024  # distinct rays per view of one bank
+    assert int(f[6]) == 1  # PGET_EINVAL
+    assert float(f[7]) == 2.0 and float(f[8]) == 0.2
+    if not torch.cuda.is_available():
+        assert int(f[9]) != 0 and int(f[10]) == 1 and int(f[11]) == 1
+    assert out[1].startswith("pget-gb300")
