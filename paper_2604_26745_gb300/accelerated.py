@@ -34,17 +34,33 @@ def params_at(p: P.pget_lm_params, k: int) -> P.pget_lm_params:
 
 
 def accelerated_solve(ctx: P.Context, g: P.pget_geometry, p: P.pget_lm_params, y: torch.Tensor,
-                      lam: torch.Tensor, mu: torch.Tensor, G=None, iters: int | None = None):
+                      lam: torch.Tensor, mu: torch.Tensor, G=None, iters: int | None = None,
+                      state: dict | None = None):
     """Run Alg. 2 from (lam, mu) (projected onto the constraint set first); returns
     (lam, mu, history) with one dict per iteration (trial scalars, check scalars, which
-    update was taken).  Every projection runs in the library (pget_project)."""
-    iters = p.max_iters if iters is None else iters
+    update was taken, and the checkpoint "state" after it).  Every projection runs in the
+    library (pget_project).
+
+    Checkpoint and resume: the solver's whole state after iteration k is the iterate
+    (lam, mu) and the scalars {"k": k + 1, "nu": damping, "nu0": first damping}, the
+    "state" of that iteration's history entry.  Called with such a state and that
+    iterate, the solve continues at iteration state["k"] (the continuation schedule and the
+    damping clamps included) and gives the same iterates, bitwise, as the uninterrupted
+    solve; the iterate is not projected again, since the solve left it in the constraint
+    set.  iters counts this call's iterations (default: up to p.max_iters in total)."""
     proj = lambda a, b: P.pget_project(ctx, p, a.contiguous().clone(), b.contiguous().clone())
-    lam, mu = proj(lam, mu)
-    nu, nu0 = 0.0, None
+    if state is None:
+        k0, nu, nu0 = 0, 0.0, None
+        lam, mu = proj(lam, mu)
+    else:
+        k0, nu, nu0 = int(state["k"]), float(state["nu"]), float(state["nu0"])
+        if k0 < 0 or not nu0 > 0.0 or not nu > 0.0:
+            raise ValueError("invalid checkpoint state")
+        lam, mu = lam.contiguous().clone(), mu.contiguous().clone()
+    iters = max(p.max_iters - k0, 0) if iters is None else iters
     s = lam.new_empty((2,) + tuple(lam.shape))
     history = []
-    for k in range(iters):
+    for k in range(k0, k0 + iters):
         pk = params_at(p, k)
         s, tr = P.pget_lm_trial(ctx, g, pk, y, lam, mu, nu, s_out=s)
         if nu0 is None:
@@ -61,5 +77,6 @@ def accelerated_solve(ctx: P.Context, g: P.pget_geometry, p: P.pget_lm_params, y
         if took == "step":
             lam, mu = proj(lam + s[0], mu + s[1])
         nu = min(max(tr["nu_next"], p.nu_min * nu0), p.nu_max * nu0)
-        history.append({"k": k, "trial": tr, "check": chk, "took": took, "nu": nu})
+        history.append({"k": k, "trial": tr, "check": chk, "took": took, "nu": nu,
+                        "state": {"k": k + 1, "nu": nu, "nu0": nu0}})
     return lam, mu, history
