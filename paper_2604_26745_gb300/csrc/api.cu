@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.cuh"
 #include "pget_internal.cuh"
 #include "vec.cuh"
@@ -29,6 +31,16 @@ static pget_status fail(pget_status s, const char* fmt, ...) {
     g_last_error = buf;
     return s;
 }
+
+// Host-side NVTX range around a public call, for profilers that show or filter by them
+// (Nsight Systems timelines, ncu's --nvtx-include); without a tool attached it does nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define PGET_RANGE(name) NvtxRange nvtx_range_(name)
 
 #define CK(call)                                                                                 \
     do {                                                                                         \
@@ -1314,6 +1326,7 @@ pget_status pget_destroy(pget_ctx* ctx) {
 
 pget_status pget_forward(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
                          void* y, void* stream) {
+    PGET_RANGE("pget_forward");
     if (!ctx || !lam || !mu || !y) return fail(PGET_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard dg(ctx->device);
@@ -1329,6 +1342,7 @@ pget_status pget_forward(pget_ctx* ctx, const pget_geometry* g, int32_t prec, co
 
 pget_status pget_jvp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
                      const void* dlam, const void* dmu, void* dy, void* stream) {
+    PGET_RANGE("pget_jvp");
     if (!ctx || !lam || !mu || !dlam || !dmu || !dy) return fail(PGET_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard dg(ctx->device);
@@ -1350,6 +1364,7 @@ pget_status pget_jvp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const 
 
 pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
                      const void* r, void* glam, void* gmu, void* stream) {
+    PGET_RANGE("pget_vjp");
     if (!ctx || !lam || !mu || !r || !glam || !gmu) return fail(PGET_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard dg(ctx->device);
@@ -1362,6 +1377,7 @@ pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const 
 
 pget_status pget_reg_apply(pget_ctx* ctx, int32_t n, int32_t prec, double alpha, double eps, const void* u,
                            const void* v, void* out, double* value_host, void* stream) {
+    PGET_RANGE("pget_reg_apply");
     if (!ctx || !u || !v || !out) return fail(PGET_EINVAL, "null argument");
     if (n < 2) return fail(PGET_EINVAL, "n must be >= 2");
     if (prec != PGET_F64 && prec != PGET_F32 && prec != PGET_F32_KAHAN) return fail(PGET_EINVAL, "unknown precision");
@@ -1401,6 +1417,7 @@ pget_status pget_reg_apply(pget_ctx* ctx, int32_t n, int32_t prec, double alpha,
 
 pget_status pget_cg_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* lam,
                           const void* mu, double nu, const void* rhs, void* x, int32_t* iters, void* stream) {
+    PGET_RANGE("pget_cg_solve");
     if (!ctx || !lam || !mu || !rhs || !x) return fail(PGET_EINVAL, "null argument");
     pget_status s = check_params(p);
     if (s != PGET_OK) return s;
@@ -1418,6 +1435,7 @@ pget_status pget_cg_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_p
 
 pget_status pget_initial_guess(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, double mu_init,
                                const void* y, void* lam, void* mu, void* stream) {
+    PGET_RANGE("pget_initial_guess");
     if (!ctx || !y || !lam || !mu) return fail(PGET_EINVAL, "null argument");
     pget_status s = check_params(p);
     if (s != PGET_OK) return s;
@@ -1434,6 +1452,7 @@ pget_status pget_initial_guess(pget_ctx* ctx, const pget_geometry* g, const pget
 pget_status pget_lm_trial(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
                           const void* lam, const void* mu, double nu, void* s_out, pget_trial_report* rep,
                           void* stream) {
+    PGET_RANGE("pget_lm_trial");
     if (!ctx || !y || !lam || !mu || !s_out || !rep) return fail(PGET_EINVAL, "null argument");
     pget_status s = check_params(p);
     if (s != PGET_OK) return s;
@@ -1450,6 +1469,7 @@ pget_status pget_lm_trial(pget_ctx* ctx, const pget_geometry* g, const pget_lm_p
 pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
                                 const void* lam, const void* mu, const void* s_step, const void* prop_lam,
                                 const void* prop_mu, pget_check_report* rep, void* stream) {
+    PGET_RANGE("pget_proposal_check");
     if (!ctx || !y || !lam || !mu || !s_step || !prop_lam || !prop_mu || !rep)
         return fail(PGET_EINVAL, "null argument");
     pget_status s = check_params(p);
@@ -1480,6 +1500,7 @@ pget_status pget_geometry_info(const pget_geometry* gin, int32_t* n_samples, int
 }
 
 pget_status pget_project(pget_ctx* ctx, const pget_lm_params* p, int32_t n, void* lam, void* mu, void* stream) {
+    PGET_RANGE("pget_project");
     if (!ctx || !lam || !mu) return fail(PGET_EINVAL, "null argument");
     if (n < 1) return fail(PGET_EINVAL, "n must be >= 1");
     pget_status s = check_params(p);
@@ -1496,6 +1517,7 @@ pget_status pget_project(pget_ctx* ctx, const pget_lm_params* p, int32_t n, void
 
 pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
                           void* lam_io, void* mu_io, pget_lm_report* rep, void* stream) {
+    PGET_RANGE("pget_lm_solve");
     if (!ctx || !y || !lam_io || !mu_io) return fail(PGET_EINVAL, "null argument");
     pget_status s = check_params(p);
     if (s != PGET_OK) return s;
@@ -1511,6 +1533,7 @@ pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_p
 
 pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y_host,
                                void* lam_host, void* mu_host, int32_t init_guess, pget_lm_report* rep, void* stream) {
+    PGET_RANGE("pget_lm_solve_host");
     if (!ctx || !y_host || !lam_host || !mu_host) return fail(PGET_EINVAL, "null argument");
     pget_status s = check_params(p);
     if (s != PGET_OK) return s;
@@ -1547,6 +1570,7 @@ pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget
 
 pget_status pget_submit(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
                         const void* lam0, const void* mu0, uint64_t* ticket) {
+    PGET_RANGE("pget_submit");
     if (!ctx || !y || !ticket) return fail(PGET_EINVAL, "null argument");
     if ((lam0 == nullptr) != (mu0 == nullptr)) return fail(PGET_EINVAL, "give both lam0 and mu0, or neither");
     pget_status s = check_params(p);

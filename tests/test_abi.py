@@ -100,8 +100,9 @@ def test_geometry_info_and_depth_table_checks(lib, O):
 def test_plain_c_program_links_and_runs(lib, O):
     """A C program linked against libpget.so (no Python) uses the host-only calls:
     pget_geometry_info gives the oracle's derived sizes, an invalid geometry returns
-    PGET_EINVAL, pget_default_params fills the documented defaults, and without a GPU
-    pget_create returns an error status with a message and leaves *ctx NULL."""
+    PGET_EINVAL, pget_default_params fills the documented defaults, a compute call with null
+    arrays returns PGET_EINVAL (through its NVTX range), and without a GPU pget_create
+    returns an error status with a message and leaves *ctx NULL."""
     import subprocess
     import tempfile
     import torch
@@ -125,8 +126,9 @@ int main(void) {
   pget_ctx* ctx = (pget_ctx*)&g;
   int sc = pget_create(&ctx, 0, 0);
   const char* msg = pget_last_error(NULL);
-  printf("%d %d %d %.17g %.17g %d %d %.17g %.17g %d %d %d\n", s, T, nb, r, p, slots, sbad,
-         prm.lambda_max, prm.mu_max, sc, ctx == NULL, msg && msg[0] != 0);
+  int snull = pget_forward(NULL, &g, PGET_F32, NULL, NULL, NULL, NULL);  /* opens and closes a range */
+  printf("%d %d %d %.17g %.17g %d %d %.17g %.17g %d %d %d %d\n", s, T, nb, r, p, slots, sbad,
+         prm.lambda_max, prm.mu_max, sc, ctx == NULL, msg && msg[0] != 0, snull);
   if (sc == PGET_OK) pget_destroy(ctx);
   printf("%s\n", pget_version());
   return 0;
@@ -148,4 +150,5 @@ int main(void) {
     assert float(f[7]) == 2.0 and float(f[8]) == 0.2
     if not torch.cuda.is_available():
         assert int(f[9]) != 0 and int(f[10]) == 1 and int(f[11]) == 1
+    assert int(f[12]) == 1  # PGET_EINVAL for null arrays, through the profiler range
     assert out[1].startswith("pget-gb300")
