@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = OUT + f".{os.getpid()}.tmp"
-    cmd = [nvcc, *ARCH, "-shared", *objs, "-o", tmp]
+    cmd = [nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-ldl"]  # dlopen: NVTX looks for an attached tool
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
