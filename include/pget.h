@@ -36,12 +36,14 @@ extern "C" {
 typedef enum {
     PGET_OK = 0,
     PGET_EINVAL = 1,      /* bad argument: geometry, size, null pointer, precision      */
-    PGET_ENOMEM = 2,      /* workspace would exceed the context's memory budget         */
+    PGET_ENOMEM = 2,      /* workspace would exceed the context's memory budget, or a   *
+                           * host allocation failed                                      */
     PGET_EAGAIN = 3,      /* serving: no free slot or memory right now, retry later     */
     PGET_ECUDA = 4,       /* a CUDA runtime call failed (message has the CUDA error)    */
     PGET_ETIMEOUT = 5,    /* a bounded device-side wait ran out                         */
     PGET_ENUMERIC = 6,    /* NaN or Inf met in a result that must be finite             */
-    PGET_ENOTFOUND = 7    /* serving: unknown ticket                                     */
+    PGET_ENOTFOUND = 7,   /* serving: unknown ticket                                     */
+    PGET_EINTERNAL = 8    /* any other host-side failure inside the library (message)    */
 } pget_status;
 
 typedef enum {
@@ -61,7 +63,7 @@ typedef enum {
  *   j = 0..T-1, T = ceil(2 r / h), theta_perp = (-sin, cos); the detector is at +theta. */
 typedef struct {
     int32_t n;            /* grid size n >= 2                                             */
-    int32_t n_angles;     /* >= 1, phi_a = 2 pi a / n_angles                              */
+    int32_t n_angles;     /* 1..2^20, phi_a = 2 pi a / n_angles                          */
     int32_t n_det;        /* detectors in total, all banks                                */
     int32_t n_banks;      /* 1 or 2; 0 selects 2 when n_det == 182, else 1                */
     int32_t n_sub;        /* sub-rays per detector, 1..64                                 */

@@ -9,6 +9,8 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -28,8 +30,27 @@ static pget_status fail(pget_status s, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    g_last_error = buf;
+    try {
+        g_last_error = buf;
+    } catch (...) {  // out of host memory: the status still reports the failure
+    }
     return s;
+}
+
+// Every pget_status entry point runs its body through guarded(): a host-side exception (a
+// failed host allocation, a failed mutex) becomes a status instead of crossing the C
+// boundary, where it would end the caller's process.
+template <typename F>
+static pget_status guarded(F&& body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        return fail(PGET_ENOMEM, "host memory allocation failed");
+    } catch (const std::exception& e) {
+        return fail(PGET_EINTERNAL, "internal error: %s", e.what());
+    } catch (...) {
+        return fail(PGET_EINTERNAL, "internal error");
+    }
 }
 
 // Host-side NVTX range around a public call, for profilers that show or filter by them
@@ -1237,27 +1258,34 @@ const char* pget_version(void) { return "pget-gb300 0.1 (sm_103a)"; }
 long long pget_launch_count(void) { return pget::launch_count(); }
 
 pget_status pget_profile_enable(pget_ctx* ctx, int32_t enable) {
-    if (!ctx) return fail(PGET_EINVAL, "null ctx");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    ctx->prof.reset();
-    ctx->prof.on = enable != 0;
-    return PGET_OK;
+    return guarded([&]() -> pget_status {
+        if (!ctx) return fail(PGET_EINVAL, "null ctx");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        ctx->prof.reset();
+        ctx->prof.on = enable != 0;
+        return PGET_OK;
+    });
 }
 
 int32_t pget_profile_read(pget_ctx* ctx, pget_kernel_stat* out, int32_t max) {
-    if (!ctx) return 0;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    ctx->prof.collect();
-    int k = 0;
-    for (; k < kPKinds && k < max; ++k) {
-        memset(&out[k], 0, sizeof out[k]);
-        strncpy(out[k].name, kProfNames[k], sizeof out[k].name - 1);
-        out[k].launches = ctx->prof.count[k];
-        out[k].total_ms = ctx->prof.total_ms[k];
+    if (!ctx || !out) return 0;
+    try {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        ctx->prof.collect();
+        int k = 0;
+        for (; k < kPKinds && k < max; ++k) {
+            memset(&out[k], 0, sizeof out[k]);
+            strncpy(out[k].name, kProfNames[k], sizeof out[k].name - 1);
+            out[k].launches = ctx->prof.count[k];
+            out[k].total_ms = ctx->prof.total_ms[k];
+        }
+        return k;
+    } catch (...) {  // nothing read: a host-side failure is reported as no entries
+        fail(PGET_EINTERNAL, "profile read failed");
+        return 0;
     }
-    return k;
 }
 
 const char* pget_last_error(pget_ctx*) { return g_last_error.c_str(); }
@@ -1295,416 +1323,450 @@ void pget_default_params(pget_lm_params* o) {
 }
 
 pget_status pget_create(pget_ctx** ctx, int device, size_t budget) {
-    if (!ctx) return fail(PGET_EINVAL, "null ctx pointer");
-    *ctx = nullptr;
-    int nd = 0;
-    cudaError_t e = cudaGetDeviceCount(&nd);
-    if (e != cudaSuccess) return fail(PGET_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
-    if (device < 0 || device >= nd) return fail(PGET_EINVAL, "device %d out of range (%d devices)", device, nd);
-    auto c = new (std::nothrow) pget_ctx;
-    if (!c) return fail(PGET_ENOMEM, "host allocation failed");
-    c->device = device;
-    c->budget = budget;
-    *ctx = c;
-    g_last_error.clear();
-    return PGET_OK;
+    return guarded([&]() -> pget_status {
+        if (!ctx) return fail(PGET_EINVAL, "null ctx pointer");
+        *ctx = nullptr;
+        int nd = 0;
+        cudaError_t e = cudaGetDeviceCount(&nd);
+        if (e != cudaSuccess) return fail(PGET_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+        if (device < 0 || device >= nd) return fail(PGET_EINVAL, "device %d out of range (%d devices)", device, nd);
+        auto c = new (std::nothrow) pget_ctx;
+        if (!c) return fail(PGET_ENOMEM, "host allocation failed");
+        c->device = device;
+        c->budget = budget;
+        *ctx = c;
+        g_last_error.clear();
+        return PGET_OK;
+    });
 }
 
 pget_status pget_destroy(pget_ctx* ctx) {
-    if (!ctx) return PGET_OK;
-    {
-        DeviceGuard dg(ctx->device);
-        cudaDeviceSynchronize();
-        ctx->slots.clear();
-        ctx->pool.clear();
-        ctx->ws.reset();
-        if (ctx->scratch) cudaFree(ctx->scratch);
-    }
-    delete ctx;
-    return PGET_OK;
+    return guarded([&]() -> pget_status {
+        if (!ctx) return PGET_OK;
+        {
+            DeviceGuard dg(ctx->device);
+            cudaDeviceSynchronize();
+            ctx->slots.clear();
+            ctx->pool.clear();
+            ctx->ws.reset();
+            if (ctx->scratch) cudaFree(ctx->scratch);
+        }
+        delete ctx;
+        return PGET_OK;
+    });
 }
 
 pget_status pget_forward(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
                          void* y, void* stream) {
-    PGET_RANGE("pget_forward");
-    if (!ctx || !lam || !mu || !y) return fail(PGET_EINVAL, "null argument");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    pget_status s = get_workspace(ctx, g, prec, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (w->f64) pack_pair<double>(*w, lam, mu, w->pk_u, st);
-    else pack_pair<float>(*w, lam, mu, w->pk_u, st);
-    CK(op_forward(*w, w->pk_u, nullptr, y, nullptr, st));
-    return PGET_OK;
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_forward");
+        if (!ctx || !lam || !mu || !y) return fail(PGET_EINVAL, "null argument");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        pget_status s = get_workspace(ctx, g, prec, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        if (w->f64) pack_pair<double>(*w, lam, mu, w->pk_u, st);
+        else pack_pair<float>(*w, lam, mu, w->pk_u, st);
+        CK(op_forward(*w, w->pk_u, nullptr, y, nullptr, st));
+        return PGET_OK;
+    });
 }
 
 pget_status pget_jvp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
                      const void* dlam, const void* dmu, void* dy, void* stream) {
-    PGET_RANGE("pget_jvp");
-    if (!ctx || !lam || !mu || !dlam || !dmu || !dy) return fail(PGET_EINVAL, "null argument");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    pget_status s = get_workspace(ctx, g, prec, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (w->f64) {
-        pack_pair<double>(*w, lam, mu, w->pk_u, st);
-        pack_pair<double>(*w, dlam, dmu, w->pk_p, st);
-    } else {
-        pack_pair<float>(*w, lam, mu, w->pk_u, st);
-        pack_pair<float>(*w, dlam, dmu, w->pk_p, st);
-    }
-    CK(op_jvp(*w, w->pk_u, w->pk_p, dy, nullptr, st));
-    return PGET_OK;
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_jvp");
+        if (!ctx || !lam || !mu || !dlam || !dmu || !dy) return fail(PGET_EINVAL, "null argument");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        pget_status s = get_workspace(ctx, g, prec, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        if (w->f64) {
+            pack_pair<double>(*w, lam, mu, w->pk_u, st);
+            pack_pair<double>(*w, dlam, dmu, w->pk_p, st);
+        } else {
+            pack_pair<float>(*w, lam, mu, w->pk_u, st);
+            pack_pair<float>(*w, dlam, dmu, w->pk_p, st);
+        }
+        CK(op_jvp(*w, w->pk_u, w->pk_p, dy, nullptr, st));
+        return PGET_OK;
+    });
 }
 
 
 pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const void* lam, const void* mu,
                      const void* r, void* glam, void* gmu, void* stream) {
-    PGET_RANGE("pget_vjp");
-    if (!ctx || !lam || !mu || !r || !glam || !gmu) return fail(PGET_EINVAL, "null argument");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    pget_status s = get_workspace(ctx, g, prec, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    return w->f64 ? vjp_impl<double>(*w, lam, mu, r, glam, gmu, st) : vjp_impl<float>(*w, lam, mu, r, glam, gmu, st);
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_vjp");
+        if (!ctx || !lam || !mu || !r || !glam || !gmu) return fail(PGET_EINVAL, "null argument");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        pget_status s = get_workspace(ctx, g, prec, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        return w->f64 ? vjp_impl<double>(*w, lam, mu, r, glam, gmu, st) : vjp_impl<float>(*w, lam, mu, r, glam, gmu, st);
+    });
 }
 
 pget_status pget_reg_apply(pget_ctx* ctx, int32_t n, int32_t prec, double alpha, double eps, const void* u,
                            const void* v, void* out, double* value_host, void* stream) {
-    PGET_RANGE("pget_reg_apply");
-    if (!ctx || !u || !v || !out) return fail(PGET_EINVAL, "null argument");
-    if (n < 2) return fail(PGET_EINVAL, "n must be >= 2");
-    if (prec != PGET_F64 && prec != PGET_F32 && prec != PGET_F32_KAHAN) return fail(PGET_EINVAL, "unknown precision");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t elt = prec == PGET_F64 ? 8 : 4;
-    const size_t need = elt * (size_t)n * n + sizeof(double) * (kRedBlocks + 1);
-    if (ctx->scratch_bytes < need) {
-        CK(cudaStreamSynchronize(st));
-        if (ctx->scratch) cudaFree(ctx->scratch);
-        ctx->scratch = nullptr;
-        ctx->scratch_bytes = 0;
-        CK(cudaMalloc(&ctx->scratch, need));
-        ctx->scratch_bytes = need;
-    }
-    double* part = (double*)ctx->scratch;
-    void* W = (char*)ctx->scratch + sizeof(double) * (kRedBlocks + 1);
-    if (prec == PGET_F64) {
-        reg_weights<double>((const double*)u, n, eps, (double*)W, nullptr, st);
-        reg_apply<double>((const double*)v, (const double*)W, n, alpha, (double*)out, st);
-        if (value_host) reg_value<double>((const double*)u, n, alpha, eps, part, nullptr, st);
-    } else {
-        reg_weights<float>((const float*)u, n, eps, (float*)W, nullptr, st);
-        reg_apply<float>((const float*)v, (const float*)W, n, alpha, (float*)out, st);
-        if (value_host) reg_value<float>((const float*)u, n, alpha, eps, part, nullptr, st);
-    }
-    CK(cudaGetLastError());
-    if (value_host) {
-        finish_sum(part, part + kRedBlocks, nullptr, st);
-        CK(cudaMemcpyAsync(value_host, part + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-    }
-    return PGET_OK;
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_reg_apply");
+        if (!ctx || !u || !v || !out) return fail(PGET_EINVAL, "null argument");
+        if (n < 2) return fail(PGET_EINVAL, "n must be >= 2");
+        if (prec != PGET_F64 && prec != PGET_F32 && prec != PGET_F32_KAHAN) return fail(PGET_EINVAL, "unknown precision");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t elt = prec == PGET_F64 ? 8 : 4;
+        const size_t need = elt * (size_t)n * n + sizeof(double) * (kRedBlocks + 1);
+        if (ctx->scratch_bytes < need) {
+            CK(cudaStreamSynchronize(st));
+            if (ctx->scratch) cudaFree(ctx->scratch);
+            ctx->scratch = nullptr;
+            ctx->scratch_bytes = 0;
+            CK(cudaMalloc(&ctx->scratch, need));
+            ctx->scratch_bytes = need;
+        }
+        double* part = (double*)ctx->scratch;
+        void* W = (char*)ctx->scratch + sizeof(double) * (kRedBlocks + 1);
+        if (prec == PGET_F64) {
+            reg_weights<double>((const double*)u, n, eps, (double*)W, nullptr, st);
+            reg_apply<double>((const double*)v, (const double*)W, n, alpha, (double*)out, st);
+            if (value_host) reg_value<double>((const double*)u, n, alpha, eps, part, nullptr, st);
+        } else {
+            reg_weights<float>((const float*)u, n, eps, (float*)W, nullptr, st);
+            reg_apply<float>((const float*)v, (const float*)W, n, alpha, (float*)out, st);
+            if (value_host) reg_value<float>((const float*)u, n, alpha, eps, part, nullptr, st);
+        }
+        CK(cudaGetLastError());
+        if (value_host) {
+            finish_sum(part, part + kRedBlocks, nullptr, st);
+            CK(cudaMemcpyAsync(value_host, part + kRedBlocks, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        return PGET_OK;
+    });
 }
 
 
 pget_status pget_cg_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* lam,
                           const void* mu, double nu, const void* rhs, void* x, int32_t* iters, void* stream) {
-    PGET_RANGE("pget_cg_solve");
-    if (!ctx || !lam || !mu || !rhs || !x) return fail(PGET_EINVAL, "null argument");
-    pget_status s = check_params(p);
-    if (s != PGET_OK) return s;
-    if (!(nu >= 0) || !std::isfinite(nu)) return fail(PGET_EINVAL, "nu must be finite and >= 0");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    s = get_workspace(ctx, g, p->precision, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    return w->f64 ? cg_impl<double>(*w, *p, lam, mu, nu, rhs, x, iters, st)
-                  : cg_impl<float>(*w, *p, lam, mu, nu, rhs, x, iters, st);
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_cg_solve");
+        if (!ctx || !lam || !mu || !rhs || !x) return fail(PGET_EINVAL, "null argument");
+        pget_status s = check_params(p);
+        if (s != PGET_OK) return s;
+        if (!(nu >= 0) || !std::isfinite(nu)) return fail(PGET_EINVAL, "nu must be finite and >= 0");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        s = get_workspace(ctx, g, p->precision, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        return w->f64 ? cg_impl<double>(*w, *p, lam, mu, nu, rhs, x, iters, st)
+                      : cg_impl<float>(*w, *p, lam, mu, nu, rhs, x, iters, st);
+    });
 }
 
 
 pget_status pget_initial_guess(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, double mu_init,
                                const void* y, void* lam, void* mu, void* stream) {
-    PGET_RANGE("pget_initial_guess");
-    if (!ctx || !y || !lam || !mu) return fail(PGET_EINVAL, "null argument");
-    pget_status s = check_params(p);
-    if (s != PGET_OK) return s;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    s = get_workspace(ctx, g, p->precision, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    return w->f64 ? init_impl<double>(*w, *p, mu_init, y, lam, mu, st)
-                  : init_impl<float>(*w, *p, mu_init, y, lam, mu, st);
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_initial_guess");
+        if (!ctx || !y || !lam || !mu) return fail(PGET_EINVAL, "null argument");
+        pget_status s = check_params(p);
+        if (s != PGET_OK) return s;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        s = get_workspace(ctx, g, p->precision, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        return w->f64 ? init_impl<double>(*w, *p, mu_init, y, lam, mu, st)
+                      : init_impl<float>(*w, *p, mu_init, y, lam, mu, st);
+    });
 }
 
 pget_status pget_lm_trial(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
                           const void* lam, const void* mu, double nu, void* s_out, pget_trial_report* rep,
                           void* stream) {
-    PGET_RANGE("pget_lm_trial");
-    if (!ctx || !y || !lam || !mu || !s_out || !rep) return fail(PGET_EINVAL, "null argument");
-    pget_status s = check_params(p);
-    if (s != PGET_OK) return s;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    s = get_workspace(ctx, g, p->precision, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    return w->f64 ? trial_impl<double>(*w, *p, y, lam, mu, nu, s_out, rep, st)
-                  : trial_impl<float>(*w, *p, y, lam, mu, nu, s_out, rep, st);
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_lm_trial");
+        if (!ctx || !y || !lam || !mu || !s_out || !rep) return fail(PGET_EINVAL, "null argument");
+        pget_status s = check_params(p);
+        if (s != PGET_OK) return s;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        s = get_workspace(ctx, g, p->precision, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        return w->f64 ? trial_impl<double>(*w, *p, y, lam, mu, nu, s_out, rep, st)
+                      : trial_impl<float>(*w, *p, y, lam, mu, nu, s_out, rep, st);
+    });
 }
 
 pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
                                 const void* lam, const void* mu, const void* s_step, const void* prop_lam,
                                 const void* prop_mu, pget_check_report* rep, void* stream) {
-    PGET_RANGE("pget_proposal_check");
-    if (!ctx || !y || !lam || !mu || !s_step || !prop_lam || !prop_mu || !rep)
-        return fail(PGET_EINVAL, "null argument");
-    pget_status s = check_params(p);
-    if (s != PGET_OK) return s;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    s = get_workspace(ctx, g, p->precision, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    return w->f64 ? check_impl<double>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st)
-                  : check_impl<float>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st);
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_proposal_check");
+        if (!ctx || !y || !lam || !mu || !s_step || !prop_lam || !prop_mu || !rep)
+            return fail(PGET_EINVAL, "null argument");
+        pget_status s = check_params(p);
+        if (s != PGET_OK) return s;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        s = get_workspace(ctx, g, p->precision, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        return w->f64 ? check_impl<double>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st)
+                      : check_impl<float>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st);
+    });
 }
 
 pget_status pget_geometry_info(const pget_geometry* gin, int32_t* n_samples, int32_t* n_banks, double* fov_radius,
                                double* det_pitch, int32_t* max_slots) {
-    if (!gin) return fail(PGET_EINVAL, "null geometry");
-    Geometry g;
-    std::string msg;
-    pget_status s = build_geometry(*gin, &g, &msg);
-    if (s != PGET_OK) return fail(s, "%s", msg.c_str());
-    if (n_samples) *n_samples = g.T;
-    if (n_banks) *n_banks = g.n_banks;
-    if (fov_radius) *fov_radius = g.r;
-    if (det_pitch) *det_pitch = g.p;
-    if (max_slots) *max_slots = g.max_slots;
-    return PGET_OK;
+    return guarded([&]() -> pget_status {
+        if (!gin) return fail(PGET_EINVAL, "null geometry");
+        Geometry g;
+        std::string msg;
+        pget_status s = build_geometry(*gin, &g, &msg);
+        if (s != PGET_OK) return fail(s, "%s", msg.c_str());
+        if (n_samples) *n_samples = g.T;
+        if (n_banks) *n_banks = g.n_banks;
+        if (fov_radius) *fov_radius = g.r;
+        if (det_pitch) *det_pitch = g.p;
+        if (max_slots) *max_slots = g.max_slots;
+        return PGET_OK;
+    });
 }
 
 pget_status pget_project(pget_ctx* ctx, const pget_lm_params* p, int32_t n, void* lam, void* mu, void* stream) {
-    PGET_RANGE("pget_project");
-    if (!ctx || !lam || !mu) return fail(PGET_EINVAL, "null argument");
-    if (n < 1) return fail(PGET_EINVAL, "n must be >= 1");
-    pget_status s = check_params(p);
-    if (s != PGET_OK) return s;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t nn = (size_t)n * n;
-    if (p->precision == PGET_F64) project_pair<double>((double*)lam, (double*)mu, nn, feas_of(*p), st);
-    else project_pair<float>((float*)lam, (float*)mu, nn, feas_of(*p), st);
-    CK(cudaGetLastError());
-    return PGET_OK;
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_project");
+        if (!ctx || !lam || !mu) return fail(PGET_EINVAL, "null argument");
+        if (n < 1) return fail(PGET_EINVAL, "n must be >= 1");
+        pget_status s = check_params(p);
+        if (s != PGET_OK) return s;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t nn = (size_t)n * n;
+        if (p->precision == PGET_F64) project_pair<double>((double*)lam, (double*)mu, nn, feas_of(*p), st);
+        else project_pair<float>((float*)lam, (float*)mu, nn, feas_of(*p), st);
+        CK(cudaGetLastError());
+        return PGET_OK;
+    });
 }
 
 pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
                           void* lam_io, void* mu_io, pget_lm_report* rep, void* stream) {
-    PGET_RANGE("pget_lm_solve");
-    if (!ctx || !y || !lam_io || !mu_io) return fail(PGET_EINVAL, "null argument");
-    pget_status s = check_params(p);
-    if (s != PGET_OK) return s;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    s = get_workspace(ctx, g, p->precision, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    return w->f64 ? lm_solve_impl<double>(*w, *p, y, lam_io, mu_io, lam_io, mu_io, rep, st)
-                  : lm_solve_impl<float>(*w, *p, y, lam_io, mu_io, lam_io, mu_io, rep, st);
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_lm_solve");
+        if (!ctx || !y || !lam_io || !mu_io) return fail(PGET_EINVAL, "null argument");
+        pget_status s = check_params(p);
+        if (s != PGET_OK) return s;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        s = get_workspace(ctx, g, p->precision, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        return w->f64 ? lm_solve_impl<double>(*w, *p, y, lam_io, mu_io, lam_io, mu_io, rep, st)
+                      : lm_solve_impl<float>(*w, *p, y, lam_io, mu_io, lam_io, mu_io, rep, st);
+    });
 }
 
 pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y_host,
                                void* lam_host, void* mu_host, int32_t init_guess, pget_lm_report* rep, void* stream) {
-    PGET_RANGE("pget_lm_solve_host");
-    if (!ctx || !y_host || !lam_host || !mu_host) return fail(PGET_EINVAL, "null argument");
-    pget_status s = check_params(p);
-    if (s != PGET_OK) return s;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Workspace* w;
-    s = get_workspace(ctx, g, p->precision, &w);
-    if (s != PGET_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t nn = w->nn, e = w->elt;
-    // inputs: y into the measured-data buffer, the initial guess into x (the solve copies
-    // it into the iterate before CG first writes x)
-    CK(cudaMemcpyAsync(w->yb, y_host, e * w->M, cudaMemcpyHostToDevice, st));
-    void* ld = w->x;
-    void* md = (char*)w->x + e * nn;
-    if (init_guess) {
-        s = w->f64 ? init_impl<double>(*w, *p, 0.01, w->yb, ld, md, st)
-                   : init_impl<float>(*w, *p, 0.01, w->yb, ld, md, st);
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_lm_solve_host");
+        if (!ctx || !y_host || !lam_host || !mu_host) return fail(PGET_EINVAL, "null argument");
+        pget_status s = check_params(p);
         if (s != PGET_OK) return s;
-    } else {
-        CK(cudaMemcpyAsync(ld, lam_host, e * nn, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(md, mu_host, e * nn, cudaMemcpyHostToDevice, st));
-    }
-    void* lx = w->x;
-    void* mx = (char*)w->x + e * nn;
-    s = w->f64 ? lm_solve_impl<double>(*w, *p, w->yb, lx, mx, w->q, (char*)w->q + e * nn, rep, st)
-               : lm_solve_impl<float>(*w, *p, w->yb, lx, mx, w->q, (char*)w->q + e * nn, rep, st);
-    if (s != PGET_OK) return s;
-    CK(cudaMemcpyAsync(lam_host, w->q, e * nn, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(mu_host, (char*)w->q + e * nn, e * nn, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return PGET_OK;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        s = get_workspace(ctx, g, p->precision, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t nn = w->nn, e = w->elt;
+        // inputs: y into the measured-data buffer, the initial guess into x (the solve copies
+        // it into the iterate before CG first writes x)
+        CK(cudaMemcpyAsync(w->yb, y_host, e * w->M, cudaMemcpyHostToDevice, st));
+        void* ld = w->x;
+        void* md = (char*)w->x + e * nn;
+        if (init_guess) {
+            s = w->f64 ? init_impl<double>(*w, *p, 0.01, w->yb, ld, md, st)
+                       : init_impl<float>(*w, *p, 0.01, w->yb, ld, md, st);
+            if (s != PGET_OK) return s;
+        } else {
+            CK(cudaMemcpyAsync(ld, lam_host, e * nn, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(md, mu_host, e * nn, cudaMemcpyHostToDevice, st));
+        }
+        void* lx = w->x;
+        void* mx = (char*)w->x + e * nn;
+        s = w->f64 ? lm_solve_impl<double>(*w, *p, w->yb, lx, mx, w->q, (char*)w->q + e * nn, rep, st)
+                   : lm_solve_impl<float>(*w, *p, w->yb, lx, mx, w->q, (char*)w->q + e * nn, rep, st);
+        if (s != PGET_OK) return s;
+        CK(cudaMemcpyAsync(lam_host, w->q, e * nn, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(mu_host, (char*)w->q + e * nn, e * nn, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return PGET_OK;
+    });
 }
 
 pget_status pget_submit(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, const void* y,
                         const void* lam0, const void* mu0, uint64_t* ticket) {
-    PGET_RANGE("pget_submit");
-    if (!ctx || !y || !ticket) return fail(PGET_EINVAL, "null argument");
-    if ((lam0 == nullptr) != (mu0 == nullptr)) return fail(PGET_EINVAL, "give both lam0 and mu0, or neither");
-    pget_status s = check_params(p);
-    if (s != PGET_OK) return s;
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    Geometry geo;
-    std::string key;
-    int groups = 1;
-    size_t need = 0;
-    s = resolve(g, p->precision, &geo, &key, &groups, &need);
-    if (s != PGET_OK) return s;
-    if (ctx->budget && need > ctx->budget)
-        return fail(PGET_ENOMEM, "request needs %zu bytes of workspace, budget is %zu", need, ctx->budget);
-    if (ctx->slots.empty())
-        for (int k = 0; k < max_inflight(); ++k) ctx->slots.emplace_back(new Slot);
-    // a free slot, preferably one whose cached workspace fits this request as is
-    Slot* sl = nullptr;
-    for (auto& c : ctx->slots)
-        if (c->state == Slot::kFree && c->ws && c->ws_key == key) {
-            sl = c.get();
-            break;
-        }
-    if (!sl)
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_submit");
+        if (!ctx || !y || !ticket) return fail(PGET_EINVAL, "null argument");
+        if ((lam0 == nullptr) != (mu0 == nullptr)) return fail(PGET_EINVAL, "give both lam0 and mu0, or neither");
+        pget_status s = check_params(p);
+        if (s != PGET_OK) return s;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Geometry geo;
+        std::string key;
+        int groups = 1;
+        size_t need = 0;
+        s = resolve(g, p->precision, &geo, &key, &groups, &need);
+        if (s != PGET_OK) return s;
+        if (ctx->budget && need > ctx->budget)
+            return fail(PGET_ENOMEM, "request needs %zu bytes of workspace, budget is %zu", need, ctx->budget);
+        if (ctx->slots.empty())
+            for (int k = 0; k < max_inflight(); ++k) ctx->slots.emplace_back(new Slot);
+        // a free slot, preferably one whose cached workspace fits this request as is
+        Slot* sl = nullptr;
         for (auto& c : ctx->slots)
-            if (c->state == Slot::kFree && !c->ws) {
+            if (c->state == Slot::kFree && c->ws && c->ws_key == key) {
                 sl = c.get();
                 break;
             }
-    if (!sl)
-        for (auto& c : ctx->slots)
-            if (c->state == Slot::kFree) {
-                sl = c.get();
-                break;
-            }
-    if (!sl) return fail(PGET_EAGAIN, "all %zu serving slots are busy", ctx->slots.size());
-    if (!(sl->ws && sl->ws_key == key)) {
-        // park the slot's workspace (idle: its last request was collected) and take an
-        // idle one of this geometry if there is one
-        if (sl->ws) ctx->pool.push_back({sl->ws_key, std::move(sl->ws), ++ctx->use_clock});
-        sl->ws_key.clear();
-        for (size_t i = 0; i < ctx->pool.size(); ++i)
-            if (ctx->pool[i].key == key) {
-                sl->ws = std::move(ctx->pool[i].ws);
-                sl->ws_key = key;
-                ctx->pool.erase(ctx->pool.begin() + i);
-                break;
-            }
-    }
-    if (!sl->ws) {
-        // a new workspace: make room by freeing idle ones, least recently used first
-        auto held = [&] { return serving_bytes(ctx) + (ctx->ws ? ctx->ws->bytes : 0); };
-        const size_t cap = ctx->budget ? ctx->budget : default_serving_cap();
-        while (held() + need > cap && evict_idle(ctx)) {
+        if (!sl)
+            for (auto& c : ctx->slots)
+                if (c->state == Slot::kFree && !c->ws) {
+                    sl = c.get();
+                    break;
+                }
+        if (!sl)
+            for (auto& c : ctx->slots)
+                if (c->state == Slot::kFree) {
+                    sl = c.get();
+                    break;
+                }
+        if (!sl) return fail(PGET_EAGAIN, "all %zu serving slots are busy", ctx->slots.size());
+        if (!(sl->ws && sl->ws_key == key)) {
+            // park the slot's workspace (idle: its last request was collected) and take an
+            // idle one of this geometry if there is one
+            if (sl->ws) ctx->pool.push_back({sl->ws_key, std::move(sl->ws), ++ctx->use_clock});
+            sl->ws_key.clear();
+            for (size_t i = 0; i < ctx->pool.size(); ++i)
+                if (ctx->pool[i].key == key) {
+                    sl->ws = std::move(ctx->pool[i].ws);
+                    sl->ws_key = key;
+                    ctx->pool.erase(ctx->pool.begin() + i);
+                    break;
+                }
         }
-        if (ctx->budget && held() + need > ctx->budget)
-            return fail(PGET_EAGAIN, "device memory budget in use (%zu of %zu bytes held, %zu needed)", held(),
-                        ctx->budget, need);
-        std::unique_ptr<Workspace> w;
-        s = make_workspace(ctx, std::move(geo), p->precision, groups, &w);
+        if (!sl->ws) {
+            // a new workspace: make room by freeing idle ones, least recently used first
+            auto held = [&] { return serving_bytes(ctx) + (ctx->ws ? ctx->ws->bytes : 0); };
+            const size_t cap = ctx->budget ? ctx->budget : default_serving_cap();
+            while (held() + need > cap && evict_idle(ctx)) {
+            }
+            if (ctx->budget && held() + need > ctx->budget)
+                return fail(PGET_EAGAIN, "device memory budget in use (%zu of %zu bytes held, %zu needed)", held(),
+                            ctx->budget, need);
+            std::unique_ptr<Workspace> w;
+            s = make_workspace(ctx, std::move(geo), p->precision, groups, &w);
+            if (s != PGET_OK) return s;
+            sl->ws = std::move(w);
+            sl->ws_key = key;
+        }
+        if (!sl->stream) CK(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
+        if (!sl->done) CK(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
+        Workspace& w = *sl->ws;
+        cudaStream_t st = sl->stream;
+        const size_t nn = w.nn, e = w.elt;
+        // inputs into slot memory; the caller may free its buffers when this call returns
+        CK(cudaMemcpyAsync(w.yb, y, e * w.M, cudaMemcpyDeviceToDevice, st));
+        if (lam0) {
+            CK(cudaMemcpyAsync(w.u, lam0, e * nn, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync((char*)w.u + e * nn, mu0, e * nn, cudaMemcpyDeviceToDevice, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        if (!lam0) {
+            s = w.f64 ? init_async<double>(w, *p, 0.01, w.u, (char*)w.u + e * nn, st)
+                      : init_async<float>(w, *p, 0.01, w.u, (char*)w.u + e * nn, st);
+            if (s != PGET_OK) return s;
+        }
+        s = w.f64 ? lm_launch<double>(w, *p, st) : lm_launch<float>(w, *p, st);
         if (s != PGET_OK) return s;
-        sl->ws = std::move(w);
-        sl->ws_key = key;
-    }
-    if (!sl->stream) CK(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
-    if (!sl->done) CK(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
-    Workspace& w = *sl->ws;
-    cudaStream_t st = sl->stream;
-    const size_t nn = w.nn, e = w.elt;
-    // inputs into slot memory; the caller may free its buffers when this call returns
-    CK(cudaMemcpyAsync(w.yb, y, e * w.M, cudaMemcpyDeviceToDevice, st));
-    if (lam0) {
-        CK(cudaMemcpyAsync(w.u, lam0, e * nn, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync((char*)w.u + e * nn, mu0, e * nn, cudaMemcpyDeviceToDevice, st));
-    }
-    CK(cudaStreamSynchronize(st));
-    if (!lam0) {
-        s = w.f64 ? init_async<double>(w, *p, 0.01, w.u, (char*)w.u + e * nn, st)
-                  : init_async<float>(w, *p, 0.01, w.u, (char*)w.u + e * nn, st);
-        if (s != PGET_OK) return s;
-    }
-    s = w.f64 ? lm_launch<double>(w, *p, st) : lm_launch<float>(w, *p, st);
-    if (s != PGET_OK) return s;
-    CK(cudaEventRecord(sl->done, st));
-    sl->state = Slot::kRunning;
-    sl->ticket = ctx->next_ticket++;
-    *ticket = sl->ticket;
-    return PGET_OK;
+        CK(cudaEventRecord(sl->done, st));
+        sl->state = Slot::kRunning;
+        sl->ticket = ctx->next_ticket++;
+        *ticket = sl->ticket;
+        return PGET_OK;
+    });
 }
 
 pget_status pget_poll(pget_ctx* ctx, uint64_t ticket, void* lam_out, void* mu_out, pget_lm_report* rep, int* done) {
-    if (!ctx || !done) return fail(PGET_EINVAL, "null argument");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    *done = 0;
-    Slot* sl = nullptr;
-    for (auto& c : ctx->slots)
-        if (c->state != Slot::kFree && c->ticket == ticket) sl = c.get();
-    if (!sl) return fail(PGET_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
-    if (sl->state == Slot::kRunning) {
-        cudaError_t q = cudaEventQuery(sl->done);
-        if (q == cudaErrorNotReady) return PGET_OK;
-        if (q != cudaSuccess) {
-            sl->state = Slot::kFree;
-            sl->ws.reset();
-            sl->ws_key.clear();
-            *done = 1;
-            return fail(PGET_ECUDA, "request %llu: %s", (unsigned long long)ticket, cudaGetErrorString(q));
+    return guarded([&]() -> pget_status {
+        if (!ctx || !done) return fail(PGET_EINVAL, "null argument");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        *done = 0;
+        Slot* sl = nullptr;
+        for (auto& c : ctx->slots)
+            if (c->state != Slot::kFree && c->ticket == ticket) sl = c.get();
+        if (!sl) return fail(PGET_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+        if (sl->state == Slot::kRunning) {
+            cudaError_t q = cudaEventQuery(sl->done);
+            if (q == cudaErrorNotReady) return PGET_OK;
+            if (q != cudaSuccess) {
+                sl->state = Slot::kFree;
+                sl->ws.reset();
+                sl->ws_key.clear();
+                *done = 1;
+                return fail(PGET_ECUDA, "request %llu: %s", (unsigned long long)ticket, cudaGetErrorString(q));
+            }
+            sl->state = Slot::kDone;
         }
-        sl->state = Slot::kDone;
-    }
-    Workspace& w = *sl->ws;
-    const size_t nn = w.nn, e = w.elt;
-    if (lam_out) CK(cudaMemcpyAsync(lam_out, w.u, e * nn, cudaMemcpyDeviceToDevice, sl->stream));
-    if (mu_out) CK(cudaMemcpyAsync(mu_out, (char*)w.u + e * nn, e * nn, cudaMemcpyDeviceToDevice, sl->stream));
-    CK(cudaStreamSynchronize(sl->stream));
-    pget_status s = lm_finish(w, rep);
-    sl->state = Slot::kFree;
-    *done = 1;
-    return s;
+        Workspace& w = *sl->ws;
+        const size_t nn = w.nn, e = w.elt;
+        if (lam_out) CK(cudaMemcpyAsync(lam_out, w.u, e * nn, cudaMemcpyDeviceToDevice, sl->stream));
+        if (mu_out) CK(cudaMemcpyAsync(mu_out, (char*)w.u + e * nn, e * nn, cudaMemcpyDeviceToDevice, sl->stream));
+        CK(cudaStreamSynchronize(sl->stream));
+        pget_status s = lm_finish(w, rep);
+        sl->state = Slot::kFree;
+        *done = 1;
+        return s;
+    });
 }
 
 pget_status pget_cancel(pget_ctx* ctx, uint64_t ticket) {
-    if (!ctx) return fail(PGET_EINVAL, "null ctx");
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    DeviceGuard dg(ctx->device);
-    for (auto& c : ctx->slots)
-        if (c->state != Slot::kFree && c->ticket == ticket) {
-            // kernels cannot be aborted once queued: wait for them, then drop the result
-            cudaStreamSynchronize(c->stream);
-            c->state = Slot::kFree;
-            return PGET_OK;
-        }
-    return fail(PGET_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    return guarded([&]() -> pget_status {
+        if (!ctx) return fail(PGET_EINVAL, "null ctx");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        for (auto& c : ctx->slots)
+            if (c->state != Slot::kFree && c->ticket == ticket) {
+                // kernels cannot be aborted once queued: wait for them, then drop the result
+                cudaStreamSynchronize(c->stream);
+                c->state = Slot::kFree;
+                return PGET_OK;
+            }
+        return fail(PGET_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    });
 }
 
 int32_t pget_inflight(pget_ctx* ctx) {

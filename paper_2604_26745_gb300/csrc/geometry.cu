@@ -23,7 +23,7 @@ pget_status build_geometry(const pget_geometry& in, Geometry* G, std::string* ms
     g.n_sub = in.n_sub;
     g.collimator = in.collimator;
     if (g.n < 2 || g.n > 16384) return *msg = "n must be in [2, 16384]", PGET_EINVAL;
-    if (g.n_angles < 1) return *msg = "n_angles must be >= 1", PGET_EINVAL;
+    if (g.n_angles < 1 || g.n_angles > kMaxAngles) return *msg = "n_angles must be in [1, 1048576]", PGET_EINVAL;
     if (g.n_det < 1) return *msg = "n_det must be >= 1", PGET_EINVAL;
     if (g.n_sub < 1 || g.n_sub > kMaxSub) return *msg = "n_sub must be in [1, 64]", PGET_EINVAL;
     if (g.collimator != 0 && g.collimator != 1) return *msg = "collimator must be 0 or 1", PGET_EINVAL;

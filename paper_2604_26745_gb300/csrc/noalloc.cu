@@ -62,7 +62,7 @@ extern "C" pget_status pget_forward_noalloc(const pget_geometry* gin, int32_t pr
 
     // ---- geometry (same definitions as the context path, computed without the heap)
     const int n = gin->n, na = gin->n_angles, nd = gin->n_det, S = gin->n_sub, col = gin->collimator;
-    if (n < 2 || n > 16384 || na < 1 || nd < 1 || S < 1 || S > kMaxSub || (col != 0 && col != 1)) return PGET_EINVAL;
+    if (n < 2 || n > 16384 || na < 1 || na > kMaxAngles || nd < 1 || S < 1 || S > kMaxSub || (col != 0 && col != 1)) return PGET_EINVAL;
     const int nbk = gin->n_banks == 0 ? (nd == 182 ? 2 : 1) : gin->n_banks;
     if ((nbk != 1 && nbk != 2) || nd % nbk) return PGET_EINVAL;
     const int nb = nd / nbk;

@@ -12,7 +12,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpget.so")
 
-PGET_OK, PGET_EINVAL, PGET_ENOMEM, PGET_EAGAIN, PGET_ECUDA, PGET_ETIMEOUT, PGET_ENUMERIC, PGET_ENOTFOUND = range(8)
+PGET_OK, PGET_EINVAL, PGET_ENOMEM, PGET_EAGAIN, PGET_ECUDA, PGET_ETIMEOUT, PGET_ENUMERIC, PGET_ENOTFOUND, PGET_EINTERNAL = range(9)
 PGET_F64, PGET_F32, PGET_F32_KAHAN = 0, 1, 2
 PGET_TRACE = 256
 

@@ -152,3 +152,27 @@ int main(void) {
         assert int(f[9]) != 0 and int(f[10]) == 1 and int(f[11]) == 1
     assert int(f[12]) == 1  # PGET_EINVAL for null arrays, through the profiler range
     assert out[1].startswith("pget-gb300")
+
+
+def test_status_codes_match_header(lib):
+    """The binding's status constants are the header's enum, value for value."""
+    from paper_2604_26745_gb300 import pget
+    src = open(HEADER).read()
+    body = src[src.index("typedef enum {"):src.index("} pget_status;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    codes = dict((k, int(v)) for k, v in re.findall(r"(PGET_[A-Z]+)\s*=\s*(\d+)", body))
+    assert len(codes) == 9 and sorted(codes.values()) == list(range(9))
+    for k, v in codes.items():
+        assert getattr(pget, k) == v, k
+
+
+def test_geometry_limits(lib):
+    """Sizes outside the documented ranges are rejected on the host, never computed."""
+    from paper_2604_26745_gb300 import pget
+    assert pget.geometry_info(pget.geometry(16, 4096, 91))["n_banks"] == 1
+    for bad in (dict(n=16, n_angles=(1 << 20) + 1, n_det=91), dict(n=16, n_angles=0, n_det=91),
+                dict(n=16385, n_angles=8, n_det=91), dict(n=1, n_angles=8, n_det=91),
+                dict(n=16, n_angles=8, n_det=91, n_sub=65)):
+        kw = dict(bad)
+        with pytest.raises(ValueError):
+            pget.geometry_info(pget.geometry(kw.pop("n"), kw.pop("n_angles"), kw.pop("n_det"), **kw))
