@@ -85,6 +85,8 @@ def _args():
     ap.add_argument("--impl", default="pget", choices=["pget", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dist-timeout", type=float, default=300.0,
+                    help="seconds a collective waits for the other ranks before it fails")
     return ap.parse_args()
 
 
@@ -139,6 +141,17 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def init_dist(backend: str, timeout_s: float, **kw):
+    """The process group of a multi-rank run, with a bounded timeout: a rank that dies or
+    never arrives makes the others' next collective fail after timeout_s instead of
+    hanging.  Ranks leave only between steps, with none of their kernels in flight."""
+    import datetime
+
+    import torch.distributed as dist
+    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=timeout_s), **kw)
+    return dist
 
 
 def rank_request_ids(rank: int, world: int, per_rank: int) -> list:
@@ -257,9 +270,7 @@ def main():
     dev = f"cuda:{local}"
     dist = None
     if world > 1:
-        import torch.distributed as dist_
-        dist_.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-        dist = dist_
+        dist = init_dist("nccl" if torch.cuda.is_available() else "gloo", args.dist_timeout)
     W = WORKLOAD
     ctx = P.Context(local)
     prec = P.PGET_F32_KAHAN

@@ -50,3 +50,52 @@ def test_two_ranks_weak_scaling():
     assert tmax0 == tmax1 and abs(tmax0 - max(e0, e1)) < 1e-12
     assert not set(ids0) & set(ids1)  # independent work per rank
     assert len(ids0) == len(ids1) == 8
+
+
+def _leaver(rank, world, port, q, how):
+    import time
+
+    import torch
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import bench
+    dist = bench.init_dist("gloo", 5.0, rank=rank, world_size=world)
+    t = torch.ones(1)
+    dist.all_reduce(t)  # one step together
+    if rank == 1:
+        if how == "stall":
+            time.sleep(40.0)  # alive, but never joins another collective
+        os._exit(0)  # leaves between steps, without a word to the others
+    time.sleep(0.5)
+    t0 = time.perf_counter()
+    try:
+        dist.all_reduce(t)
+        q.put(("returned", time.perf_counter() - t0))
+    except Exception as e:  # the failure the survivor must see
+        q.put((type(e).__name__, time.perf_counter() - t0))
+    q.close()
+    q.join_thread()  # the report is written before the process ends
+    os._exit(0)
+
+
+@pytest.mark.parametrize("how", ["exit", "stall"])
+def test_a_rank_that_leaves_fails_the_next_collective(how):
+    """Failure detection on the host.
+
+    Rank 1 leaves between steps, either by exiting or by stalling alive. Rank 0's next
+    collective must end with an error instead of waiting for ever. An exit closes the
+    connection at once. A stall is caught by the process group's timeout: 5 s here, set
+    in the bench by --dist-timeout."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_leaver, args=(r, 2, port, q, how)) for r in range(2)]
+    for p in procs:
+        p.start()
+    what, waited = q.get(timeout=120)
+    procs[0].join(timeout=60)
+    procs[1].kill()  # the stalled rank: this test's own child process
+    procs[1].join(timeout=60)
+    assert what != "returned", "the collective completed without the rank that left"
+    assert waited < 30.0
+    if how == "stall":
+        assert waited >= 4.0  # ended by the timeout, not by a closed connection
