@@ -149,13 +149,33 @@ def _check(status: int, ctx=None):
         raise PgetError(status, msg)
 
 
-def _ptr(t) -> int:
+def _arr(t, precision, numel: int, device, name: str, host: bool = False):
+    """Pointer of an array argument, after the checks a raw pointer cannot carry: a
+    contiguous tensor on the right side (the context's CUDA device, or the host), with the
+    precision's element size (8 bytes for PGET_F64, else 4) and at least numel elements.
+    A mismatch raises here instead of reaching the kernels as an out-of-range pointer.
+    precision None skips the element-size check (pget_poll: the request's precision)."""
     if t is None:
         return None
     if not isinstance(t, torch.Tensor):
-        raise TypeError("expected a torch tensor")
+        raise TypeError(f"{name}: expected a torch tensor")
+    if host:
+        if t.is_cuda:
+            raise ValueError(f"{name} must be a CPU tensor")
+    else:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if device is not None and t.device.index != device:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{device}")
     if not t.is_contiguous():
-        raise ValueError("tensor must be contiguous")
+        raise ValueError(f"{name} must be contiguous")
+    if precision is not None:
+        want = 8 if precision == PGET_F64 else 4
+        if not t.is_floating_point() or t.element_size() != want:
+            raise ValueError(f"{name} is {t.dtype}; precision {precision} takes "
+                             f"{'float64' if want == 8 else 'float32'}")
+    if t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, {numel} needed")
     return t.data_ptr()
 
 
@@ -251,7 +271,9 @@ class Context:
 def pget_forward(ctx: Context, g: pget_geometry, precision: int, lam, mu, y=None, stream=None):
     if y is None:
         y = torch.empty((g.n_angles, g.n_det), dtype=lam.dtype, device=lam.device)
-    _check(load().pget_forward(ctx.h, C.byref(g), precision, _ptr(lam), _ptr(mu), _ptr(y),
+    nn, M, d = g.n * g.n, g.n_angles * g.n_det, ctx.device
+    _check(load().pget_forward(ctx.h, C.byref(g), precision, _arr(lam, precision, nn, d, "lam"),
+                               _arr(mu, precision, nn, d, "mu"), _arr(y, precision, M, d, "y"),
                                _stream(stream)), ctx.h)
     return y
 
@@ -259,8 +281,11 @@ def pget_forward(ctx: Context, g: pget_geometry, precision: int, lam, mu, y=None
 def pget_jvp(ctx: Context, g: pget_geometry, precision: int, lam, mu, dlam, dmu, dy=None, stream=None):
     if dy is None:
         dy = torch.empty((g.n_angles, g.n_det), dtype=lam.dtype, device=lam.device)
-    _check(load().pget_jvp(ctx.h, C.byref(g), precision, _ptr(lam), _ptr(mu), _ptr(dlam),
-                           _ptr(dmu), _ptr(dy), _stream(stream)), ctx.h)
+    nn, M, d = g.n * g.n, g.n_angles * g.n_det, ctx.device
+    _check(load().pget_jvp(ctx.h, C.byref(g), precision, _arr(lam, precision, nn, d, "lam"),
+                           _arr(mu, precision, nn, d, "mu"), _arr(dlam, precision, nn, d, "dlam"),
+                           _arr(dmu, precision, nn, d, "dmu"), _arr(dy, precision, M, d, "dy"),
+                           _stream(stream)), ctx.h)
     return dy
 
 
@@ -270,8 +295,11 @@ def pget_vjp(ctx: Context, g: pget_geometry, precision: int, lam, mu, r, glam=No
         glam = torch.empty_like(lam)
     if gmu is None:
         gmu = torch.empty_like(mu)
-    _check(load().pget_vjp(ctx.h, C.byref(g), precision, _ptr(lam), _ptr(mu), _ptr(r),
-                           _ptr(glam), _ptr(gmu), _stream(stream)), ctx.h)
+    nn, M, d = g.n * g.n, g.n_angles * g.n_det, ctx.device
+    _check(load().pget_vjp(ctx.h, C.byref(g), precision, _arr(lam, precision, nn, d, "lam"),
+                           _arr(mu, precision, nn, d, "mu"), _arr(r, precision, M, d, "r"),
+                           _arr(glam, precision, nn, d, "glam"), _arr(gmu, precision, nn, d, "gmu"),
+                           _stream(stream)), ctx.h)
     return glam, gmu
 
 
@@ -280,7 +308,9 @@ def pget_reg_apply(ctx: Context, n: int, precision: int, alpha: float, eps: floa
     if out is None:
         out = torch.empty_like(v)
     val = C.c_double(0.0)
-    _check(load().pget_reg_apply(ctx.h, n, precision, alpha, eps, _ptr(u), _ptr(v), _ptr(out),
+    nn, d = int(n) * int(n), ctx.device
+    _check(load().pget_reg_apply(ctx.h, n, precision, alpha, eps, _arr(u, precision, nn, d, "u"),
+                                 _arr(v, precision, nn, d, "v"), _arr(out, precision, nn, d, "out"),
                                  C.byref(val) if want_value else None, _stream(stream)), ctx.h)
     return (out, val.value) if want_value else out
 
@@ -290,8 +320,10 @@ def pget_cg_solve(ctx: Context, g: pget_geometry, p: pget_lm_params, lam, mu, nu
     if x is None:
         x = torch.empty_like(rhs)
     it = C.c_int32(0)
-    _check(load().pget_cg_solve(ctx.h, C.byref(g), C.byref(p), _ptr(lam), _ptr(mu), float(nu),
-                                _ptr(rhs), _ptr(x), C.byref(it), _stream(stream)), ctx.h)
+    q, nn, d = p.precision, g.n * g.n, ctx.device
+    _check(load().pget_cg_solve(ctx.h, C.byref(g), C.byref(p), _arr(lam, q, nn, d, "lam"),
+                                _arr(mu, q, nn, d, "mu"), float(nu), _arr(rhs, q, 2 * nn, d, "rhs"),
+                                _arr(x, q, 2 * nn, d, "x"), C.byref(it), _stream(stream)), ctx.h)
     return x, it.value
 
 
@@ -299,8 +331,10 @@ def pget_initial_guess(ctx: Context, g: pget_geometry, p: pget_lm_params, y, mu_
                        stream=None):
     lam = torch.empty((g.n, g.n), dtype=y.dtype, device=y.device)
     mu = torch.empty_like(lam)
-    _check(load().pget_initial_guess(ctx.h, C.byref(g), C.byref(p), float(mu_init), _ptr(y),
-                                     _ptr(lam), _ptr(mu), _stream(stream)), ctx.h)
+    q, nn, M, d = p.precision, g.n * g.n, g.n_angles * g.n_det, ctx.device
+    _check(load().pget_initial_guess(ctx.h, C.byref(g), C.byref(p), float(mu_init), _arr(y, q, M, d, "y"),
+                                     _arr(lam, q, nn, d, "lam"), _arr(mu, q, nn, d, "mu"),
+                                     _stream(stream)), ctx.h)
     return lam, mu
 
 
@@ -311,8 +345,10 @@ def pget_lm_trial(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam, mu,
     if s_out is None:
         s_out = lam.new_empty((2,) + tuple(lam.shape))
     rep = pget_trial_report()
-    _check(load().pget_lm_trial(ctx.h, C.byref(g), C.byref(p), _ptr(y), _ptr(lam), _ptr(mu), float(nu),
-                                _ptr(s_out), C.byref(rep), _stream(stream)), ctx.h)
+    q, nn, M, d = p.precision, g.n * g.n, g.n_angles * g.n_det, ctx.device
+    _check(load().pget_lm_trial(ctx.h, C.byref(g), C.byref(p), _arr(y, q, M, d, "y"), _arr(lam, q, nn, d, "lam"),
+                                _arr(mu, q, nn, d, "mu"), float(nu), _arr(s_out, q, 2 * nn, d, "s_out"),
+                                C.byref(rep), _stream(stream)), ctx.h)
     return s_out, _fields(rep)
 
 
@@ -320,9 +356,11 @@ def pget_proposal_check(ctx: Context, g: pget_geometry, p: pget_lm_params, y, la
                         prop_mu, stream=None) -> dict:
     """The convergence check of Alg. 2 for the proposal (prop_lam, prop_mu)."""
     rep = pget_check_report()
-    _check(load().pget_proposal_check(ctx.h, C.byref(g), C.byref(p), _ptr(y), _ptr(lam), _ptr(mu),
-                                      _ptr(s_step), _ptr(prop_lam), _ptr(prop_mu), C.byref(rep),
-                                      _stream(stream)), ctx.h)
+    q, nn, M, d = p.precision, g.n * g.n, g.n_angles * g.n_det, ctx.device
+    _check(load().pget_proposal_check(ctx.h, C.byref(g), C.byref(p), _arr(y, q, M, d, "y"),
+                                      _arr(lam, q, nn, d, "lam"), _arr(mu, q, nn, d, "mu"),
+                                      _arr(s_step, q, 2 * nn, d, "s_step"), _arr(prop_lam, q, nn, d, "prop_lam"),
+                                      _arr(prop_mu, q, nn, d, "prop_mu"), C.byref(rep), _stream(stream)), ctx.h)
     return _fields(rep)
 
 
@@ -333,27 +371,30 @@ def pget_project(ctx: Context, p: pget_lm_params, lam, mu, stream=None):
         raise ValueError("lam and mu must be square images of one shape")
     if not (lam.is_contiguous() and mu.is_contiguous()):
         raise ValueError("lam and mu must be contiguous")
-    _check(load().pget_project(ctx.h, C.byref(p), int(lam.shape[0]), _ptr(lam), _ptr(mu), _stream(stream)), ctx.h)
+    q, nn, d = p.precision, lam.numel(), ctx.device
+    _check(load().pget_project(ctx.h, C.byref(p), int(lam.shape[0]), _arr(lam, q, nn, d, "lam"),
+                               _arr(mu, q, nn, d, "mu"), _stream(stream)), ctx.h)
     return lam, mu
 
 
 def pget_lm_solve(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam, mu, stream=None):
     """Solve in place (lam, mu: initial guess in, result out); returns the report dict."""
     rep = pget_lm_report()
-    _check(load().pget_lm_solve(ctx.h, C.byref(g), C.byref(p), _ptr(y), _ptr(lam), _ptr(mu),
-                                C.byref(rep), _stream(stream)), ctx.h)
+    q, nn, M, d = p.precision, g.n * g.n, g.n_angles * g.n_det, ctx.device
+    _check(load().pget_lm_solve(ctx.h, C.byref(g), C.byref(p), _arr(y, q, M, d, "y"), _arr(lam, q, nn, d, "lam"),
+                                _arr(mu, q, nn, d, "mu"), C.byref(rep), _stream(stream)), ctx.h)
     return rep.to_dict()
 
 
 def pget_lm_solve_host(ctx: Context, g: pget_geometry, p: pget_lm_params, y_host, lam_host,
                        mu_host, init_guess: bool = True, stream=None):
     """Host-buffer solve (y_host, lam_host, mu_host: CPU tensors, pinned for async copies)."""
-    for t in (y_host, lam_host, mu_host):
-        if t.is_cuda or not t.is_contiguous():
-            raise ValueError("host tensors must be contiguous CPU tensors")
+    q, nn, M = p.precision, g.n * g.n, g.n_angles * g.n_det
+    y_p = _arr(y_host, q, M, None, "y_host", host=True)
+    lam_p = _arr(lam_host, q, nn, None, "lam_host", host=True)
+    mu_p = _arr(mu_host, q, nn, None, "mu_host", host=True)
     rep = pget_lm_report()
-    _check(load().pget_lm_solve_host(ctx.h, C.byref(g), C.byref(p), y_host.data_ptr(),
-                                     lam_host.data_ptr(), mu_host.data_ptr(), int(bool(init_guess)),
+    _check(load().pget_lm_solve_host(ctx.h, C.byref(g), C.byref(p), y_p, lam_p, mu_p, int(bool(init_guess)),
                                      C.byref(rep), _stream(stream)), ctx.h)
     return rep.to_dict()
 
@@ -362,8 +403,9 @@ def pget_submit(ctx: Context, g: pget_geometry, p: pget_lm_params, y, lam0=None,
     """Queue a reconstruction; returns its ticket.  Raises PgetError (status PGET_EAGAIN
     when no slot or memory is free right now)."""
     t = C.c_uint64(0)
-    _check(load().pget_submit(ctx.h, C.byref(g), C.byref(p), _ptr(y), _ptr(lam0), _ptr(mu0),
-                              C.byref(t)), ctx.h)
+    q, nn, M, d = p.precision, g.n * g.n, g.n_angles * g.n_det, ctx.device
+    _check(load().pget_submit(ctx.h, C.byref(g), C.byref(p), _arr(y, q, M, d, "y"), _arr(lam0, q, nn, d, "lam0"),
+                              _arr(mu0, q, nn, d, "mu0"), C.byref(t)), ctx.h)
     return t.value
 
 
@@ -371,8 +413,9 @@ def pget_poll(ctx: Context, ticket: int, lam_out=None, mu_out=None):
     """(done, report): report is None while the request still runs."""
     rep = pget_lm_report()
     done = C.c_int(0)
-    _check(load().pget_poll(ctx.h, C.c_uint64(ticket), _ptr(lam_out), _ptr(mu_out), C.byref(rep),
-                            C.byref(done)), ctx.h)
+    d = ctx.device
+    _check(load().pget_poll(ctx.h, C.c_uint64(ticket), _arr(lam_out, None, 0, d, "lam_out"),
+                            _arr(mu_out, None, 0, d, "mu_out"), C.byref(rep), C.byref(done)), ctx.h)
     return bool(done.value), (rep.to_dict() if done.value else None)
 
 
@@ -387,7 +430,9 @@ def pget_inflight(ctx: Context) -> int:
 def pget_forward_noalloc(g: pget_geometry, precision: int, lam, mu, y, stream=None) -> int:
     """Forward projection without a context and without allocating (see pget.h); y must
     be preallocated.  Returns the pget status (no exception, no message)."""
-    return load().pget_forward_noalloc(C.byref(g), precision, _ptr(lam), _ptr(mu), _ptr(y),
+    nn, M = g.n * g.n, g.n_angles * g.n_det
+    return load().pget_forward_noalloc(C.byref(g), precision, _arr(lam, precision, nn, None, "lam"),
+                                       _arr(mu, precision, nn, None, "mu"), _arr(y, precision, M, None, "y"),
                                        _stream(stream))
 
 
