@@ -32,7 +32,8 @@ CASES = {
     "two_banks_s5": (40, 36, 182, 5, 1, 4),
     "box_even_s4": (36, 20, 182, 4, 0, 3),
     "odd_n_s3": (27, 17, 91, 3, 1, 3),
-    # 1009 distinct rays per view: more than 896, so the 64-register instantiation runs
+    # 1009 lattice slots per view (910 on a sub-ray): more than 896 threads, so the
+    # 64-register instantiation runs
     "many_rays_s10": (24, 8, 182, 10, 1, 3),
 }
 
