@@ -13,7 +13,8 @@
  *   - Arrays are caller-owned, contiguous DEVICE pointers unless a name ends in _host.
  *     Element type: double for PGET_F64, float for PGET_F32 and PGET_F32_KAHAN.
  *     The library never frees caller memory and never keeps a caller pointer after a
- *     call returns.
+ *     call returns, with one exception: a request queued by pget_submit reads the
+ *     geometry-prior mask p->geo_mask while it runs.
  *   - stream is a cudaStream_t passed as void* (NULL: the legacy default stream).
  *     forward / jvp / vjp / reg_apply only enqueue work and return; they may reuse
  *     context workspace, so calls on one context must not overlap on different streams.
