@@ -6,7 +6,8 @@
 - a brute-force dense J on an 8 x 8 grid, columns from JVPs and rows from VJPs;
 - the gradient of 1/2 |A(u) - y|^2 against finite differences;
 - the attenuation part of the JVP converging to the derivative of the concentric-disk
-  closed form.
+  closed form;
+- the Lipschitz bound of the derivative that Sec. 2.1 proves (a loose bound: a weak pin).
 """
 import numpy as np
 import pytest
@@ -142,3 +143,44 @@ def test_closed_form_derivative_by_differences():
             m * np.sqrt(np.clip(8.0 ** 2 - s ** 2, 0, None)))
         fd = (y(mu0 + h) - y(mu0 - h)) / (2 * h)
         np.testing.assert_allclose(_closed_disk_dmu(s, 1.0, mu0, 8.0, 11.0), fd, rtol=1e-6, atol=1e-7)
+
+
+def test_lipschitz_bound_of_the_derivative(O):
+    """The Lipschitz lemma of Sec. 2.1 bounds ‖DF(u1) − DF(u2)‖ by
+    2 sqrt(π r)(1 + C_λ)(‖λ1 − λ2‖ + ‖μ1 − μ2‖), with C_λ = sqrt(2r)·max λ.
+
+    The left side is the discrete operator norm of the JVP difference: power iteration
+    with the VJPs, data weighted by ds dθ = p · 2π/N_a per bin, pixel area 1. The bound
+    holds with a ratio of about 0.01. This weak pin catches only gross errors of scale in
+    the derivative; the other pins do the fine work."""
+    import math
+    N, Na = 24, 24
+    g = O.geom(N, Na, 91, n_sub=1)
+    info = O.geom_info(g)
+    r, wbin = info["radius"], info["pitch"] * 2 * math.pi / Na
+    rs = np.random.default_rng(0)
+    ph = synth.lattice_phantom(N, 3, seed=5)
+    l1, m1 = ph.lam, ph.mu
+    for scale in (1e-1, 1e-2):
+        dl, dm = scale * rs.uniform(0, 1, (N, N)), 0.1 * scale * rs.uniform(0, 1, (N, N))
+        l2, m2 = l1 + dl, m1 + dm
+
+        def op(x):
+            a, b = x[:N * N].reshape(N, N), x[N * N:].reshape(N, N)
+            return O.jvp(g, l1, m1, a, b) - O.jvp(g, l2, m2, a, b)
+
+        def op_t(y):
+            a1, b1 = O.vjp(g, l1, m1, y)
+            a2, b2 = O.vjp(g, l2, m2, y)
+            return np.concatenate([(a1 - a2).ravel(), (b1 - b2).ravel()])
+
+        x = rs.standard_normal(2 * N * N)
+        x /= np.linalg.norm(x)
+        for _ in range(40):
+            x = op_t(wbin * op(x))
+            nx = np.linalg.norm(x)
+            x /= nx
+        lhs = math.sqrt(nx)
+        c_lam = math.sqrt(2 * r) * max(l1.max(), l2.max())
+        rhs = 2 * math.sqrt(math.pi * r) * (1 + c_lam) * (np.linalg.norm(dl) + np.linalg.norm(dm))
+        assert 0 < lhs <= rhs, (scale, lhs, rhs)
