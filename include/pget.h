@@ -261,8 +261,9 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
                                 const void* s_step, const void* prop_lam, const void* prop_mu,
                                 pget_check_report* rep, void* stream);
 
-/* Derived sizes of a geometry (any output pointer may be NULL): samples per ray T (the
- * length of the depth tables), detector banks, field-of-view radius r, detector pitch p
+/* Derived sizes of a geometry (any output pointer may be NULL; host only, no context):
+ * samples per ray T of the discretised ray integral of Eq. (5) (the length of the depth
+ * tables), detector banks and pitch p of the device of Sec. 2, field-of-view radius r,
  * and distinct rays per view (slots).  PGET_EINVAL for an invalid geometry. */
 pget_status pget_geometry_info(const pget_geometry* g, int32_t* n_samples, int32_t* n_banks, double* fov_radius,
                                double* det_pitch, int32_t* max_slots);
@@ -275,7 +276,8 @@ pget_status pget_geometry_info(const pget_geometry* g, int32_t* n_samples, int32
  * parameters. */
 pget_status pget_project(pget_ctx* ctx, const pget_lm_params* p, int32_t n, void* lam, void* mu, void* stream);
 
-/* As pget_lm_solve with HOST buffers (pinned or pageable): copies y_host to the device,
+/* The LM solve of Sec. 2.2 and 3.1, as pget_lm_solve, with HOST buffers (pinned or
+ * pageable) in the element type of p->precision: copies y_host to the device,
  * computes the initial guess (mu_init 0.01) when init_guess != 0 (else takes
  * lam_host / mu_host as the initial guess), solves, and copies the result back. */
 pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
@@ -283,7 +285,8 @@ pget_status pget_lm_solve_host(pget_ctx* ctx, const pget_geometry* g, const pget
                                int32_t init_guess, pget_lm_report* rep, void* stream);
 
 /* ---------------------------------------------------------------- serving
- * Continuous batching of reconstructions: each accepted request gets an in-flight slot
+ * Continuous batching of reconstructions (the LM solve of Sec. 2.2 and 3.1 per request;
+ * the paper has no serving layer): each accepted request gets an in-flight slot
  * (its own workspace, stream and captured LM graph, all state on the device); requests
  * that arrive while others run are admitted as soon as a slot and device memory are
  * free, and their kernels overlap on the GPU with those of the requests in flight.
@@ -312,7 +315,8 @@ pget_status pget_cancel(pget_ctx* ctx, uint64_t ticket);
 int32_t pget_inflight(pget_ctx* ctx);
 
 /* ------------------------------------------------------ allocation-free forward
- * The paper has no counterpart to this call; it serves callers that are not allowed to
+ * The forward model of Eq. (1) in its discrete form Eq. (5), as pget_forward computes it.
+ * The paper has no counterpart to this entry point; it serves callers that are not allowed to
  * allocate device memory (a host framework whose allocator owns the GPU, allocation-free
  * real-time sections, processes with a memory budget fixed up front), which cannot use
  * the context-based calls above because a pget_ctx obtains its workspace with cudaMalloc.
