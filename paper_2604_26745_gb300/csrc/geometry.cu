@@ -31,6 +31,9 @@ pget_status build_geometry(const pget_geometry& in, Geometry* G, std::string* ms
     if (g.n_banks != 1 && g.n_banks != 2) return *msg = "n_banks must be 1 or 2", PGET_EINVAL;
     if (g.n_det % g.n_banks) return *msg = "n_det must be a multiple of n_banks", PGET_EINVAL;
     g.nb = g.n_det / g.n_banks;
+    // every detector of a bank adds at least one distinct ray: refuse before any table
+    // is sized by the detector count
+    if (g.nb > kMaxSlots) return *msg = "more than 1024 detectors per bank", PGET_EINVAL;
     g.h = in.step > 0 ? in.step : 1.0;
     g.r = in.fov_radius > 0 ? in.fov_radius : g.n / std::sqrt(2.0);
     g.p = in.det_pitch > 0 ? in.det_pitch : 2.0 * g.r / g.nb;
@@ -116,7 +119,9 @@ pget_status build_geometry(const pget_geometry& in, Geometry* G, std::string* ms
         }
     }
 
-    // per-view canonical frames
+    // per-view canonical frames; the view and clip tables grow with views x slots
+    if ((size_t)g.n_angles * g.n_banks * g.max_slots > kMaxTableSlots)
+        return *msg = "geometry tables too large (views x rays per view above 2^26)", PGET_ENOMEM;
     g.views.resize((size_t)g.n_angles * g.n_banks);
     g.views_transposed = 0;
     for (int a = 0; a < g.n_angles; ++a)

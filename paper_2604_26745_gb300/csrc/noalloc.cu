@@ -66,6 +66,7 @@ extern "C" pget_status pget_forward_noalloc(const pget_geometry* gin, int32_t pr
     const int nbk = gin->n_banks == 0 ? (nd == 182 ? 2 : 1) : gin->n_banks;
     if ((nbk != 1 && nbk != 2) || nd % nbk) return PGET_EINVAL;
     const int nb = nd / nbk;
+    if (nb > kMaxSlots) return PGET_EINVAL;  // at least one distinct ray per detector
     const double h = gin->step > 0 ? gin->step : 1.0;
     const double r = gin->fov_radius > 0 ? gin->fov_radius : n / std::sqrt(2.0);
     const double p = gin->det_pitch > 0 ? gin->det_pitch : 2.0 * r / nb;

@@ -14,6 +14,7 @@ namespace pget {
 constexpr int kMaxSub = 64;
 constexpr int kMaxSlots = 1024;   // rays per bank and view handled by one CTA (one per thread)
 constexpr int kMaxAngles = 1 << 20;  // views = angles x banks stay far inside int and the launch grid
+constexpr size_t kMaxTableSlots = size_t(1) << 26;  // views x rays per view of the host tables (512 MB of clips)
 constexpr int kWalkThreads = 896; // block bound of the walk kernels for views up to this size
 
 // ---------------------------------------------------------------- geometry

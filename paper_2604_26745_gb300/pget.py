@@ -212,8 +212,9 @@ def geometry_info(g: pget_geometry) -> dict:
     T, nb, ms = C.c_int32(), C.c_int32(), C.c_int32()
     r, p = C.c_double(), C.c_double()
     st = load().pget_geometry_info(C.byref(g), C.byref(T), C.byref(nb), C.byref(r), C.byref(p), C.byref(ms))
-    if st != 0:
-        raise ValueError("invalid geometry")
+    if st == PGET_EINVAL:
+        raise ValueError("invalid geometry: " + load().pget_last_error(None).decode())
+    _check(st)
     return {"n_samples": T.value, "n_banks": nb.value, "fov_radius": r.value, "det_pitch": p.value,
             "max_slots": ms.value}
 

@@ -176,3 +176,11 @@ def test_geometry_limits(lib):
         kw = dict(bad)
         with pytest.raises(ValueError):
             pget.geometry_info(pget.geometry(kw.pop("n"), kw.pop("n_angles"), kw.pop("n_det"), **kw))
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(ValueError, match="detectors per bank"):  # refused before any table is sized
+        pget.geometry_info(pget.geometry(16, 8, 2 ** 31 - 1, n_sub=64))
+    with pytest.raises(pget.PgetError) as e:  # 2^21 views x 275 rays: tables refused, not built
+        pget.geometry_info(pget.geometry(64, 1 << 20, 182, n_sub=5))
+    assert e.value.status == pget.PGET_ENOMEM
+    assert time.perf_counter() - t0 < 5.0
