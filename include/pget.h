@@ -261,6 +261,11 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
                                 const void* s_step, const void* prop_lam, const void* prop_mu,
                                 pget_check_report* rep, void* stream);
 
+/* Validate LM parameters on the host, without a context: PGET_OK, or PGET_EINVAL with a
+ * message naming the field (NaN or out-of-range values, unknown precision or options).
+ * Every call that takes parameters runs the same check first. */
+pget_status pget_check_params(const pget_lm_params* p);
+
 /* Derived sizes of a geometry (any output pointer may be NULL; host only, no context):
  * samples per ray T of the discretised ray integral of Eq. (5) (the length of the depth
  * tables), detector banks and pitch p of the device of Sec. 2, field-of-view radius r,

@@ -709,6 +709,12 @@ pget_status check_params(const pget_lm_params* p) {
     if (!(p->lambda_max > 0) || !(p->mu_max > 0)) return fail(PGET_EINVAL, "box bounds must be positive");
     if (!(p->alpha_lambda >= 0) || !(p->alpha_mu >= 0)) return fail(PGET_EINVAL, "prior weights must be >= 0");
     if (!(p->nu_up >= 1) || !(p->nu_down > 0 && p->nu_down <= 1)) return fail(PGET_EINVAL, "bad nu_up / nu_down");
+    if (!std::isfinite(p->tv_eps)) return fail(PGET_EINVAL, "tv_eps must be finite (<= 0: quadratic prior)");
+    if (std::isnan(p->cg_rel_tol)) return fail(PGET_EINVAL, "cg_rel_tol is NaN");
+    if (!(p->nu0_scale > 0) || !std::isfinite(p->nu0_scale)) return fail(PGET_EINVAL, "nu0_scale must be finite and > 0");
+    if (!std::isfinite(p->eta) || !std::isfinite(p->rho_lo) || !std::isfinite(p->rho_hi) || !(p->rho_lo <= p->rho_hi))
+        return fail(PGET_EINVAL, "eta, rho_lo and rho_hi must be finite, rho_lo <= rho_hi");
+    if (!(p->nu_min > 0) || !(p->nu_min <= p->nu_max)) return fail(PGET_EINVAL, "need 0 < nu_min <= nu_max");
     if (p->precision != PGET_F64 && p->precision != PGET_F32 && p->precision != PGET_F32_KAHAN)
         return fail(PGET_EINVAL, "unknown precision %d", p->precision);
     if (!(p->alpha_decay == 0.0 || p->alpha_decay >= 1.0) || p->alpha_decay_iters < 0)
@@ -1530,6 +1536,10 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
         return w->f64 ? check_impl<double>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st)
                       : check_impl<float>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st);
     });
+}
+
+pget_status pget_check_params(const pget_lm_params* p) {
+    return guarded([&]() -> pget_status { return check_params(p); });
 }
 
 pget_status pget_geometry_info(const pget_geometry* gin, int32_t* n_samples, int32_t* n_banks, double* fov_radius,

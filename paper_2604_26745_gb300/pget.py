@@ -104,6 +104,7 @@ _SIGS = {
     "pget_proposal_check": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp, _vp,
                              _vp, _vp, C.POINTER(pget_check_report), _vp], C.c_int),
     "pget_project": ([_vp, C.POINTER(pget_lm_params), C.c_int32, _vp, _vp, _vp], C.c_int),
+    "pget_check_params": ([C.POINTER(pget_lm_params)], C.c_int),
     "pget_geometry_info": ([C.POINTER(pget_geometry), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)], C.c_int),
     "pget_lm_solve_host": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
@@ -217,6 +218,14 @@ def geometry_info(g: pget_geometry) -> dict:
     _check(st)
     return {"n_samples": T.value, "n_banks": nb.value, "fov_radius": r.value, "det_pitch": p.value,
             "max_slots": ms.value}
+
+
+def check_params(p: pget_lm_params) -> None:
+    """Raise ValueError (with the library's message) if p would be refused by any call."""
+    st = load().pget_check_params(C.byref(p))
+    if st == PGET_EINVAL:
+        raise ValueError("invalid parameters: " + load().pget_last_error(None).decode())
+    _check(st)
 
 
 def default_params(**kw) -> pget_lm_params:
