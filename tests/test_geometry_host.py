@@ -55,3 +55,25 @@ def test_benchmark_geometry_counts():
     assert len(o5) == 275 and _slots(o5) == 275
     o10 = _offsets(91, 10, 1, 0)
     assert len(o10) == 910 and _slots(o10) == 1009
+
+
+def test_allocation_free_path_refuses_before_any_work():
+    """pget_forward_noalloc validates its geometry on the host like the context path.
+
+    Oversized detector counts are refused at once (PGET_EINVAL), not walked. Without a GPU
+    a valid geometry ends in PGET_ECUDA at the first CUDA call. The array arguments are
+    placeholders that the host code never reads. This test runs only where there is no
+    GPU, so they can never reach a kernel."""
+    import ctypes
+    import time
+
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("placeholder pointers are for machines without a GPU")
+    L = P.load()
+    fake = ctypes.c_void_p(256)
+    t0 = time.perf_counter()
+    for n_det, want in ((2 ** 31 - 1, P.PGET_EINVAL), (1025, P.PGET_EINVAL), (182, P.PGET_ECUDA)):
+        g = P.geometry(16, 8, n_det, n_sub=64 if n_det != 182 else 5)
+        assert L.pget_forward_noalloc(ctypes.byref(g), P.PGET_F32, fake, fake, fake, None) == want
+    assert time.perf_counter() - t0 < 5.0
