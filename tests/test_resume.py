@@ -1,6 +1,6 @@
 """Checkpoint and resume of the Alg. 2 driver (accelerated.accelerated_solve), on the CPU.
 
-The driver's state after iteration k is the iterate and the scalars (k + 1, ν, ν₀). A solve
+The Alg. 2 driver's state after iteration k is the iterate and the scalars (k + 1, ν, ν₀). A solve
 stopped there and resumed from that checkpoint must give the uninterrupted solve's
 iterates bitwise, with the same decisions and damping. The cases:
 - the plain LM (no proposal);
@@ -8,7 +8,7 @@ iterates bitwise, with the same decisions and damping. The cases:
 - proposals, some of them taken;
 - a binding linear bound, where the resumed iterate is not projected a second time.
 
-The driver's host logic runs unchanged. Only its four library calls (trial, proposal
+The Alg. 2 driver's host logic runs unchanged. Only its four library calls (trial, proposal
 check, projection, parameters) are served by the oracle on CPU tensors; on the GPU the same
 calls go to the CUDA library.
 """
