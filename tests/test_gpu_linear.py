@@ -115,7 +115,7 @@ def test_driver_under_the_bound(O, P, torch):
         assert float((la - lb).abs().max()) <= 1e-12 and float((ma - mb).abs().max()) <= 1e-12
     # a proposal outside the polygon (the truth, whose brightest rods violate a tighter
     # bound), made near it from noiseless data: the oracle's Alg. 2 step takes it, and so
-    # must the driver, landing on its projection
+    # must the Alg. 2 driver, landing on its projection
     k2, b2 = 14.0, 0.0
     ph = synth.lattice_phantom(N, 3, radius=2.0, seed=57)
     go = O.geom(N, NA, ND, n_sub=S)
