@@ -34,10 +34,12 @@ WORKLOAD = dict(n=128, n_lat=9, radius=5.0, n_angles=360, n_det=182, n_sub=5, co
 WORKLOAD_NAME = ("single-request LM: 128x128 grid, 9x9 rods r=5, 360 angles x 182 det (2 banks) "
                  "x 5 triangular sub-rays, Poisson 1e5, 20 LM x 30 CG, FP32-Kahan rays / FP64 scalars")
 METRIC = "recon/s"
+# precisions whose reconstruction of the oracle-stored case is compared with the oracle
+PRECISIONS_CHECKED = (("f32_kahan", 2), ("f64", 0))
 SUB = (16, 16)
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture
-# (profiles/walk_kernels_single128.md), valid only for the kernel code it was taken on:
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
+# adjoint walk on this workload, valid only for the kernel code it was taken on:
 # reported while the device code of csrc/walk.cu (the part before its host section) and
 # csrc/kernels.cuh, without comments, blank lines and includes, hash to these values; null
 # otherwise.
@@ -171,41 +173,13 @@ def make_problem(P, ctx, torch, seed: int, device: str):
     return g, ph, y
 
 
-def samples_per_launch(g_np) -> dict:
-    """Ray samples one walk launch processes (distinct rays x in-grid samples), counted on
-    the host from the geometry (bilinear base pixel inside [-1, n-1]^2)."""
-    import numpy as np
-    n, na, nd, S = g_np["n"], g_np["n_angles"], g_np["n_det"], g_np["n_sub"]
-    nbk = 2 if nd == 182 else 1
-    nb = nd // nbk
-    r = n / math.sqrt(2.0)
-    p = 2 * r / nb
-    T = math.ceil(2 * r)
-    c = 0.5 * (n - 1)
-    t = -r + (np.arange(T) + 0.5)
-    u = np.array([(k - (S - 1) / 2) * 2 * p / (S + 1) for k in range(S)])
-    total_sub, total_distinct = 0, 0
-    for a in range(na):
-        for b in range(nbk):
-            psi = 2 * math.pi * a / na + b * math.pi
-            ct, st = math.cos(psi), math.sin(psi)
-            s = ((np.arange(nb) - 0.5 * (nb - 1) + 0.5 * b) * p)[:, None] + u[None, :]
-            s_all = s.ravel()
-            for arr, acc in ((s_all, "sub"), (np.unique(np.round(s_all / p * 2 * (S + 1)) * p / (2 * (S + 1))), "dist")):
-                fx = -arr[:, None] * st + t[None, :] * ct + c
-                fy = arr[:, None] * ct + t[None, :] * st + c
-                ok = (np.floor(fx) >= -1) & (np.floor(fx) <= n - 1) & (np.floor(fy) >= -1) & (np.floor(fy) <= n - 1)
-                if acc == "sub":
-                    total_sub += int(ok.sum())
-                else:
-                    total_distinct += int(ok.sum())
-    return {"sub_ray_samples": total_sub, "distinct_ray_samples": total_distinct}
-
-
 def cpu_baseline(y, g_dims) -> dict:
     """The FP64 oracle as it stands, on this host's cores: one LM iteration (of 20) of one
-    reconstruction of the same workload; recon/s scaled by 20 iterations."""
+    reconstruction of the same workload on all cores, recon/s scaled by 20 iterations; and
+    one forward, one JVP and one adjoint pass on a single thread, scaled by the passes of
+    one reconstruction."""
     from oracle import oracle as O
+    import numpy as np
     W = WORKLOAD
     go = O.geom(W["n"], W["n_angles"], W["n_det"], n_sub=W["n_sub"], collimator=W["collimator"])
     pr = O.default_params(max_iters=1, cg_max_iters=W["cg_max_iters"], cg_rel_tol=1e-6)
@@ -214,9 +188,74 @@ def cpu_baseline(y, g_dims) -> dict:
     O.lm(go, pr, y, l0, m0)
     dt = time.perf_counter() - t0
     per_recon = dt * W["max_iters"]
-    return {"value": 1.0 / per_recon, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"initial guess + 1 of {W['max_iters']} LM iterations (30 CG steps) of one "
-                      f"reconstruction, {dt:.2f} s, scaled x{W['max_iters']}"}
+    out = {"value": 1.0 / per_recon, "unit": METRIC, "cores": O.num_threads(), "kind": "oracle",
+           "sample": f"initial guess + 1 of {W['max_iters']} LM iterations (30 CG steps) of one "
+                     f"reconstruction, {dt:.2f} s, scaled x{W['max_iters']}"}
+    # single thread: per pass, then the passes of one reconstruction (initial guess: 2
+    # forward; per iteration: gradient adjoint, 30 CG steps of JVP + adjoint, the trial's
+    # JVP and forward), vector work neglected
+    O.set_num_threads(1)
+    try:
+        r = np.asarray(y) - O.forward(go, l0, m0)
+        t0 = time.perf_counter()
+        O.forward(go, l0, m0)
+        t_f = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.jvp(go, l0, m0, l0, m0)
+        t_j = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.vjp(go, l0, m0, r)
+        t_v = time.perf_counter() - t0
+    finally:
+        O.set_num_threads(0)
+    it, cg = W["max_iters"], W["cg_max_iters"]
+    n_f, n_j, n_v = 2 + it, 1 + it * (cg + 1), 1 + it * (cg + 1)
+    t1 = n_f * t_f + n_j * t_j + n_v * t_v
+    out["single_thread"] = {"value": 1.0 / t1, "unit": METRIC, "cores": 1, "kind": "oracle",
+                            "sample": f"1 forward ({t_f:.2f} s), 1 JVP ({t_j:.2f} s), 1 adjoint ({t_v:.2f} s) "
+                                      f"on one thread, scaled by the {n_f} + {n_j} + {n_v} passes of one "
+                                      f"reconstruction"}
+    return out
+
+
+def accuracy_vs_oracle(P, ctx, torch, dev: str) -> dict | None:
+    """GPU reconstructions of the oracle's stored single-request case (the same workload,
+    phantom seed 1100, data from the oracle's forward model with the stored Poisson
+    counts) against the oracle's own FP64 reconstruction, and the oracle's spread under
+    changes of its rounding alone (both written by tests/golden/make_lm_single128.py)."""
+    import numpy as np
+    from paper_2604_26745_gb300 import synth
+    base = os.path.join(ROOT, "tests", "golden", "lm_single128")
+    if not (os.path.exists(base + ".npz") and os.path.exists(base + ".json")):
+        return None
+    z = np.load(base + ".npz")
+    with open(base + ".json") as fh:
+        meta = json.load(fh)
+    c = meta["case"]
+    y = z["counts"].astype(np.float64) * float(z["ymax"]) / c["counts"]
+    ref = np.concatenate([z["lam"].ravel(), z["mu"].ravel()])
+    ph = synth.lattice_phantom(c["n"], c["n_lat"], radius=c["radius"], seed=c["phantom_seed"])
+    g = P.geometry(c["n"], c["n_angles"], c["n_det"], n_sub=c["n_sub"], collimator=c["collimator"])
+    out = {"case": "oracle-stored single request (phantom seed 1100), " + WORKLOAD_NAME,
+           "oracle_self_spread_rel_l2_max": meta["spread_max_rel_l2_u"],
+           "oracle_self_spread_rel_l2_median": meta["spread_median_rel_l2_u"],
+           "oracle_rel_err_truth_lambda": meta["base"]["rel_err_truth_lambda"],
+           "oracle_rel_err_truth_mu": meta["base"]["rel_err_truth_mu"],
+           "initial_rel_err_truth_mu": meta["base"]["initial_rel_err_truth_mu"],
+           "oracle_accepted": meta["base"]["accepted"]}
+    for name, prec in PRECISIONS_CHECKED:
+        p = P.default_params(max_iters=c["max_iters"], cg_max_iters=c["cg_max_iters"], cg_rel_tol=c["cg_rel_tol"],
+                             precision=prec)
+        dt = P.dtype_of(prec)
+        yd = torch.tensor(y, dtype=dt, device=dev)
+        lam, mu = P.pget_initial_guess(ctx, g, p, yd)
+        rep = P.pget_lm_solve(ctx, g, p, yd, lam, mu)
+        u = np.concatenate([lam.double().cpu().numpy().ravel(), mu.double().cpu().numpy().ravel()])
+        out[f"gpu_{name}_vs_oracle_rel_l2"] = float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+        out[f"gpu_{name}_rel_err_truth_mu"] = float(np.linalg.norm(mu.double().cpu().numpy() - ph.mu)
+                                                   / np.linalg.norm(ph.mu))
+        out[f"gpu_{name}_accepted"] = rep["acc"]
+    return out
 
 
 # ------------------------------------------------------------------ reference
@@ -297,7 +336,7 @@ def main():
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    P.pget_profile_enable(ctx, True)
+    P.pget_profile_enable(ctx, False)  # the timed region runs the plain graph (no event nodes)
     launches0 = P.pget_launch_count()
     torch.cuda.synchronize()
     for i in range(args.steps):
@@ -307,13 +346,8 @@ def main():
         l0, m0 = P.pget_initial_guess(ctx, g, p, yd)
         reps.append(P.pget_lm_solve(ctx, g, p, yd, l0, m0))
         ev[i][1].record(stream)
-        lam, mu = l0, m0
-        if i == 0:
-            first = (lam.clone(), mu.clone())
     torch.cuda.synchronize()
     launches = P.pget_launch_count() - launches0
-    prof = P.pget_profile_read(ctx)
-    P.pget_profile_enable(ctx, False)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
@@ -323,6 +357,25 @@ def main():
         dist.barrier()
         total_s = float(t.item())
     value = world * args.steps / total_s
+
+    # per-kernel device times: a separate, untimed pass over the same steps with CUDA events
+    # recorded around every hot kernel on its launching stream (they become event nodes of
+    # the captured graph; the headline above runs without them)
+    P.pget_profile_enable(ctx, True)
+    prof_ms = []
+    for i in range(args.steps):
+        g, ph, yd = probs[args.warmup + i]
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        l0, m0 = P.pget_initial_guess(ctx, g, p, yd)
+        P.pget_lm_solve(ctx, g, p, yd, l0, m0)
+        b.record(stream)
+        prof_ms.append((a, b))
+    torch.cuda.synchronize()
+    prof = P.pget_profile_read(ctx)
+    P.pget_profile_enable(ctx, False)
+    prof_step_ms = [a.elapsed_time(b) for a, b in prof_ms]
 
     # end to end through the host-buffer entry point (pinned buffers, copies inside)
     e2e = None
@@ -354,33 +407,34 @@ def main():
             dist.destroy_process_group()
         return
 
-    # accuracy of the first timed reconstruction: vs truth, and FP32-Kahan vs FP64 GPU path
+    # accuracy: the reconstruction of the oracle-stored case against the oracle's own, and
+    # the first timed reconstruction against its phantom
     g, ph, yd = probs[args.warmup]
-    p64 = P.default_params(max_iters=W["max_iters"], cg_max_iters=W["cg_max_iters"], cg_rel_tol=1e-6,
-                           precision=P.PGET_F64)
-    yd64 = yd.double()
-    l64, m64 = P.pget_initial_guess(ctx, g, p64, yd64)
-    P.pget_lm_solve(ctx, g, p64, yd64, l64, m64)
-    l32, m32 = first
-    u32 = torch.cat([l32.double().ravel(), m32.double().ravel()])
-    u64 = torch.cat([l64.ravel(), m64.ravel()])
-    f32_vs_f64 = float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64))
-    err_l = float(np.linalg.norm(l32.cpu().numpy() - ph.lam) / np.linalg.norm(ph.lam))
-    err_m = float(np.linalg.norm(m32.cpu().numpy() - ph.mu) / np.linalg.norm(ph.mu))
+    acc = accuracy_vs_oracle(P, ctx, torch, dev) or {"oracle_case": "tests/golden/lm_single128.* missing"}
+    l0, m0 = P.pget_initial_guess(ctx, g, p, yd)
+    P.pget_lm_solve(ctx, g, p, yd, l0, m0)
+    acc["first_timed_rel_err_truth_lambda"] = float(np.linalg.norm(l0.double().cpu().numpy() - ph.lam)
+                                                    / np.linalg.norm(ph.lam))
+    acc["first_timed_rel_err_truth_mu"] = float(np.linalg.norm(m0.double().cpu().numpy() - ph.mu)
+                                                / np.linalg.norm(ph.mu))
+    acc["first_timed_f0"], acc["first_timed_f_final"] = reps[0]["f0"], reps[0]["f_final"]
+    acc["first_timed_accepted"] = reps[0]["accepted"]
 
     # roofline of the dominant kernel: algorithmic on-chip bytes per launch / measured time
+    from paper_2604_26745_gb300.config_bench import samples_per_launch
     counts = samples_per_launch(dict(n=W["n"], n_angles=W["n_angles"], n_det=W["n_det"], n_sub=W["n_sub"]))
     bytes_per_sample = {"walk_forward": 32, "walk_jvp": 64, "walk_vjp": 64}
     dom = max(prof, key=lambda k: prof[k]["total_ms"])
     kern = {}
     sm_mhz = clk.get("sm_mhz") or 1432.0
-    smem_peak = 152 * 128 * sm_mhz * 1e6 / 1e9  # GB/s: 152 SMs x 128 B/clk at the sampled clock
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    smem_peak = n_sm * 128 * sm_mhz * 1e6 / 1e9  # GB/s: SMs x 128 B/clk at the sampled clock
     for k, v in prof.items():
         if v["launches"] == 0:
             continue
         avg_ms = v["total_ms"] / v["launches"]
         d = {"launches": v["launches"], "total_ms": round(v["total_ms"], 3), "avg_us": round(avg_ms * 1e3, 2),
-             "share_of_timed": round(v["total_ms"] / (sum(step_ms)), 4)}
+             "share_of_step": round(v["total_ms"] / (sum(prof_step_ms)), 4)}
         if k in bytes_per_sample:
             d["achieved_gbs"] = bytes_per_sample[k] * counts["distinct_ray_samples"] / (avg_ms * 1e-3) / 1e9
         kern[k] = d
@@ -402,7 +456,9 @@ def main():
     roof = {"kernel": dk, "bound": "smem", "achieved": round(achieved, 1), "peak": round(smem_peak, 1),
             "unit": "GB/s", "frac": round(achieved / smem_peak, 4), "traffic": traffic,
             "traffic_unit": "DRAM bytes read + written per launch (ncu)", "hbm": hbm,
-            "peak_source": "derived: 152 SMs x 128 B/clk shared-memory bandwidth x median sampled SM clock",
+            "peak_source": f"derived: {n_sm} SMs x 128 B/clk shared-memory bandwidth x median sampled SM clock",
+            "timing": "average launch time from CUDA events on the launching stream, in an untimed pass "
+                      "over the same steps (the headline pass runs without events)",
             "algorithmic_bytes_per_launch": bytes_per_sample[dk] * counts["distinct_ray_samples"],
             "units_per_launch": counts["distinct_ray_samples"],
             "unit_desc": "in-grid samples of distinct rays (sub-rays sharing a line are one ray)"}
@@ -415,10 +471,9 @@ def main():
         "config": workload_config(world),
         "latency_ms": {"p50": round(statistics.median(step_ms), 3),
                        "p99": round(sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)], 3)},
-        "accuracy": {"f32_kahan_vs_f64_gpu_rel_l2": f32_vs_f64, "rel_err_vs_truth_lambda": err_l,
-                     "rel_err_vs_truth_mu": err_m, "f_final": reps[0]["f_final"], "f0": reps[0]["f0"],
-                     "accepted": reps[0]["accepted"]},
+        "accuracy": acc,
         "roofline": roof, "kernels": kern, "gpu_launches": int(launches),
+        "profiled_pass_ms_per_step": round(sum(prof_step_ms) / len(prof_step_ms), 3),
         "clocks": clk, "e2e": e2e,
     }
     if not args.no_cpu_baseline:

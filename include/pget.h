@@ -175,6 +175,16 @@ pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t precision,
                      const void* lam, const void* mu, const void* r, void* glam, void* gmu,
                      void* stream);
 
+/* Device-side status of the asynchronous operator calls above (pget_forward, pget_jvp,
+ * pget_vjp) made on this context since the last call of this function or since the
+ * geometry or precision last changed.  Waits for `stream`, reads the kernels' error word
+ * and clears it: PGET_OK; PGET_ETIMEOUT when a chunk copy of a walk did not arrive within
+ * its wait limit (the outputs of that call are void); PGET_ECUDA when an adjoint stencil
+ * bound was violated (never expected: the geometry guarantees it).  This is how a caller
+ * checks results those calls could not check without waiting for the device.  The
+ * paper has no counterpart. */
+pget_status pget_operator_status(pget_ctx* ctx, void* stream);
+
 /* Prior of the objective above (it stands in for the P1/P2 terms of Eq. (6)):
  * out = alpha grad^T W(u) grad v with the lagged-diffusivity weights
  * W(u) = 1 / sqrt(|grad u|^2 + eps^2) (eps <= 0: W = 1), and, when value_host is not
@@ -202,9 +212,11 @@ pget_status pget_initial_guess(pget_ctx* ctx, const pget_geometry* g, const pget
  * Eq. (9) (or gradient projection, inner_solver), takes s = P(u + delta) - u with P the
  * projection onto the constraint set (the box, and the linear bound if set), evaluates the
  * model decrease of Eq. (8) and rho of Eq. (12), accepts iff rho > eta and updates nu.
- * All state stays on the device; one host synchronisation per iteration reads the
- * FP64 scalars into the report.  lam_io, mu_io: initial guess in, result out.
- * rep: host memory.  Blocks until done. */
+ * All state stays on the device: the whole solve (every iteration, with device-side
+ * flags for the CG exit and the acceptance) is one CUDA graph, captured on the first call
+ * with these parameters and replayed afterwards; one host synchronisation at the end reads
+ * the FP64 scalars and traces into the report.  lam_io, mu_io: initial guess in, result
+ * out.  rep: host memory.  Blocks until done. */
 pget_status pget_lm_solve(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
                           const void* y, void* lam_io, void* mu_io, pget_lm_report* rep,
                           void* stream);
@@ -333,14 +345,24 @@ int32_t pget_inflight(pget_ctx* ctx);
  *   - A geometry whose scratch exceeds 8 MiB returns PGET_ENOMEM before any work is
  *     queued (2 * (n+2)^2 image elements of 8 or 16 bytes plus 8 bytes per ray slot and
  *     view; e.g. n = 128 with 360 angles x 182 detectors x 5 sub-rays needs about 2 MiB).
- *   - Bad arguments return PGET_EINVAL, CUDA failures PGET_ECUDA.  Errors are reported
- *     by the status only: pget_last_error is not updated (storing a message could
- *     allocate).
+ *   - Bad arguments return PGET_EINVAL, CUDA failures PGET_ECUDA, a host-side failure
+ *     (a failed mutex) PGET_EINTERNAL.  Errors are reported by the status only:
+ *     pget_last_error is not updated (storing a message could allocate).
  *   - The first call on a device looks up the array's device address and caches it; make
- *     that first call before any stream capture.
- *   - Every call overwrites the same array (image borders are cleared on each call);
- *     calls that overlap on the GPU (several streams or host threads) race.
- *   - The call allocates no device or host memory.
+ *     that first call before any stream capture.  The call refuses to run while `stream`
+ *     is being captured into a CUDA graph (PGET_EINVAL): its table copy reads a host
+ *     staging buffer shared by all calls, which a replay would read later.
+ *   - Every call overwrites the same array (image borders are cleared on each call), and
+ *     the tables are built in one host staging buffer for the whole process.  Calls that
+ *     overlapped on the GPU, or built their tables at the same time, would race; to
+ *     prevent that, each call holds one process-wide lock from building its tables until
+ *     its projection has finished, so concurrent calls (several host threads, one device
+ *     or several) run one after another.
+ *   - The call waits for its projection (it synchronises `stream`) and reads the kernel's
+ *     error word: PGET_ETIMEOUT when a chunk copy did not arrive within its wait limit
+ *     (y is then void), PGET_ECUDA for any other device-side condition.
+ *   - The call allocates no device or host memory (the per-device tables of shared-memory
+ *     permissions and kernel variants it consults are fixed arrays).
  * lam, mu: [n][n] device in; y: [n_angles][n_det] device out; stream as above. */
 pget_status pget_forward_noalloc(const pget_geometry* g, int32_t precision, const void* lam,
                                  const void* mu, void* y, void* stream);

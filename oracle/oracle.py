@@ -126,6 +126,7 @@ def lib():
         L.og_initial_guess.argtypes = [gp, dp, C.c_double, C.c_double, C.c_double, dp, dp]
         L.og_geom_info.argtypes = [gp, C.POINTER(C.c_int32), dp, dp, C.POINTER(C.c_int32)]
         L.og_num_threads.restype = C.c_int
+        L.og_set_num_threads.argtypes = [C.c_int]
         L.og_set_vjp_chunks.argtypes = [C.c_int]
         L.og_lm_trial.argtypes = [gp, C.POINTER(Params), dp, dp, dp, C.c_double, dp, C.POINTER(Trial)]
         L.og_check_proposal.argtypes = [gp, C.POINTER(Params), dp, dp, dp, dp, dp, dp, C.POINTER(Check)]
@@ -348,3 +349,8 @@ def set_vjp_chunks(c: int = 32) -> None:
 
 def num_threads() -> int:
     return lib().og_num_threads()
+
+
+def set_num_threads(n: int = 0) -> None:
+    """Threads of the oracle's OpenMP loops (n <= 0: the default); results do not change."""
+    lib().og_set_num_threads(int(n))

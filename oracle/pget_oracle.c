@@ -1063,3 +1063,16 @@ int og_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops (the angle loops of og_forward, og_jvp and og_vjp); n <= 0
+ * restores the default.  Only the timing of the oracle changes, never a result: every
+ * reduction over angles is summed in a fixed order of chunks (og_set_vjp_chunks). */
+void og_set_num_threads(int n) {
+#ifdef _OPENMP
+    static int dflt = 0;
+    if (dflt == 0) dflt = omp_get_max_threads();
+    omp_set_num_threads(n > 0 ? n : dflt);
+#else
+    (void)n;
+#endif
+}

@@ -15,8 +15,15 @@ stress512  precision stress: K reconstructions on 512 x 512 (17 x 17 rods r = 10
            relative L2 distance of the FP32 and FP32-Kahan sinogram, gradient and final
            reconstruction from the FP64 GPU path on the same input.
 
+ops128     the three ray operators alone on the single-request geometry (128 x 128, 360 x
+           182 x 5, FP32-Kahan): forward, JVP and adjoint, K launches each after one
+           warm-up: average device time per launch and in-grid samples of distinct rays
+           per second.  --op forward|jvp|vjp|all restricts the launches (also the small,
+           named case for kernel profilers).
+ops512     the same on the precision-stress geometry (512 x 512, 720 x 182 x 9).
+
 Prints one JSON line per configuration.  Timing: CUDA events on the current stream around
-each reconstruction (after one untimed warm-up), data resident in HBM.
+each reconstruction or launch (after one untimed warm-up), data resident in HBM.
 """
 from __future__ import annotations
 
@@ -97,6 +104,38 @@ def diff256(k: int) -> dict:
     return out
 
 
+def samples_per_launch(g: dict) -> dict:
+    """Ray samples one walk launch processes, counted on the host from the geometry (dict
+    with n, n_angles, n_det, n_sub; triangular sub-rays): in-grid samples (bilinear base
+    pixel inside [-1, n-1]^2) of every sub-ray, and of the distinct rays the kernels trace
+    (sub-rays of neighbouring detectors that lie on one line are one ray)."""
+    n, na, nd, S = g["n"], g["n_angles"], g["n_det"], g["n_sub"]
+    nbk = 2 if nd == 182 else 1
+    nb = nd // nbk
+    r = n / math.sqrt(2.0)
+    p = 2 * r / nb
+    T = math.ceil(2 * r)
+    c = 0.5 * (n - 1)
+    t = -r + (np.arange(T) + 0.5)
+    u = np.array([(k - (S - 1) / 2) * 2 * p / (S + 1) for k in range(S)])
+    total_sub, total_distinct = 0, 0
+    for a in range(na):
+        for b in range(nbk):
+            psi = 2 * math.pi * a / na + b * math.pi
+            ct, st = math.cos(psi), math.sin(psi)
+            s_all = (((np.arange(nb) - 0.5 * (nb - 1) + 0.5 * b) * p)[:, None] + u[None, :]).ravel()
+            s_dist = np.unique(np.round(s_all / p * 2 * (S + 1)) * p / (2 * (S + 1)))
+            for arr, sub in ((s_all, True), (s_dist, False)):
+                fx = -arr[:, None] * st + t[None, :] * ct + c
+                fy = arr[:, None] * ct + t[None, :] * st + c
+                ok = (np.floor(fx) >= -1) & (np.floor(fx) <= n - 1) & (np.floor(fy) >= -1) & (np.floor(fy) <= n - 1)
+                if sub:
+                    total_sub += int(ok.sum())
+                else:
+                    total_distinct += int(ok.sum())
+    return {"sub_ray_samples": total_sub, "distinct_ray_samples": total_distinct}
+
+
 def _in_grid_samples(n, na, nd, S) -> int:
     """In-grid samples of all sub-rays of one pass (host count from the geometry)."""
     nbk = 2 if nd == 182 else 1
@@ -162,12 +201,58 @@ def stress512(k: int) -> dict:
             "rel_l2_vs_f64_gpu": per}
 
 
+OPS = {"ops128": dict(n=128, n_lat=9, radius=5.0, n_angles=360, n_det=182, n_sub=5),
+       "ops512": dict(n=512, n_lat=17, radius=10.0, n_angles=720, n_det=182, n_sub=9)}
+
+
+def ops(k: int, name: str, op: str = "all", prec: int = P.PGET_F32_KAHAN) -> dict:
+    c = OPS[name]
+    dt = P.dtype_of(prec)
+    ph = synth.lattice_phantom(c["n"], c["n_lat"], radius=c["radius"], seed=1)
+    g = P.geometry(c["n"], c["n_angles"], c["n_det"], n_sub=c["n_sub"])
+    t = lambda x: torch.tensor(x, dtype=dt, device="cuda")
+    lam, mu = t(ph.lam), t(ph.mu)
+    rs = np.random.default_rng(0)
+    dl, dm = t(rs.standard_normal(ph.lam.shape)), t(0.01 * rs.standard_normal(ph.lam.shape))
+    samples = samples_per_launch(c)["distinct_ray_samples"]
+    out = {"config": f"operators: {c['n']}x{c['n']}, {c['n_angles']} x {c['n_det']} x {c['n_sub']}",
+           "precision": prec, "launches": k}
+    with P.Context(0) as ctx:
+        y = P.pget_forward(ctx, g, prec, lam, mu)
+        r = t(rs.standard_normal(tuple(y.shape)))
+        calls = {"forward": lambda: P.pget_forward(ctx, g, prec, lam, mu, y),
+                 "jvp": lambda: P.pget_jvp(ctx, g, prec, lam, mu, dl, dm),
+                 "vjp": lambda: P.pget_vjp(ctx, g, prec, lam, mu, r)}
+        for nm, fn in calls.items():
+            if op not in ("all", nm):
+                continue
+            fn()  # warm-up
+            P.pget_profile_enable(ctx, True)
+            for _ in range(k):
+                fn()
+            torch.cuda.synchronize()
+            prof = P.pget_profile_read(ctx)
+            P.pget_profile_enable(ctx, False)
+            P.pget_operator_status(ctx)
+            out[nm] = {kk: {"avg_us": round(1e3 * v["total_ms"] / v["launches"], 2), "launches": v["launches"]}
+                       for kk, v in prof.items() if v["launches"]}
+            walk = out[nm].get("walk_" + nm)
+            if walk:
+                walk["distinct_ray_samples_per_s"] = round(samples / (walk["avg_us"] * 1e-6), 1)
+    out["distinct_ray_samples_per_launch"] = samples
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--config", required=True, choices=["plain64", "diff256", "stress512"])
+    ap.add_argument("--config", required=True, choices=["plain64", "diff256", "stress512", "ops128", "ops512"])
     ap.add_argument("--count", type=int, default=0)
+    ap.add_argument("--op", default="all", choices=["all", "forward", "jvp", "vjp"])
     a = ap.parse_args()
     build.build()
+    if a.config in OPS:
+        print(json.dumps(ops(a.count or 20, a.config, a.op)), flush=True)
+        return
     fn, k0 = {"plain64": (plain64, 16), "diff256": (diff256, 32), "stress512": (stress512, 4)}[a.config]
     print(json.dumps(fn(a.count or k0)), flush=True)
 

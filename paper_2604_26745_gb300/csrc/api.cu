@@ -1419,6 +1419,21 @@ pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const 
     });
 }
 
+pget_status pget_operator_status(pget_ctx* ctx, void* stream) {
+    return guarded([&]() -> pget_status {
+        if (!ctx) return fail(PGET_EINVAL, "null ctx");
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        if (!ctx->ws) return PGET_OK;  // no operator call yet
+        cudaStream_t st = (cudaStream_t)stream;
+        Workspace& w = *ctx->ws;
+        CK(cudaMemcpyAsync(w.host_err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+        CK(cudaStreamSynchronize(st));
+        return flags_status(*w.host_err);
+    });
+}
+
 pget_status pget_reg_apply(pget_ctx* ctx, int32_t n, int32_t prec, double alpha, double eps, const void* u,
                            const void* v, void* out, double* value_host, void* stream) {
     return guarded([&]() -> pget_status {

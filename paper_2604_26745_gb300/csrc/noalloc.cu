@@ -17,11 +17,20 @@
 //     capture;
 //   - every call uses the same array and overwrites it; calls that overlap on the GPU
 //     (different streams, or several host threads) race and give wrong results;
+//   - the host side of every call (building the geometry tables in one process-wide
+//     staging buffer and copying them to the device) runs under one process-wide mutex,
+//     so calls from several host threads, on one device or several, never mix their
+//     tables; the device-side race above remains for calls on one device;
+//   - the call refuses to run while its stream is being captured into a CUDA graph
+//     (PGET_EINVAL): the table copy reads the shared staging buffer when it runs;
+//   - the call waits for its forward projection and reads the kernel's error word: a
+//     chunk copy that did not arrive in time returns PGET_ETIMEOUT, never a void result;
 //   - the call allocates no device or host memory; errors are reported by the returned
 //     status only (pget_last_error is not updated, because storing a message may allocate).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <utility>
 
@@ -42,6 +51,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 // host staging for the geometry tables (same layout as the front of the device array)
 alignas(256) static unsigned char g_noalloc_host[kNoAllocScratchBytes];
 static void* g_noalloc_dev[kNoAllocMaxDevices];
+// serialises the host side of every call: the staging buffer and the device-address table
+// are process-wide (locking allocates nothing)
+static std::mutex g_noalloc_mu;
 
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -51,8 +63,21 @@ static long long fixed32(double v) { return llrint(v * 4294967296.0); }
 
 using namespace pget;
 
+static pget_status forward_noalloc(const pget_geometry* gin, int32_t precision, const void* lam, const void* mu,
+                                   void* y, void* stream);
+
 extern "C" pget_status pget_forward_noalloc(const pget_geometry* gin, int32_t precision, const void* lam,
                                             const void* mu, void* y, void* stream) {
+    // no C++ exception crosses the C boundary (a failed mutex would throw)
+    try {
+        return forward_noalloc(gin, precision, lam, mu, y, stream);
+    } catch (...) {
+        return PGET_EINTERNAL;
+    }
+}
+
+static pget_status forward_noalloc(const pget_geometry* gin, int32_t precision, const void* lam, const void* mu,
+                                   void* y, void* stream) {
     if (!gin || !lam || !mu || !y) return PGET_EINVAL;
     if (gin->depth_w || gin->depth_c) return PGET_EINVAL;  // depth tables need a context workspace
     if (precision != PGET_F64 && precision != PGET_F32 && precision != PGET_F32_KAHAN) return PGET_EINVAL;
@@ -122,6 +147,12 @@ extern "C" pget_status pget_forward_noalloc(const pget_geometry* gin, int32_t pr
     off = align256(off + img_bytes);
     if (off > kNoAllocScratchBytes) return PGET_ENOMEM;
 
+    // a captured table copy would read the shared staging buffer at replay time
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return PGET_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return PGET_EINVAL;
+
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
     // ---- per-device address of the scratch array (looked up once per device)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return PGET_ECUDA;
@@ -252,5 +283,12 @@ extern "C" pget_status pget_forward_noalloc(const pget_geometry* gin, int32_t pr
     a.y_out = y;
     a.err = (int*)(D + o_err);
     if (launch_walk(kFwd, precision, pl, a, V, st) != cudaSuccess) return PGET_ECUDA;
-    return cudaGetLastError() == cudaSuccess ? PGET_OK : PGET_ECUDA;
+    // the kernel's error word (zeroed with the tables above): wait for the projection and
+    // read it into a stack word (a copy to pageable memory returns once it has completed)
+    int err = 0;
+    if (cudaMemcpyAsync(&err, D + o_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PGET_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PGET_ECUDA;
+    if (err & 4) return PGET_ETIMEOUT;  // a chunk copy did not arrive in time: y is void
+    if (err) return PGET_ECUDA;
+    return PGET_OK;
 }

@@ -32,7 +32,6 @@
 #include <climits>
 #include <cstdio>
 #include <cstdlib>
-#include <map>
 #include <mutex>
 #include <utility>
 
@@ -590,17 +589,30 @@ WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, 
     return pl;
 }
 
-// dynamic shared memory already permitted for each instantiation (set outside any
-// stream capture: prepare_walk runs before a CUDA graph is captured); guarded, as contexts
-// may be driven from several host threads
+// Devices the per-device caches below cover (ordinals 0 .. kCacheDevices - 1); a launch on a
+// higher ordinal is refused with cudaErrorInvalidDevice.
+constexpr int kCacheDevices = 64;
+
+static int current_device() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) d = -1;
+    return d;
+}
+
+// dynamic shared memory already permitted for each instantiation, per device (the
+// attribute is set per device: a launch on another device needs its own call); set
+// outside any stream capture (prepare_walk runs before a CUDA graph is captured) and
+// guarded, as contexts may be driven from several host threads
 template <typename T, bool K, int M, bool D, int X>
 static cudaError_t allow_smem_x(size_t bytes) {
     static std::mutex mu;
-    static size_t allowed = 0;
+    static size_t allowed[kCacheDevices] = {};
+    const int dev = current_device();
+    if (dev < 0 || dev >= kCacheDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
-    if (bytes <= allowed) return cudaSuccess;
+    if (bytes <= allowed[dev]) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(walk_kernel<T, K, M, D, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) allowed = bytes;
+    if (e == cudaSuccess) allowed[dev] = bytes;
     return e;
 }
 template <typename T, bool K, int M, bool D>
@@ -612,26 +624,37 @@ static cudaError_t allow_smem(size_t bytes) {
 // The instantiation for a plan: the 72-register one when the block fits it and it keeps
 // at least as many CTAs resident per SM as the 64-register one (with 480 threads, say,
 // 72 registers allow one CTA per SM where 64 allow two).  The occupancy query runs once per
-// (block, shared memory) and is cached: prepare_walk makes it before any stream capture.
-// Needs allow_smem first.
+// (device, block, shared memory) and is cached in a fixed table (no heap allocation, so
+// the allocation-free entry point can use it): prepare_walk makes it before any stream
+// capture.  When the table is full the query runs again on each launch (never expected:
+// a process sees a handful of plan shapes).  Needs allow_smem first.
+struct ChoiceEntry {
+    int dev, threads;
+    size_t smem;
+    bool wide;
+};
+constexpr int kChoiceEntries = 256;
+
 template <typename T, bool K, int M, bool D>
 static void (*walk_choice(const WalkPlan& pl))(WalkArgs) {
     if (pl.threads > kWalkThreads) return walk_kernel<T, K, M, D, kMaxSlots>;
     static std::mutex mu;
-    static std::map<std::pair<int, size_t>, bool> wide;  // (threads, smem) -> 72 registers
+    static ChoiceEntry table[kChoiceEntries];
+    static int used = 0;
+    const int dev = current_device();
     std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_pair(pl.threads, pl.smem);
-    auto it = wide.find(key);
-    if (it == wide.end()) {
-        int o72 = 0, o64 = 0;
-        bool ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o72, walk_kernel<T, K, M, D, kWalkThreads>,
-                                                                pl.threads, pl.smem) == cudaSuccess &&
-                  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o64, walk_kernel<T, K, M, D, kMaxSlots>,
-                                                                pl.threads, pl.smem) == cudaSuccess;
-        if (!ok) cudaGetLastError();  // a failed query is no launch error: the 64-register one runs
-        it = wide.emplace(key, ok && o72 >= o64 && o72 > 0).first;
-    }
-    return it->second ? walk_kernel<T, K, M, D, kWalkThreads> : walk_kernel<T, K, M, D, kMaxSlots>;
+    for (int i = 0; i < used; ++i)
+        if (table[i].dev == dev && table[i].threads == pl.threads && table[i].smem == pl.smem)
+            return table[i].wide ? walk_kernel<T, K, M, D, kWalkThreads> : walk_kernel<T, K, M, D, kMaxSlots>;
+    int o72 = 0, o64 = 0;
+    const bool ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o72, walk_kernel<T, K, M, D, kWalkThreads>,
+                                                                  pl.threads, pl.smem) == cudaSuccess &&
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o64, walk_kernel<T, K, M, D, kMaxSlots>,
+                                                                  pl.threads, pl.smem) == cudaSuccess;
+    if (!ok) cudaGetLastError();  // a failed query is no launch error: the 64-register one runs
+    const bool wide = ok && o72 >= o64 && o72 > 0;
+    if (used < kChoiceEntries) table[used++] = ChoiceEntry{dev, pl.threads, pl.smem, wide};
+    return wide ? walk_kernel<T, K, M, D, kWalkThreads> : walk_kernel<T, K, M, D, kMaxSlots>;
 }
 
 template <typename T, bool K, int M, bool D>

@@ -91,6 +91,7 @@ _SIGS = {
     "pget_forward": ([_vp, C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
     "pget_jvp": ([_vp, C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "pget_vjp": ([_vp, C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "pget_operator_status": ([_vp, _vp], C.c_int),
     "pget_reg_apply": ([_vp, C.c_int32, C.c_int32, C.c_double, C.c_double, _vp, _vp, _vp,
                         C.POINTER(C.c_double), _vp], C.c_int),
     "pget_cg_solve": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
@@ -311,6 +312,12 @@ def pget_vjp(ctx: Context, g: pget_geometry, precision: int, lam, mu, r, glam=No
                            _arr(glam, precision, nn, d, "glam"), _arr(gmu, precision, nn, d, "gmu"),
                            _stream(stream)), ctx.h)
     return glam, gmu
+
+
+def pget_operator_status(ctx: Context, stream=None) -> None:
+    """Waits for the stream and raises if a forward, JVP or adjoint call made since the
+    last check met a device-side error (a chunk copy wait that ran out: PGET_ETIMEOUT)."""
+    _check(load().pget_operator_status(ctx.h, _stream(stream)), ctx.h)
 
 
 def pget_reg_apply(ctx: Context, n: int, precision: int, alpha: float, eps: float, u, v, out=None,

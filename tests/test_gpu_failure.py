@@ -49,3 +49,23 @@ def test_lost_chunk_copy_times_out_and_device_stays_usable(P, torch, monkeypatch
     for a, b in zip(got, ref):
         assert torch.equal(a, b)
     assert np.isfinite(got[0].cpu().numpy()).all()
+
+
+def test_operator_status_reports_a_lost_chunk_copy(P, torch, monkeypatch):
+    """The asynchronous operator calls cannot wait for their kernels; the error word they
+    leave is read by pget_operator_status, which reports the timed-out chunk copy."""
+    g, y = _problem(P, torch)
+    lam = torch.full((48, 48), 0.5, dtype=torch.float32, device="cuda")
+    mu = torch.full((48, 48), 0.01, dtype=torch.float32, device="cuda")
+    monkeypatch.setenv("PGET_TEST_TX_EXTRA", "16")
+    monkeypatch.setenv("PGET_TEST_WAIT_NS", "2000000")
+    with P.Context(0) as c:
+        P.pget_forward(c, g, P.PGET_F32_KAHAN, lam, mu)
+        with pytest.raises(P.PgetError) as e:
+            P.pget_operator_status(c)
+        assert e.value.status == P.PGET_ETIMEOUT
+    monkeypatch.delenv("PGET_TEST_TX_EXTRA")
+    monkeypatch.delenv("PGET_TEST_WAIT_NS")
+    with P.Context(0) as c:
+        P.pget_forward(c, g, P.PGET_F32_KAHAN, lam, mu)
+        P.pget_operator_status(c)  # clean: no error

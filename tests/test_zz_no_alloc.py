@@ -44,3 +44,49 @@ def test_noalloc_small_geometry_and_limit(ctx, P, torch):
     yb = torch.zeros((720, 182), dtype=torch.float32, device="cuda")
     assert P.pget_forward_noalloc(big, P.PGET_F32_KAHAN, z, z, yb) == P.PGET_ENOMEM
     assert P.pget_forward_noalloc(P.geometry(1, 4, 91), P.PGET_F32, z, z, yb) == P.PGET_EINVAL
+
+
+def test_noalloc_two_host_threads_different_geometries(ctx, P, torch):
+    """Two host threads call the allocation-free forward at the same time with different
+    geometries; the process-wide lock keeps their host tables and device scratch apart,
+    so every result equals the context forward of its own geometry bitwise."""
+    import threading
+    cases = []
+    for n, na, nd, S, seed in ((48, 60, 182, 3, 11), (40, 36, 91, 5, 12)):
+        g = P.geometry(n, na, nd, n_sub=S)
+        ph = synth.lattice_phantom(n, 4, seed=seed)
+        lam = torch.tensor(ph.lam, dtype=torch.float32, device="cuda")
+        mu = torch.tensor(ph.mu, dtype=torch.float32, device="cuda")
+        cases.append((g, lam, mu, P.pget_forward(ctx, g, P.PGET_F32_KAHAN, lam, mu).clone()))
+    torch.cuda.synchronize()
+    bad = []
+
+    def worker(i):
+        g, lam, mu, ref = cases[i]
+        s = torch.cuda.Stream()
+        y = torch.empty_like(ref)
+        for _ in range(20):
+            st = P.pget_forward_noalloc(g, P.PGET_F32_KAHAN, lam, mu, y, s)
+            if st != P.PGET_OK or not torch.equal(y, ref):
+                bad.append((i, st))
+
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not bad, bad
+
+
+def test_noalloc_refuses_stream_capture(ctx, P, torch):
+    g = P.geometry(40, 36, 182, n_sub=3)
+    lam = torch.zeros((40, 40), dtype=torch.float32, device="cuda")
+    y = torch.zeros((36, 182), dtype=torch.float32, device="cuda")
+    assert P.pget_forward_noalloc(g, P.PGET_F32, lam, lam, y) == P.PGET_OK  # first call: set-up
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        graph.capture_begin()
+        st = P.pget_forward_noalloc(g, P.PGET_F32, lam, lam, y, s)
+        graph.capture_end()
+    assert st == P.PGET_EINVAL
