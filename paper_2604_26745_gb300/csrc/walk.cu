@@ -239,7 +239,7 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
     const float dXrf = (float)vp.dXrd, dYrf = (float)vp.dYrd;
     const float invR2 = 1.0f / (dXrf * dXrf + dYrf * dYrf);
     const float wI = (fabsf(dXrf) + fabsf(dYrf)) * invR2 + 0.01f;
-    const float inv_n = 1.0f / (float)n;
+    const float inv_np = 1.0f / (float)((n + 1) / 2);  // pixel pairs per row (gather)
 
     // copy of chunk ck into buffer b, issued by warp 0: lane 0 announces the bytes on the
     // buffer's barrier, then every lane issues its rows
@@ -387,42 +387,52 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
         if constexpr (TMA) aborted = *s_abort != 0;
         if constexpr (MODE == kVjp) {
             const int r0 = max(row_lo, 0), r1 = min(row_hi + 1, n - 1);
-            const int nout = (r1 - r0 + 1) * n;
             T2* carry_rd = (ck & 1) ? carry0 : carry1;
             T2* carry_wr = (ck & 1) ? carry1 : carry0;
             T* gp = (T*)A.gpart + (size_t)g * 2 * n * n;
-            for (int e = tid; e < nout; e += blockDim.x) {
-                const int dy = __float2int_rz(((float)e + 0.5f) * inv_n);
-                const int Yr = r0 + dy, Xc = e - dy * n;
+            // every thread gathers two neighbouring pixels (Xa, Xa + 1) of a row: their
+            // candidate rays overlap, so one pass over the union loads each ray's stencil
+            // origin once; a ray outside one pixel's own window holds zeros at that pixel,
+            // and each pixel's sum keeps the ascending order of the rays
+            const int npair = (n + 1) / 2;
+            const int nout2 = (r1 - r0 + 1) * npair;
+            for (int e2 = tid; e2 < nout2; e2 += blockDim.x) {
+                const int dy = __float2int_rz(((float)e2 + 0.5f) * inv_np);
+                const int Yr = r0 + dy, Xa = 2 * (e2 - dy * npair);
                 const int rl = Yr - row_lo;
-                const float fi = ((float)Xc - X00f) * dXrf * invR2 + ((float)Yr - Y00f) * dYrf * invR2;
-                const int ilo = max(0, (int)ceilf(fi - wI - wa)), ihi = min(wn - 1, (int)floorf(fi + wI - wa));
-                T2 acc = mk2(T(0), T(0));
+                const float fa = ((float)Xa - X00f) * dXrf * invR2 + ((float)Yr - Y00f) * dYrf * invR2;
+                const float fb = fa + dXrf * invR2;
+                const int ilo = max(0, (int)ceilf(fminf(fa, fb) - wI - wa));
+                const int ihi = min(wn - 1, (int)floorf(fmaxf(fa, fb) + wI - wa));
+                T2 acca = mk2(T(0), T(0)), accb = mk2(T(0), T(0));
                 const short* c0r = C0 + rl * nth;
                 const T2* str = ST + (size_t)rl * SW * nth;
-                // window columns of the candidate rays, two at a time (their loads are
-                // independent); the sum keeps the order of t
-                for (int t = ilo; t <= ihi; t += 2) {
-                    const bool two = t + 1 <= ihi;
-                    const int k0 = Xc - (int)c0r[t];
-                    const int k1 = two ? Xc - (int)c0r[t + 1] : -1;
-                    const T2 v0 = (unsigned)k0 < (unsigned)SW ? str[k0 * nth + t] : mk2(T(0), T(0));
-                    const T2 v1 = (unsigned)k1 < (unsigned)SW ? str[k1 * nth + t + 1] : mk2(T(0), T(0));
-                    acc = add2(add2(acc, v0), v1);
+                for (int t = ilo; t <= ihi; ++t) {
+                    const int ka = Xa - (int)c0r[t];
+                    const T2 va = (unsigned)ka < (unsigned)SW ? str[ka * nth + t] : mk2(T(0), T(0));
+                    const T2 vb = (unsigned)(ka + 1) < (unsigned)SW ? str[(ka + 1) * nth + t] : mk2(T(0), T(0));
+                    acca = add2(acca, va);
+                    accb = add2(accb, vb);
                 }
-                if (ck > 0 && Yr == row_hi + 1) acc = add2(acc, carry_rd[Xc]);
-                if (Yr == row_lo && ck < A.nchunks - 1) {
-                    carry_wr[Xc] = acc;
-                } else {
-                    const int row = vp.flipped ? (n - 1 - Yr) : Yr;
-                    T* o0 = gp + (size_t)row * n + Xc;
-                    T* o1 = o0 + (size_t)n * n;
-                    if (first_view) {
-                        *o0 = acc.x;
-                        *o1 = acc.y;
+#pragma unroll
+                for (int q2 = 0; q2 < 2; ++q2) {
+                    const int Xc = Xa + q2;
+                    if (Xc >= n) break;
+                    T2 acc = q2 ? accb : acca;
+                    if (ck > 0 && Yr == row_hi + 1) acc = add2(acc, carry_rd[Xc]);
+                    if (Yr == row_lo && ck < A.nchunks - 1) {
+                        carry_wr[Xc] = acc;
                     } else {
-                        *o0 += acc.x;
-                        *o1 += acc.y;
+                        const int row = vp.flipped ? (n - 1 - Yr) : Yr;
+                        T* o0 = gp + (size_t)row * n + Xc;
+                        T* o1 = o0 + (size_t)n * n;
+                        if (first_view) {
+                            *o0 = acc.x;
+                            *o1 = acc.y;
+                        } else {
+                            *o0 += acc.x;
+                            *o1 += acc.y;
+                        }
                     }
                 }
             }
