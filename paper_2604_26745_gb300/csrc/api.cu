@@ -352,11 +352,15 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     w->M = (size_t)G.n_angles * G.n_det;
     w->nslots = (size_t)V * G.max_slots;
     w->img_elems = (size_t)(G.n + 2) * w->P;
-    // shared memory per CTA: three CTAs of up to 1024 threads share an SM's 227 KB;
-    // PGET_SMEM_KB_{FWD,JVP,VJP} override for tuning
+    // shared memory per CTA: three CTAs of up to 1024 threads share an SM's 227 KB
+    // (a build with -DPGET_TUNING reads PGET_SMEM_KB_{FWD,JVP,VJP} to sweep the budgets)
     auto budget = [](const char* env, size_t kb) {
+#ifdef PGET_TUNING
         const char* v = getenv(env);
         if (v && atoi(v) > 0) kb = (size_t)atoi(v);
+#else
+        (void)env;
+#endif
         return kb * 1024;
     };
     w->pf = plan_walk(G, w->P, kFwd, w->f64, budget("PGET_SMEM_KB_FWD", 64));
@@ -366,11 +370,12 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
         ray_rows(G, w->f64, &rows);
         w->pv = plan_walk(G, w->P, kVjp, w->f64, budget("PGET_SMEM_KB_VJP", 72), &rows);
     }
-    // views per adjoint CTA: one by default (the hardware scheduler balances single-view
-    // CTAs across SMs best); PGET_VJP_VIEWS_PER_CTA > 1 groups views of one orientation,
-    // which shrinks the partial images but assigns work statically; 0 sizes groups so that
-    // every CTA is resident at once
+    // views per adjoint CTA: one (the hardware scheduler balances single-view CTAs across
+    // SMs best); a build with -DPGET_TUNING reads PGET_VJP_VIEWS_PER_CTA > 1 to group views
+    // of one orientation, which shrinks the partial images but assigns work statically (0
+    // sizes groups so that every CTA is resident at once)
     int K = 1;
+#ifdef PGET_TUNING
     if (const char* kv = getenv("PGET_VJP_VIEWS_PER_CTA")) {
         K = atoi(kv);
         if (K <= 0) {
@@ -380,6 +385,7 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
             K = std::max(1, (V + slots - 1) / slots);
         }
     }
+#endif
     std::vector<int> goff{0}, gview, gtrans;
     for (int cls = 0; cls < 2; ++cls) {
         std::vector<int> vs;

@@ -464,10 +464,12 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
 // shared-memory row pitch of a staged chunk (a skew against bank conflicts between lanes
 // sampling two neighbouring rows)
 static int smem_pitch(int P, bool f64) {
-    if (const char* e = getenv("PGET_SMEM_SKEW")) {  // tuning: extra elements per row (even)
+#ifdef PGET_TUNING
+    if (const char* e = getenv("PGET_SMEM_SKEW")) {  // sweep: extra elements per row (even)
         const int k = atoi(e);
         return P + (k > 0 ? (k + 1) / 2 * 2 : 0);
     }
+#endif
     (void)f64;
     return P + 4;  // measured best of skews 0..14 at 128 x 128 (forward and JVP)
 }
