@@ -273,6 +273,39 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
                                 const void* s_step, const void* prop_lam, const void* prop_mu,
                                 pget_check_report* rep, void* stream);
 
+/* Outcome of one iteration of Alg. 2 after its proposal check (host memory). */
+typedef struct {
+    pget_check_report check;  /* the check of the proposal; zero when none was given            */
+    int32_t checked;          /* 1 when a proposal was given and checked                         */
+    int32_t took;             /* the new iterate: 0 u_k (nothing accepted), 1 u_k + s_k (the LM
+                                 step), 2 P(u~) (the proposal)                                    */
+    double nu_next;           /* damping of iteration k + 1: the trial's nu_next clamped to
+                                 [nu_min nu0, nu_max nu0], as a plain solve clamps it            */
+} pget_step_report;
+
+/* One iteration of the accelerated scheme (Alg. 2) after its LM trial: with the trial's
+ * step s_step ([2][n][n] device) and report `trial` at the feasible point (lam_io, mu_io),
+ * checks the proposal u~ = (prop_lam, prop_mu) (device [n][n]; both NULL: no proposal) by
+ * Prop. conv_check (rho(s~) > eta and m_k(s~) <= m_k(s_k), as pget_proposal_check) and
+ * replaces (lam_io, mu_io) in place by the next iterate: P(u~) if the proposal passes,
+ * else P(u_k + s_k) if the trial was accepted, else u_k unchanged (P: projection onto the
+ * constraint set; u_k + s_k is feasible already, the projection only rounds).  The
+ * parameters of iteration k follow the continuation of Sec. 3.1 (pget_params_at(p, k));
+ * nu0 is the first damping of the solve (the trial of iteration 0 reports it).  The
+ * paper's Alg. 2 leaves the damping after an accepted proposal open: the trial's rho
+ * drives it, as in a plain solve.  rep: host.  Synchronises the stream. */
+pget_status pget_lm_step_with_proposal(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p,
+                                       int32_t k, const void* y, void* lam_io, void* mu_io,
+                                       const void* s_step, const pget_trial_report* trial, double nu0,
+                                       const void* prop_lam, const void* prop_mu, pget_step_report* rep,
+                                       void* stream);
+
+/* The parameters of LM iteration k under the continuation of Sec. 3.1 (host only): the
+ * prior weights (TV and geometry priors) divided by alpha_decay^min(k, alpha_decay_iters),
+ * everything else copied; fixed weights when alpha_decay <= 1 or alpha_decay_iters = 0.
+ * pget_lm_solve uses the same schedule.  PGET_EINVAL for null pointers or k < 0. */
+pget_status pget_params_at(const pget_lm_params* p, int32_t k, pget_lm_params* out);
+
 /* Validate LM parameters on the host, without a context: PGET_OK, or PGET_EINVAL with a
  * message naming the field (NaN or out-of-range values, unknown precision or options).
  * Every call that takes parameters runs the same check first. */

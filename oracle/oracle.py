@@ -131,6 +131,7 @@ def lib():
         L.og_lm_trial.argtypes = [gp, C.POINTER(Params), dp, dp, dp, C.c_double, dp, C.POINTER(Trial)]
         L.og_check_proposal.argtypes = [gp, C.POINTER(Params), dp, dp, dp, dp, dp, dp, C.POINTER(Check)]
         L.og_project.argtypes = [C.POINTER(Params), C.c_int, dp, dp]
+        L.og_params_at_k.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(Params)]
         _lib = L
     return _lib
 
@@ -236,6 +237,15 @@ def default_params(**kw) -> Params:
         pr.geo_mask = m.ctypes.data
         pr._keep = m  # the array must live as long as the parameters
     return pr
+
+
+def params_at(pr: Params, k: int) -> Params:
+    """The parameters of LM iteration k under the continuation of Sec. 3.1."""
+    out = Params()
+    lib().og_params_at_k(C.byref(pr), int(k), C.byref(out))
+    if hasattr(pr, "_keep"):
+        out._keep = pr._keep
+    return out
 
 
 def project(pr: Params, lam, mu):

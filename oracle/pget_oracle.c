@@ -1076,3 +1076,6 @@ void og_set_num_threads(int n) {
     (void)n;
 #endif
 }
+
+/* The parameters of LM iteration k under the continuation of Sec. 3.1 (og_params_at). */
+void og_params_at_k(const og_params* pr, int k, og_params* out) { *out = og_params_at(pr, k); }

@@ -1230,6 +1230,38 @@ static pget_status check_impl(Workspace& w, const pget_lm_params& p, const void*
     return PGET_OK;
 }
 
+// Alg. 2 after the trial of iteration k: the proposal's check, then the next iterate in
+// (lam, mu): P(u~), else P(u_k + s_k) when the trial was accepted, else u_k.
+template <typename T>
+static pget_status step_impl(Workspace& w, const pget_lm_params& p0, int k, const void* y, void* lam, void* mu,
+                             const void* s_step, const pget_trial_report& tr, double nu0, const void* pl,
+                             const void* pm, pget_step_report* rep, cudaStream_t st) {
+    const size_t nn = w.nn, e = w.elt;
+    const pget_lm_params p = params_at(p0, k);
+    memset(rep, 0, sizeof *rep);
+    rep->took = tr.accept ? 1 : 0;
+    if (pl) {
+        pget_status s = check_impl<T>(w, p, y, lam, mu, s_step, pl, pm, &rep->check, st);
+        if (s != PGET_OK) return s;
+        rep->checked = 1;
+        if (rep->check.accept) {  // check_impl left the projected proposal in w.ut
+            CK(cudaMemcpyAsync(lam, w.ut, e * nn, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(mu, (const char*)w.ut + e * nn, e * nn, cudaMemcpyDeviceToDevice, st));
+            rep->took = 2;
+        }
+    }
+    if (rep->took == 1) {  // u_k + s_k, projected like every iterate
+        CK(cudaMemcpyAsync(w.u, lam, e * nn, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync((char*)w.u + e * nn, mu, e * nn, cudaMemcpyDeviceToDevice, st));
+        lm_step<T>((const T*)w.u, (const T*)s_step, (T*)w.ut, (T*)w.s, nn, feas_of(p), st);
+        CK(cudaMemcpyAsync(lam, w.ut, e * nn, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(mu, (const char*)w.ut + e * nn, e * nn, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    rep->nu_next = std::min(std::max(tr.nu_next, p.nu_min * nu0), p.nu_max * nu0);
+    return PGET_OK;
+}
+
 template <typename T>
 static pget_status init_impl(Workspace& w, const pget_lm_params& p, double mu_init, const void* y, void* lam,
                              void* mu, cudaStream_t st) {
@@ -1556,6 +1588,38 @@ pget_status pget_proposal_check(pget_ctx* ctx, const pget_geometry* g, const pge
         cudaStream_t st = (cudaStream_t)stream;
         return w->f64 ? check_impl<double>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st)
                       : check_impl<float>(*w, *p, y, lam, mu, s_step, prop_lam, prop_mu, rep, st);
+    });
+}
+
+pget_status pget_lm_step_with_proposal(pget_ctx* ctx, const pget_geometry* g, const pget_lm_params* p, int32_t k,
+                                       const void* y, void* lam, void* mu, const void* s_step,
+                                       const pget_trial_report* trial, double nu0, const void* pl, const void* pm,
+                                       pget_step_report* rep, void* stream) {
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_lm_step_with_proposal");
+        if (!ctx || !y || !lam || !mu || !s_step || !trial || !rep) return fail(PGET_EINVAL, "null argument");
+        if ((pl == nullptr) != (pm == nullptr)) return fail(PGET_EINVAL, "give both proposal images or neither");
+        if (k < 0) return fail(PGET_EINVAL, "iteration k must be >= 0");
+        if (!(nu0 > 0.0) || !std::isfinite(nu0)) return fail(PGET_EINVAL, "nu0 must be finite and > 0");
+        pget_status s = check_params(p);
+        if (s != PGET_OK) return s;
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard dg(ctx->device);
+        Workspace* w;
+        s = get_workspace(ctx, g, p->precision, &w);
+        if (s != PGET_OK) return s;
+        cudaStream_t st = (cudaStream_t)stream;
+        return w->f64 ? step_impl<double>(*w, *p, k, y, lam, mu, s_step, *trial, nu0, pl, pm, rep, st)
+                      : step_impl<float>(*w, *p, k, y, lam, mu, s_step, *trial, nu0, pl, pm, rep, st);
+    });
+}
+
+pget_status pget_params_at(const pget_lm_params* p, int32_t k, pget_lm_params* out) {
+    return guarded([&]() -> pget_status {
+        if (!p || !out) return fail(PGET_EINVAL, "null argument");
+        if (k < 0) return fail(PGET_EINVAL, "iteration k must be >= 0");
+        *out = params_at(*p, k);
+        return PGET_OK;
     });
 }
 

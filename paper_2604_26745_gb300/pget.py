@@ -80,6 +80,10 @@ class pget_check_report(C.Structure):
                 ("ared_prop", C.c_double), ("rho_prop", C.c_double), ("accept", C.c_int32), ("pad", C.c_int32)]
 
 
+class pget_step_report(C.Structure):
+    _fields_ = [("check", pget_check_report), ("checked", C.c_int32), ("took", C.c_int32), ("nu_next", C.c_double)]
+
+
 def _fields(st) -> dict:
     return {k: getattr(st, k) for k, _ in st._fields_ if k != "pad"}
 
@@ -105,6 +109,10 @@ _SIGS = {
     "pget_proposal_check": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp, _vp,
                              _vp, _vp, C.POINTER(pget_check_report), _vp], C.c_int),
     "pget_project": ([_vp, C.POINTER(pget_lm_params), C.c_int32, _vp, _vp, _vp], C.c_int),
+    "pget_lm_step_with_proposal": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), C.c_int32, _vp, _vp,
+                                    _vp, _vp, C.POINTER(pget_trial_report), C.c_double, _vp, _vp,
+                                    C.POINTER(pget_step_report), _vp], C.c_int),
+    "pget_params_at": ([C.POINTER(pget_lm_params), C.c_int32, C.POINTER(pget_lm_params)], C.c_int),
     "pget_check_params": ([C.POINTER(pget_lm_params)], C.c_int),
     "pget_geometry_info": ([C.POINTER(pget_geometry), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)], C.c_int),
@@ -379,6 +387,36 @@ def pget_proposal_check(ctx: Context, g: pget_geometry, p: pget_lm_params, y, la
                                       _arr(s_step, q, 2 * nn, d, "s_step"), _arr(prop_lam, q, nn, d, "prop_lam"),
                                       _arr(prop_mu, q, nn, d, "prop_mu"), C.byref(rep), _stream(stream)), ctx.h)
     return _fields(rep)
+
+
+TOOK = ("none", "step", "proposal")
+
+
+def pget_lm_step_with_proposal(ctx: Context, g: pget_geometry, p: pget_lm_params, k: int, y, lam, mu, s_step,
+                               trial: dict, nu0: float, prop_lam=None, prop_mu=None, stream=None) -> dict:
+    """Alg. 2 after the LM trial of iteration k (see pget.h): checks the proposal (if
+    given) and replaces (lam, mu) in place by the next iterate.  trial: the report
+    pget_lm_trial returned.  Returns {"check": dict or None, "took": "none" | "step" |
+    "proposal", "nu_next": the clamped damping of iteration k + 1}."""
+    tr = pget_trial_report(**{f: trial[f] for f, _ in pget_trial_report._fields_})
+    rep = pget_step_report()
+    q, nn, M, d = p.precision, g.n * g.n, g.n_angles * g.n_det, ctx.device
+    if (prop_lam is None) != (prop_mu is None):
+        raise ValueError("give both proposal images or neither")
+    pl = None if prop_lam is None else _arr(prop_lam, q, nn, d, "prop_lam")
+    pm = None if prop_mu is None else _arr(prop_mu, q, nn, d, "prop_mu")
+    _check(load().pget_lm_step_with_proposal(ctx.h, C.byref(g), C.byref(p), int(k), _arr(y, q, M, d, "y"),
+                                             _arr(lam, q, nn, d, "lam"), _arr(mu, q, nn, d, "mu"),
+                                             _arr(s_step, q, 2 * nn, d, "s_step"), C.byref(tr), float(nu0), pl, pm,
+                                             C.byref(rep), _stream(stream)), ctx.h)
+    return {"check": _fields(rep.check) if rep.checked else None, "took": TOOK[rep.took], "nu_next": rep.nu_next}
+
+
+def pget_params_at(p: pget_lm_params, k: int) -> pget_lm_params:
+    """The parameters of LM iteration k under the continuation of Sec. 3.1."""
+    out = pget_lm_params()
+    _check(load().pget_params_at(C.byref(p), int(k), C.byref(out)))
+    return out
 
 
 def pget_project(ctx: Context, p: pget_lm_params, lam, mu, stream=None):

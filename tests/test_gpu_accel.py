@@ -176,3 +176,45 @@ def test_driver_with_the_conv_proposal(O, P, torch):
         if x["took"] == "proposal":
             assert x["check"]["rho_prop"] > p.eta and x["check"]["pred_prop"] >= x["check"]["pred_step"]
     assert (ln >= 0).all() and (mn >= 0).all()
+
+
+@pytest.mark.parametrize("case", ["truth", "noise", "none", "continuation"])
+def test_step_with_proposal_matches_oracle(O, P, torch, case):
+    """pget_lm_step_with_proposal (Alg. 2 after the trial, in the library): the check, the
+    next iterate (P(u~), P(u + s) or u) and the clamped damping equal the oracle's check
+    and projection on the same trial, FP64."""
+    ph, go, g, y = _setup(O, P, torch, seed=23, noise=None)
+    kw = dict(alpha_decay=5.0, alpha_decay_iters=3) if case == "continuation" else {}
+    k = 2 if case == "continuation" else 0
+    pr = O.params_at(O.default_params(cg_max_iters=6, **kw), k)
+    rs = np.random.default_rng(5)
+    lk = np.clip(ph.lam + 0.05 * rs.standard_normal(ph.lam.shape), 0, pr.lambda_max)
+    mk = np.clip(ph.mu + 0.005 * rs.standard_normal(ph.mu.shape), 0, pr.mu_max)
+    so, to = O.lm_trial(go, pr, y, lk, mk, 1e2)
+    prop = {"truth": (ph.lam, ph.mu), "noise": (lk + rs.uniform(-1, 1, lk.shape), mk + rs.uniform(-0.1, 0.1, mk.shape)),
+            "none": None, "continuation": (ph.lam, ph.mu)}[case]
+    co = O.check_proposal(go, pr, y, lk, mk, so, *prop) if prop else None
+    if co and co["accept"]:
+        want = O.project(pr, *prop)
+    elif to["accept"]:
+        want = O.project(pr, lk + so[0], mk + so[1])
+    else:
+        want = (lk, mk)
+    p = P.default_params(cg_max_iters=6, cg_rel_tol=1e-10, precision=0, **kw)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    lam, mu = t(lk), t(mk)
+    with P.Context(0) as c:
+        pk = P.pget_params_at(p, k)
+        assert abs(pk.alpha_lambda - pr.alpha_lambda) <= 1e-15 * pr.alpha_lambda
+        s, tr = P.pget_lm_trial(c, g, pk, t(y), lam, mu, 1e2)
+        st = P.pget_lm_step_with_proposal(c, g, p, k, t(y), lam, mu, s, tr, 7.0,
+                                          *(t(a) for a in prop) if prop else (None, None))
+    assert tr["accept"] == to["accept"]
+    assert (st["check"] is None) == (co is None)
+    if co:
+        assert st["check"]["accept"] == co["accept"]
+    assert st["took"] == ("proposal" if co and co["accept"] else ("step" if to["accept"] else "none"))
+    assert _rel(lam.cpu().numpy(), want[0]) <= 1e-10 and _rel(mu.cpu().numpy(), want[1]) <= 1e-10
+    assert st["nu_next"] == min(max(tr["nu_next"], p.nu_min * 7.0), p.nu_max * 7.0)
+    if case == "truth":
+        assert st["took"] == "proposal"

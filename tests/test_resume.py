@@ -8,9 +8,9 @@ iterates bitwise, with the same decisions and damping. The cases:
 - proposals, some of them taken;
 - a binding linear bound, where the resumed iterate is not projected a second time.
 
-The Alg. 2 driver's host logic runs unchanged. Only its four library calls (trial, proposal
-check, projection, parameters) are served by the oracle on CPU tensors; on the GPU the same
-calls go to the CUDA library.
+The Alg. 2 driver's host logic runs unchanged. Only its library calls (parameters of
+iteration k, trial, the step with the proposal check, projection) are served by the oracle
+on CPU tensors; on the GPU the same calls go to the CUDA library.
 """
 import numpy as np
 import pytest
@@ -42,9 +42,32 @@ class _OracleCalls:
         s, tr = self.O.lm_trial(self.go, self._pr(p), y.numpy(), lam.numpy(), mu.numpy(), nu)
         return torch.from_numpy(s), tr
 
-    def pget_proposal_check(self, ctx, g, p, y, lam, mu, s, pl, pm):
-        return self.O.check_proposal(self.go, self._pr(p), y.numpy(), lam.numpy(), mu.numpy(), s.numpy(),
-                                     pl.numpy(), pm.numpy())
+    def pget_params_at(self, p, k):
+        q = P.pget_lm_params.from_buffer_copy(p)
+        o = self.O.params_at(self._pr(p), k)
+        for name in ("alpha_lambda", "alpha_mu", "geo_alpha_lambda", "geo_alpha_mu"):
+            setattr(q, name, getattr(o, name))
+        return q
+
+    def pget_lm_step_with_proposal(self, ctx, g, p, k, y, lam, mu, s, tr, nu0, pl=None, pm=None):
+        # Alg. 2 after the trial, with the oracle's check and projection: P(u~) if the
+        # proposal passes, else P(u + s) if the trial was accepted, else u; the damping
+        # clamped to [nu_min nu0, nu_max nu0]
+        pr = self.O.params_at(self._pr(p), k)
+        chk, took = None, ("step" if tr["accept"] else "none")
+        if pl is not None:
+            chk = self.O.check_proposal(self.go, pr, y.numpy(), lam.numpy(), mu.numpy(), s.numpy(),
+                                        pl.numpy(), pm.numpy())
+            if chk["accept"]:
+                a, b = self.O.project(pr, pl.numpy(), pm.numpy())
+                took = "proposal"
+        if took == "step":
+            a, b = self.O.project(pr, (lam + s[0]).numpy(), (mu + s[1]).numpy())
+        if took != "none":
+            lam.copy_(torch.from_numpy(a))
+            mu.copy_(torch.from_numpy(b))
+        nu = min(max(tr["nu_next"], p.nu_min * nu0), p.nu_max * nu0)
+        return {"check": chk, "took": took, "nu_next": nu}
 
 
 def _proposal(u, s, k):
