@@ -35,7 +35,7 @@ WORKLOAD_NAME = ("single-request LM: 128x128 grid, 9x9 rods r=5, 360 angles x 18
                  "x 5 triangular sub-rays, Poisson 1e5, 20 LM x 30 CG, FP32-Kahan rays / FP64 scalars")
 METRIC = "recon/s"
 # precisions whose reconstruction of the oracle-stored case is compared with the oracle
-PRECISIONS_CHECKED = (("f32_kahan", 2), ("f64", 0))
+PRECISIONS_CHECKED = (("f32_kahan", 2), ("mixed", 3), ("f64", 0))
 SUB = (16, 16)
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the

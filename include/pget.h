@@ -11,7 +11,8 @@
  *
  * Conventions shared by every call
  *   - Arrays are caller-owned, contiguous DEVICE pointers unless a name ends in _host.
- *     Element type: double for PGET_F64, float for PGET_F32 and PGET_F32_KAHAN.
+ *     Element type: double for PGET_F64 and PGET_MIXED, float for PGET_F32 and
+ *     PGET_F32_KAHAN.
  *     The library never frees caller memory and never keeps a caller pointer after a
  *     call returns, with one exception: a request queued by pget_submit reads the
  *     geometry-prior mask p->geo_mask while it runs.
@@ -50,7 +51,15 @@ typedef enum {
 typedef enum {
     PGET_F64 = 0,         /* everything in double                                        */
     PGET_F32 = 1,         /* float ray sums and vectors; double dot products and scalars */
-    PGET_F32_KAHAN = 2    /* as PGET_F32 with Kahan-compensated sums along every ray     */
+    PGET_F32_KAHAN = 2,   /* as PGET_F32 with Kahan-compensated sums along every ray     */
+    PGET_MIXED = 3        /* the precision pattern of the solver: the Jacobian products of
+                             CG (JVP and adjoint walks) as PGET_F32_KAHAN; the forward model
+                             of every objective evaluation (the start of a solve and each
+                             trial point, whose value decides acceptance) in double, and
+                             the iterate, data, residuals, CG and LM vectors in double.
+                             Caller arrays are double; the operator calls (pget_forward,
+                             pget_jvp, pget_vjp) run the float walks.  Not taken by
+                             pget_forward_noalloc or the batched operators. */
 } pget_precision;
 
 /* Measurement geometry (Sec. 2 and Sec. 2.1 of the paper: two opposed detector banks
@@ -174,6 +183,24 @@ pget_status pget_jvp(pget_ctx* ctx, const pget_geometry* g, int32_t precision,
 pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t precision,
                      const void* lam, const void* mu, const void* r, void* glam, void* gmu,
                      void* stream);
+
+/* The three operators above for a batch of independent image pairs of one geometry
+ * (the differentiation workload: many (lambda, mu) pairs per call): item b of lam, mu
+ * ([batch][n][n]), dlam, dmu ([batch][n][n]), y, dy, r ([batch][n_angles][n_det]) and glam,
+ * gmu ([batch][n][n]) is the single-item call's argument, and its result equals the
+ * single-item call's bitwise.  The items run in chunks, each chunk one walk launch over all
+ * its items' views (the chunk holds up to 4 GiB of adjoint partial images, so at least one
+ * item); the chunk buffers stay with the context for the next call.  Precisions PGET_F64,
+ * PGET_F32 and PGET_F32_KAHAN (PGET_EINVAL otherwise); batch = 0 does nothing.
+ * Asynchronous like the single-item calls. */
+pget_status pget_forward_batch(pget_ctx* ctx, const pget_geometry* g, int32_t precision, int32_t batch,
+                               const void* lam, const void* mu, void* y, void* stream);
+pget_status pget_jvp_batch(pget_ctx* ctx, const pget_geometry* g, int32_t precision, int32_t batch,
+                           const void* lam, const void* mu, const void* dlam, const void* dmu, void* dy,
+                           void* stream);
+pget_status pget_vjp_batch(pget_ctx* ctx, const pget_geometry* g, int32_t precision, int32_t batch,
+                           const void* lam, const void* mu, const void* r, void* glam, void* gmu,
+                           void* stream);
 
 /* Device-side status of the asynchronous operator calls above (pget_forward, pget_jvp,
  * pget_vjp) made on this context since the last call of this function or since the

@@ -4,7 +4,9 @@ derivatives (Eq. (2)), computed by the library's CUDA kernels.
 ``project(lam, mu, geometry)`` returns y = A(lam, mu) for one image pair [n, n] or a batch
 [..., n, n]; reverse mode (``.backward()``) runs the adjoint kernel (pget_vjp) and forward
 mode (dual tensors of ``torch.autograd.forward_ad``) runs the Jacobian-vector kernel
-(pget_jvp).  Only lam and mu are
+(pget_jvp).  A batch runs through the batched calls (pget_forward_batch, pget_jvp_batch,
+pget_vjp_batch): one walk launch covers the views of many pairs, with every pair's result
+equal to its single-pair call's bitwise.  Only lam and mu are
 kept for the backward pass: the attenuation prefixes along every ray are recomputed by
 the kernels rather than stored (storing the per-sample factors exp(-E_j) and prefix sums
 would take 8 bytes per ray sample, ~1 GB per 256 x 256 image at 360 x 182 x 5 rays).
@@ -37,12 +39,12 @@ def _prec_of(dtype: torch.dtype, precision):
 
 
 class AttenuatedRayTransform(torch.autograd.Function):
-    """y = A(lam, mu) for one image pair on one CUDA device."""
+    """y = A(lam, mu) for image pairs [B, n, n] (B >= 1) on one CUDA device."""
 
     @staticmethod
     def forward(lam, mu, geometry, precision):
         ctx_ = context(lam.device.index or 0)
-        return P.pget_forward(ctx_, geometry, precision, lam.contiguous(), mu.contiguous())
+        return P.pget_forward_batch(ctx_, geometry, precision, lam.contiguous(), mu.contiguous())
 
     @staticmethod
     def setup_context(ctx, inputs, output):
@@ -56,8 +58,8 @@ class AttenuatedRayTransform(torch.autograd.Function):
     def backward(ctx, grad_y):
         lam, mu = ctx.saved_tensors
         c = context(lam.device.index or 0)
-        gl, gm = P.pget_vjp(c, ctx.geometry, ctx.precision, lam.contiguous(), mu.contiguous(),
-                            grad_y.contiguous())
+        gl, gm = P.pget_vjp_batch(c, ctx.geometry, ctx.precision, lam.contiguous(), mu.contiguous(),
+                                  grad_y.contiguous())
         return gl, gm, None, None
 
     @staticmethod
@@ -66,7 +68,7 @@ class AttenuatedRayTransform(torch.autograd.Function):
         c = context(lam.device.index or 0)
         dlam = torch.zeros_like(lam) if dlam is None else dlam.contiguous()
         dmu = torch.zeros_like(mu) if dmu is None else dmu.contiguous()
-        return P.pget_jvp(c, ctx.geometry, ctx.precision, lam.contiguous(), mu.contiguous(), dlam, dmu)
+        return P.pget_jvp_batch(c, ctx.geometry, ctx.precision, lam.contiguous(), mu.contiguous(), dlam, dmu)
 
 
 def project(lam: torch.Tensor, mu: torch.Tensor, geometry: P.pget_geometry, precision=None) -> torch.Tensor:
@@ -76,13 +78,11 @@ def project(lam: torch.Tensor, mu: torch.Tensor, geometry: P.pget_geometry, prec
     prec = _prec_of(lam.dtype, precision)
     if P.dtype_of(prec) != lam.dtype:
         raise ValueError("tensor dtype does not match the precision")
-    if lam.dim() == 2:
-        return AttenuatedRayTransform.apply(lam, mu, geometry, prec)
     lead = lam.shape[:-2]
     ls = lam.reshape(-1, *lam.shape[-2:])
     ms = mu.reshape(-1, *mu.shape[-2:])
-    ys = [AttenuatedRayTransform.apply(ls[i], ms[i], geometry, prec) for i in range(ls.shape[0])]
-    return torch.stack(ys).reshape(*lead, geometry.n_angles, geometry.n_det)
+    y = AttenuatedRayTransform.apply(ls, ms, geometry, prec)
+    return y.reshape(*lead, geometry.n_angles, geometry.n_det)
 
 
 def data_loss(lam, mu, y, geometry, precision=None) -> torch.Tensor:

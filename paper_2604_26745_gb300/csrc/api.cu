@@ -24,6 +24,14 @@ using namespace pget;
 
 static thread_local std::string g_last_error;
 
+static bool known_precision(int p) {
+    return p == PGET_F64 || p == PGET_F32 || p == PGET_F32_KAHAN || p == PGET_MIXED;
+}
+// the precision of the ray kernels (walks) for a solver precision
+static int walk_precision(int p) { return p == PGET_MIXED ? PGET_F32_KAHAN : p; }
+// solver vectors (iterate, data, CG and LM vectors) in double
+static bool vectors_f64(int p) { return p == PGET_F64 || p == PGET_MIXED; }
+
 static pget_status fail(pget_status s, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -161,8 +169,18 @@ struct Workspace {
     Profiler* prof = nullptr;
     Geometry g;
     int prec = 0;
-    bool f64 = false;
-    size_t elt = 4;
+    bool f64 = false;     // solver vectors in double
+    size_t elt = 4;       // bytes of a solver vector element
+    int wprec = 0;        // precision of the ray kernels (walks)
+    bool wf64 = false;    // walk images, ray totals and partial images in double
+    size_t welt = 4;      // bytes of a walk element
+    void* sino_w = nullptr;  // PGET_MIXED: a sinogram in the walks' type
+    // PGET_MIXED: the objective's forward model in double: its plan, packed layouts, ray
+    // totals (narrowed to the float ones the adjoint reads) and weight tables
+    bool obj64 = false;
+    WalkPlan pf64;
+    void* pk64[2] = {nullptr, nullptr};
+    void *U64 = nullptr, *d_w64 = nullptr, *d_depth64 = nullptr;
     int P = 0, groups = 1, n_views = 0;
     size_t nn = 0, M = 0, nslots = 0, img_elems = 0;
     WalkPlan pf, pj, pv;
@@ -236,23 +254,25 @@ struct Workspace {
 
 // bytes a workspace for this geometry and precision will take
 static size_t workspace_bytes(const Geometry& g, int prec, int groups) {
-    size_t elt = prec == PGET_F64 ? 8 : 4;
+    size_t elt = vectors_f64(prec) ? 8 : 4, welt = walk_precision(prec) == PGET_F64 ? 8 : 4;
     size_t nn = (size_t)g.n * g.n, M = (size_t)g.n_angles * g.n_det;
     size_t V = (size_t)g.n_angles * g.n_banks;
     size_t P = (size_t)((g.n + 2 + 1) / 2) * 2;
-    size_t img = (size_t)(g.n + 2) * P * 2 * elt;
+    size_t img = (size_t)(g.n + 2) * P * 2 * welt;
     size_t b = 0;
     b += 6 * img;                       // three packed pairs, two layouts each
     b += 8 * 2 * nn * elt + 2 * nn * elt;  // vectors + weights
-    b += 4 * M * elt;                   // sinograms
-    b += 2 * V * g.max_slots * elt;     // slot totals
-    b += V * 2 * nn * elt;              // per-view partial gradients
-    b += (size_t)groups * 2 * nn * elt;
+    b += 4 * M * elt + (elt != welt ? M * welt : 0);  // sinograms
+    b += 2 * V * g.max_slots * welt;    // slot totals
+    b += V * 2 * nn * welt;             // per-view partial gradients
+    b += (size_t)groups * 2 * nn * welt;
     b += 4 * kRedBlocks * 8 + sizeof(LmState) + 64;
     b += V * sizeof(ViewDev) + V * 4 + (size_t)g.n_det * g.n_sub * 4 + g.n_sub * 8;
     b += g.src_off.size() * 4 + g.src_det.size() * 12 + g.clip.size() * 4;
     b += V * (size_t)(g.n + 1) * 8;     // adjoint ray windows (at most n + 1 chunks per view)
-    if (g.depth) b += 2 * (size_t)g.T * elt;  // depth factors
+    if (g.depth) b += 2 * (size_t)g.T * welt;  // depth factors
+    if (prec == PGET_MIXED)  // the objective's double forward: layouts, ray totals, tables
+        b += (size_t)(g.n + 2) * P * 2 * 16 + 8 * V * (size_t)g.max_slots + 16 * (size_t)g.T + 8 * g.n_sub;
     return b;
 }
 
@@ -279,8 +299,27 @@ struct Slot {
 };
 }  // namespace pget
 
+namespace pget {
+// Buffers of the batched operator calls for one workspace: the packed layouts (iterate
+// and direction), ray totals, a scratch sinogram and the adjoint partial images of `cap`
+// items at once.
+struct BatchBufs {
+    std::string key;
+    int cap = 0;
+    long long s_img = 0, s_slot = 0, s_sino = 0, s_part = 0;  // bytes per item
+    void *pk_u[2] = {nullptr, nullptr}, *pk_p[2] = {nullptr, nullptr};
+    void *U = nullptr, *sino = nullptr, *gpart = nullptr;
+    std::vector<void*> allocs;
+    ~BatchBufs() {
+        for (void* a : allocs) cudaFree(a);
+    }
+};
+constexpr size_t kBatchPartBytes = size_t(4) << 30;  // adjoint partial images of one chunk of items
+}  // namespace pget
+
 struct pget_ctx {
     Profiler prof;
+    std::unique_ptr<pget::BatchBufs> batch;
     std::vector<std::unique_ptr<pget::Slot>> slots;
     // idle serving workspaces (with their captured graphs), reused by geometry key so that
     // a stream of mixed sizes does not allocate and free device memory per request
@@ -320,8 +359,7 @@ struct DeviceGuard {
 pget_status resolve(const pget_geometry* gin, int prec, Geometry* g, std::string* key, int* groups,
                     size_t* need) {
     if (!gin) return fail(PGET_EINVAL, "null geometry");
-    if (prec != PGET_F64 && prec != PGET_F32 && prec != PGET_F32_KAHAN)
-        return fail(PGET_EINVAL, "unknown precision %d", prec);
+    if (!known_precision(prec)) return fail(PGET_EINVAL, "unknown precision %d", prec);
     std::string msg;
     pget_status s = build_geometry(*gin, g, &msg);
     if (s != PGET_OK) return fail(s, "%s", msg.c_str());
@@ -343,8 +381,12 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     w->g = std::move(g);
     Geometry& G = w->g;
     w->prec = prec;
-    w->f64 = prec == PGET_F64;
+    w->f64 = vectors_f64(prec);
     w->elt = w->f64 ? 8 : 4;
+    w->wprec = walk_precision(prec);
+    w->wf64 = w->wprec == PGET_F64;
+    w->welt = w->wf64 ? 8 : 4;
+    w->obj64 = prec == PGET_MIXED;
     w->P = ((G.n + 2 + 1) / 2) * 2;
     w->groups = groups;
     w->n_views = V;
@@ -363,13 +405,14 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
 #endif
         return kb * 1024;
     };
-    w->pf = plan_walk(G, w->P, kFwd, w->f64, budget("PGET_SMEM_KB_FWD", 64));
-    w->pj = plan_walk(G, w->P, kJvp, w->f64, budget("PGET_SMEM_KB_JVP", 72));
+    w->pf = plan_walk(G, w->P, kFwd, w->wf64, budget("PGET_SMEM_KB_FWD", 64));
+    w->pj = plan_walk(G, w->P, kJvp, w->wf64, budget("PGET_SMEM_KB_JVP", 72));
     {
         std::vector<int2> rows;
-        ray_rows(G, w->f64, &rows);
-        w->pv = plan_walk(G, w->P, kVjp, w->f64, budget("PGET_SMEM_KB_VJP", 72), &rows);
+        ray_rows(G, w->wf64, &rows);
+        w->pv = plan_walk(G, w->P, kVjp, w->wf64, budget("PGET_SMEM_KB_VJP", 72), &rows);
     }
+    if (w->obj64) w->pf64 = plan_walk(G, w->P, kFwd, true, budget("PGET_SMEM_KB_FWD", 64));
     // views per adjoint CTA: one (the hardware scheduler balances single-view CTAs across
     // SMs best); a build with -DPGET_TUNING reads PGET_VJP_VIEWS_PER_CTA > 1 to group views
     // of one orientation, which shrinks the partial images but assigns work statically (0
@@ -399,20 +442,34 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     }
     w->n_groups = (int)gtrans.size();
     w->n_groups0 = (int)std::count(gtrans.begin(), gtrans.end(), 0);  // normal-frame groups come first
-    const size_t e = w->elt, e2 = 2 * e;
-    (void)e2;
+    const size_t e = w->elt, we = w->welt;  // solver and walk element bytes
     CK(w->alloc(&w->d_views, sizeof(ViewDev) * V));
     CK(cudaMemcpy(w->d_views, G.views.data(), sizeof(ViewDev) * V, cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_det_slot, sizeof(int) * G.det_slot.size()));
     CK(cudaMemcpy(w->d_det_slot, G.det_slot.data(), sizeof(int) * G.det_slot.size(), cudaMemcpyHostToDevice));
     auto upload_t = [&](void** dst, const std::vector<double>& src) -> cudaError_t {
-        cudaError_t er = w->alloc(dst, e * src.size());
+        cudaError_t er = w->alloc(dst, we * src.size());
         if (er != cudaSuccess) return er;
-        if (w->f64) return cudaMemcpy(*dst, src.data(), 8 * src.size(), cudaMemcpyHostToDevice);
+        if (w->wf64) return cudaMemcpy(*dst, src.data(), 8 * src.size(), cudaMemcpyHostToDevice);
         std::vector<float> f(src.begin(), src.end());
         return cudaMemcpy(*dst, f.data(), 4 * f.size(), cudaMemcpyHostToDevice);
     };
     CK(upload_t(&w->d_w, G.w));
+    if (w->obj64) {  // the double tables of the objective's forward model
+        CK(w->alloc(&w->d_w64, 8 * G.w.size()));
+        CK(cudaMemcpy(w->d_w64, G.w.data(), 8 * G.w.size(), cudaMemcpyHostToDevice));
+        if (G.depth) {
+            std::vector<double> dt(2 * (size_t)G.T);
+            for (int j = 0; j < G.T; ++j) {
+                dt[2 * j] = G.depth_w[j];
+                dt[2 * j + 1] = G.depth_c[j];
+            }
+            CK(w->alloc(&w->d_depth64, 8 * dt.size()));
+            CK(cudaMemcpy(w->d_depth64, dt.data(), 8 * dt.size(), cudaMemcpyHostToDevice));
+        }
+        for (int l = 0; l < 2; ++l) CK(w->alloc(&w->pk64[l], 16 * w->img_elems));
+        CK(w->alloc(&w->U64, 8 * w->nslots));
+    }
     if (G.depth) {  // interleaved (w_j, c_j) pairs
         std::vector<double> dt(2 * (size_t)G.T);
         for (int j = 0; j < G.T; ++j) {
@@ -431,9 +488,9 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     CK(cudaMemcpy(w->d_src_det, G.src_det.data(), sizeof(int) * G.src_det.size(), cudaMemcpyHostToDevice));
     CK(upload_t(&w->d_src_w, G.src_w));
     for (int l = 0; l < 2; ++l) {
-        CK(w->alloc(&w->pk_u[l], e2 * w->img_elems));
-        CK(w->alloc(&w->pk_ut[l], e2 * w->img_elems));
-        CK(w->alloc(&w->pk_p[l], e2 * w->img_elems));
+        CK(w->alloc(&w->pk_u[l], 2 * we * w->img_elems));
+        CK(w->alloc(&w->pk_ut[l], 2 * we * w->img_elems));
+        CK(w->alloc(&w->pk_p[l], 2 * we * w->img_elems));
     }
     void** vecs[] = {&w->u, &w->ut, &w->x, &w->res, &w->p, &w->q, &w->s, &w->gr};
     for (void** vp : vecs) CK(w->alloc(vp, e * 2 * w->nn));
@@ -443,14 +500,15 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     CK(w->alloc(&w->r, e * w->M));
     CK(w->alloc(&w->rt, e * w->M));
     CK(w->alloc(&w->Jp, e * w->M));
-    CK(w->alloc(&w->U, e * w->nslots));
-    CK(w->alloc(&w->Ut, e * w->nslots));
-    CK(w->alloc(&w->gpart, e * (size_t)w->n_groups * 2 * w->nn));
+    if (we != e) CK(w->alloc(&w->sino_w, we * w->M));
+    CK(w->alloc(&w->U, we * w->nslots));
+    CK(w->alloc(&w->Ut, we * w->nslots));
+    CK(w->alloc(&w->gpart, we * (size_t)w->n_groups * 2 * w->nn));
     CK(w->alloc(&w->d_group_off, sizeof(int) * goff.size()));
     CK(cudaMemcpy(w->d_group_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_group_view, sizeof(int) * gview.size()));
     CK(cudaMemcpy(w->d_group_view, gview.data(), sizeof(int) * gview.size(), cudaMemcpyHostToDevice));
-    CK(w->alloc(&w->part2, e * (size_t)groups * 2 * w->nn));
+    CK(w->alloc(&w->part2, we * (size_t)groups * 2 * w->nn));
     for (int k = 0; k < 4; ++k) CK(w->alloc(&w->dpart[k], sizeof(double) * kRedBlocks));
     CK(w->alloc(&w->lm, sizeof(LmState)));
     CK(w->alloc(&w->err, sizeof(int) * 4));
@@ -529,11 +587,12 @@ cudaError_t op_forward(const Workspace& w, void* const pk[2], void* U_out, void*
     a.u_img[0] = pk[0];
     a.u_img[1] = pk[1];
     a.slot_val = U_out;
-    a.y_out = y_out;
+    a.y_out = w.sino_w ? w.sino_w : y_out;  // a sinogram in the walks' type, widened below
     a.stop = stop;
     w.prof->begin(kPFwd, st);
-    cudaError_t e = launch_walk(kFwd, w.prec, w.pf, a, w.n_views, st);
+    cudaError_t e = launch_walk(kFwd, w.wprec, w.pf, a, w.n_views, st);
     w.prof->end(st);
+    if (e == cudaSuccess && w.sino_w) convert<float, double>((const float*)w.sino_w, (double*)y_out, w.M, stop, st);
     return e;
 }
 
@@ -545,11 +604,38 @@ cudaError_t op_jvp(const Workspace& w, void* const pku[2], void* const pkp[2], v
     a.u_img[1] = pku[1];
     a.p_img[0] = pkp[0];
     a.p_img[1] = pkp[1];
-    a.y_out = dy;
+    a.y_out = w.sino_w ? w.sino_w : dy;
     a.stop = stop;
     w.prof->begin(kPJvp, st);
-    cudaError_t e = launch_walk(kJvp, w.prec, w.pj, a, w.n_views, st);
+    cudaError_t e = launch_walk(kJvp, w.wprec, w.pj, a, w.n_views, st);
     w.prof->end(st);
+    if (e == cudaSuccess && w.sino_w) convert<float, double>((const float*)w.sino_w, (double*)dy, w.M, stop, st);
+    return e;
+}
+
+// The forward model at the planar point uvec (solver type), whose walk layouts pk the
+// caller has packed, where its value enters the objective: op_forward, except in
+// PGET_MIXED, where it runs in double (own layouts and plan) straight into the double
+// sinogram y_out, and the ray totals are narrowed to the float ones the adjoint reads.
+cudaError_t op_objective(Workspace& w, const void* uvec, void* const pk[2], void* U_out, void* y_out,
+                         const int* stop, cudaStream_t st) {
+    if (!w.obj64) return op_forward(w, pk, U_out, y_out, stop, st);
+    const double* u = (const double*)uvec;
+    pack<double, double>(u, u + w.nn, w.g.n, w.P, attenuation_scale(w.g), w.pk64[0], w.pk64[1], stop, st);
+    WalkArgs a = base_args(w);
+    a.w = w.d_w64;
+    a.depth = w.d_depth64;
+    a.Yc = w.pf64.Yc;
+    a.nchunks = w.pf64.nchunks;
+    a.u_img[0] = w.pk64[0];
+    a.u_img[1] = w.pk64[1];
+    a.slot_val = U_out ? w.U64 : nullptr;
+    a.y_out = y_out;
+    a.stop = stop;
+    w.prof->begin(kPFwd, st);
+    cudaError_t e = launch_walk(kFwd, PGET_F64, w.pf64, a, w.n_views, st);
+    w.prof->end(st);
+    if (e == cudaSuccess && U_out) convert<double, float>((const double*)w.U64, (float*)U_out, w.nslots, stop, st);
     return e;
 }
 
@@ -565,13 +651,17 @@ cudaError_t op_vjp(Workspace& w, void* const pku[2], const void* U, const void* 
     a.u_img[1] = pku[1];
     a.slot_val = (void*)U;
     a.r_in = r;
+    if (w.sino_w) {  // the residual in the walks' type
+        convert<double, float>((const double*)r, (float*)w.sino_w, w.M, stop, st);
+        a.r_in = w.sino_w;
+    }
     a.gpart = w.gpart;
     a.win = w.d_win;
     a.group_off = w.d_group_off;
     a.group_view = w.d_group_view;
     a.stop = stop;
     w.prof->begin(kPVjp, st);
-    cudaError_t e = launch_walk(kVjp, w.prec, w.pv, a, w.n_groups, st);
+    cudaError_t e = launch_walk(kVjp, w.wprec, w.pv, a, w.n_groups, st);
     w.prof->end(st);
     if (e != cudaSuccess) return e;
     ra.n = w.g.n;
@@ -579,20 +669,33 @@ cudaError_t op_vjp(Workspace& w, void* const pku[2], const void* U, const void* 
     w.prof->begin(kPRed, st);
     // the view sum is already two-level (<= ~40 terms per level): plain sums suffice;
     // the Kahan compensation of PGET_F32_KAHAN applies along rays
-    reduce_views<T>((const T*)w.gpart, w.g.n, w.n_groups, w.n_groups0, w.groups, (T*)w.part2, ra, false, st);
+    if (w.wf64 || sizeof(T) == 4)
+        reduce_views<T, T>((const T*)w.gpart, w.g.n, w.n_groups, w.n_groups0, w.groups, (T*)w.part2, ra, false, st);
+    else
+        reduce_views<T, float>((const float*)w.gpart, w.g.n, w.n_groups, w.n_groups0, w.groups, (float*)w.part2, ra,
+                               false, st);
     w.prof->end(st);
     return cudaGetLastError();
 }
 
+// planar solver vectors (type T) -> the walks' packed layouts (their own type)
+template <typename T>
+void pack_pair(const Workspace& w, const void* lam, const void* mu, void* const pk[2], const int* skip,
+               cudaStream_t st) {
+    const T* l = (const T*)lam;
+    const T* m = (const T*)mu;
+    if (w.wf64 || sizeof(T) == 4) pack<T, T>(l, m, w.g.n, w.P, attenuation_scale(w.g), pk[0], pk[1], skip, st);
+    else pack<T, float>(l, m, w.g.n, w.P, attenuation_scale(w.g), pk[0], pk[1], skip, st);
+}
+
 template <typename T>
 void pack_vec(const Workspace& w, const void* vec, void* const pk[2], const int* skip, cudaStream_t st) {
-    const T* a = (const T*)vec;
-    pack<T>(a, a + w.nn, w.g.n, w.P, attenuation_scale(w.g), pk[0], pk[1], skip, st);
+    pack_pair<T>(w, vec, (const T*)vec + w.nn, pk, skip, st);
 }
 
 template <typename T>
 void pack_pair(const Workspace& w, const void* lam, const void* mu, void* const pk[2], cudaStream_t st) {
-    pack<T>((const T*)lam, (const T*)mu, w.g.n, w.P, attenuation_scale(w.g), pk[0], pk[1], nullptr, st);
+    pack_pair<T>(w, lam, mu, pk, nullptr, st);
 }
 
 // Geometry priors of Eq. (6) in a fused reduction: the Hessian term (gradient = false) or
@@ -633,8 +736,12 @@ pget_status run_cg(Workspace& w, const void* b, double scale_b, double nu, const
         e = op_vjp<T>(w, w.pk_u, w.U, w.Jp, ra, stop, st);
         if (e != cudaSuccess) return fail(PGET_ECUDA, "vjp launch: %s", cudaGetErrorString(e));
         cg_step<T>((T*)w.x, (T*)w.res, (const T*)w.p, (const T*)w.q, m, w.dpart[0], w.dpart[1], cg, st);
-        cg_dir_pack<T>((T*)w.p, (const T*)w.res, w.dpart[1], cg, w.g.n, w.P, attenuation_scale(w.g), w.pk_p[0],
-                       w.pk_p[1], st);
+        if (w.wf64 || sizeof(T) == 4)
+            cg_dir_pack<T, T>((T*)w.p, (const T*)w.res, w.dpart[1], cg, w.g.n, w.P, attenuation_scale(w.g), w.pk_p[0],
+                              w.pk_p[1], st);
+        else
+            cg_dir_pack<T, float>((T*)w.p, (const T*)w.res, w.dpart[1], cg, w.g.n, w.P, attenuation_scale(w.g),
+                                  w.pk_p[0], w.pk_p[1], st);
     }
     CK(cudaGetLastError());
     return PGET_OK;
@@ -721,8 +828,7 @@ pget_status check_params(const pget_lm_params* p) {
     if (!std::isfinite(p->eta) || !std::isfinite(p->rho_lo) || !std::isfinite(p->rho_hi) || !(p->rho_lo <= p->rho_hi))
         return fail(PGET_EINVAL, "eta, rho_lo and rho_hi must be finite, rho_lo <= rho_hi");
     if (!(p->nu_min > 0) || !(p->nu_min <= p->nu_max)) return fail(PGET_EINVAL, "need 0 < nu_min <= nu_max");
-    if (p->precision != PGET_F64 && p->precision != PGET_F32 && p->precision != PGET_F32_KAHAN)
-        return fail(PGET_EINVAL, "unknown precision %d", p->precision);
+    if (!known_precision(p->precision)) return fail(PGET_EINVAL, "unknown precision %d", p->precision);
     if (!(p->alpha_decay == 0.0 || p->alpha_decay >= 1.0) || p->alpha_decay_iters < 0)
         return fail(PGET_EINVAL, "alpha_decay must be 0 or >= 1 and alpha_decay_iters >= 0");
     if (p->geo_mask && (!(p->geo_alpha_lambda >= 0) || !(p->geo_alpha_mu >= 0) || !std::isfinite(p->geo_mu_water)))
@@ -762,7 +868,7 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
     pack_vec<T>(w, w.u, w.pk_u, nullptr, st);
     T* u = (T*)w.u;
     // objective and gradient at u_0
-    CK(op_forward(w, w.pk_u, w.U, w.Jp, nullptr, st));
+    CK(op_objective(w, w.u, w.pk_u, w.U, w.Jp, nullptr, st));
     sub_dot<T>((const T*)w.Jp, (const T*)w.yb, (T*)w.r, M, w.dpart[0], nullptr, st);
     finish_sum(w.dpart[0], &L->rtrt, nullptr, st);
     reg_value<T>(u, n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st, (const T*)p.geo_mask, p.geo_alpha_lambda, 0.0);
@@ -828,7 +934,7 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
         CK(op_jvp(w, w.pk_u, w.pk_p, w.Jp, nullptr, st));
         dot<T>((const T*)w.Jp, (const T*)w.Jp, M, w.dpart[2], nullptr, st);
         finish_sum(w.dpart[2], &L->JsJs, nullptr, st);
-        CK(op_forward(w, w.pk_ut, w.Ut, w.rt, nullptr, st));
+        CK(op_objective(w, w.ut, w.pk_ut, w.Ut, w.rt, nullptr, st));
         sub_dot<T>((const T*)w.rt, (const T*)w.yb, (T*)w.rt, M, w.dpart[3], nullptr, st);
         finish_sum(w.dpart[3], &L->rtrt, nullptr, st);
         const T* ut = (const T*)w.ut;
@@ -840,8 +946,9 @@ pget_status lm_body(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
         const int* acc = &L->accept;
         copy_if<T>((T*)w.u, ut, 2 * nn, acc, st);
         copy_if<T>((T*)w.r, (const T*)w.rt, M, acc, st);
-        copy_if<T>((T*)w.U, (const T*)w.Ut, w.nslots, acc, st);
-        if (w.f64) {
+        if (w.wf64) copy_if<double>((double*)w.U, (const double*)w.Ut, w.nslots, acc, st);
+        else copy_if<float>((float*)w.U, (const float*)w.Ut, w.nslots, acc, st);
+        if (w.wf64) {
             copy_if<double2>((double2*)w.pk_u[0], (const double2*)w.pk_ut[0], w.img_elems, acc, st);
             copy_if<double2>((double2*)w.pk_u[1], (const double2*)w.pk_ut[1], w.img_elems, acc, st);
         } else {
@@ -883,9 +990,10 @@ pget_status lm_launch(Workspace& w, const pget_lm_params& p, cudaStream_t st) {
             }
             w.graph_events.clear();
             if (!w.cap_stream) CK(cudaStreamCreateWithFlags(&w.cap_stream, cudaStreamNonBlocking));
-            CK(prepare_walk(kFwd, w.prec, w.pf));
-            CK(prepare_walk(kJvp, w.prec, w.pj));
-            CK(prepare_walk(kVjp, w.prec, w.pv));
+            CK(prepare_walk(kFwd, w.wprec, w.pf));
+            CK(prepare_walk(kJvp, w.wprec, w.pj));
+            CK(prepare_walk(kVjp, w.wprec, w.pv));
+            if (w.obj64) CK(prepare_walk(kFwd, PGET_F64, w.pf64));
             const long long l0 = launch_count();
             CK(cudaStreamBeginCapture(w.cap_stream, cudaStreamCaptureModeThreadLocal));
             w.prof->capturing = true;
@@ -1045,6 +1153,136 @@ static pget_status vjp_impl(Workspace& w, const void* lam, const void* mu, const
     return PGET_OK;
 }
 
+// Buffers for chunks of up to B items of workspace w (reallocated when the workspace or
+// the chunk size changes); *cap gets the items per chunk.
+static pget_status get_batch(pget_ctx* ctx, Workspace& w, int B, BatchBufs** out) {
+    const long long s_img = (long long)(2 * w.welt * w.img_elems);
+    const long long s_slot = (long long)(w.welt * w.nslots), s_sino = (long long)(w.welt * w.M);
+    const long long s_part = (long long)(w.welt * (size_t)w.n_groups * 2 * w.nn);
+    int cap = (int)std::max<long long>(1, std::min<long long>(B, (long long)kBatchPartBytes / std::max(1LL, s_part)));
+    BatchBufs* bb = ctx->batch.get();
+    if (bb && bb->key == ctx->ws_key && bb->cap >= cap) {
+        *out = bb;
+        return PGET_OK;
+    }
+    ctx->batch.reset();
+    auto nb = std::make_unique<BatchBufs>();
+    auto alloc = [&](void** p, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        if (e == cudaSuccess) {
+            nb->allocs.push_back(*p);
+            e = cudaMemset(*p, 0, bytes ? bytes : 16);  // zero borders of the packed layouts
+        }
+        return e;
+    };
+    for (int l = 0; l < 2; ++l) {
+        CK(alloc(&nb->pk_u[l], (size_t)s_img * cap));
+        CK(alloc(&nb->pk_p[l], (size_t)s_img * cap));
+    }
+    CK(alloc(&nb->U, (size_t)s_slot * cap));
+    CK(alloc(&nb->sino, (size_t)s_sino * cap));
+    CK(alloc(&nb->gpart, (size_t)s_part * cap));
+    nb->key = ctx->ws_key;
+    nb->cap = cap;
+    nb->s_img = s_img;
+    nb->s_slot = s_slot;
+    nb->s_sino = s_sino;
+    nb->s_part = s_part;
+    ctx->batch = std::move(nb);
+    *out = ctx->batch.get();
+    return PGET_OK;
+}
+
+// the layouts of item k of a chunk
+static void item_layouts(void* const base[2], long long stride, int k, void* out[2]) {
+    out[0] = (char*)base[0] + stride * k;
+    out[1] = (char*)base[1] + stride * k;
+}
+
+// mode kFwd: y = A(lam, mu); kJvp: y = J (dl, dm); kVjp: (gl, gm) = J^T r, for `batch`
+// items stored one after another, in chunks of bb->cap items per walk launch.  Every
+// item's result equals the single-item call's bitwise (same kernels and plans).
+template <typename T>
+static pget_status batch_impl(pget_ctx* ctx, Workspace& w, int mode, int batch, const void* lam, const void* mu,
+                              const void* dl, const void* dm, const void* r, void* y, void* gl, void* gm,
+                              cudaStream_t st) {
+    BatchBufs* bb;
+    pget_status s = get_batch(ctx, w, batch, &bb);
+    if (s != PGET_OK) return s;
+    const size_t nn = w.nn, e = w.elt;
+    for (int i0 = 0; i0 < batch; i0 += bb->cap) {
+        const int b = std::min(bb->cap, batch - i0);
+        for (int k = 0; k < b; ++k) {
+            void* pu[2];
+            item_layouts(bb->pk_u, bb->s_img, k, pu);
+            pack_pair<T>(w, (const char*)lam + e * nn * (i0 + k), (const char*)mu + e * nn * (i0 + k), pu, st);
+            if (mode == kJvp) {
+                void* pp[2];
+                item_layouts(bb->pk_p, bb->s_img, k, pp);
+                pack_pair<T>(w, (const char*)dl + e * nn * (i0 + k), (const char*)dm + e * nn * (i0 + k), pp, st);
+            }
+        }
+        WalkArgs a = base_args(w);
+        a.u_img[0] = bb->pk_u[0];
+        a.u_img[1] = bb->pk_u[1];
+        a.n_items = b;
+        a.s_img = bb->s_img;
+        a.s_sino = bb->s_sino;
+        a.s_slot = bb->s_slot;
+        a.s_part = bb->s_part;
+        cudaError_t ce;
+        if (mode == kJvp) {
+            a.Yc = w.pj.Yc;
+            a.nchunks = w.pj.nchunks;
+            a.p_img[0] = bb->pk_p[0];
+            a.p_img[1] = bb->pk_p[1];
+            a.y_out = (char*)y + e * w.M * i0;
+            w.prof->begin(kPJvp, st);
+            ce = launch_walk(kJvp, w.wprec, w.pj, a, w.n_views, st);
+            w.prof->end(st);
+            CK(ce);
+            continue;
+        }
+        // forward: into y, or (adjoint) into the scratch sinograms with the ray totals
+        a.Yc = w.pf.Yc;
+        a.nchunks = w.pf.nchunks;
+        a.y_out = mode == kFwd ? (char*)y + e * w.M * i0 : bb->sino;
+        a.slot_val = mode == kFwd ? nullptr : bb->U;
+        w.prof->begin(kPFwd, st);
+        ce = launch_walk(kFwd, w.wprec, w.pf, a, w.n_views, st);
+        w.prof->end(st);
+        CK(ce);
+        if (mode == kFwd) continue;
+        a.Yc = w.pv.Yc;
+        a.nchunks = w.pv.nchunks;
+        a.y_out = nullptr;
+        a.slot_val = bb->U;
+        a.r_in = (const char*)r + e * w.M * i0;
+        a.gpart = bb->gpart;
+        a.win = w.d_win;
+        a.group_off = w.d_group_off;
+        a.group_view = w.d_group_view;
+        w.prof->begin(kPVjp, st);
+        ce = launch_walk(kVjp, w.wprec, w.pv, a, w.n_groups, st);
+        w.prof->end(st);
+        CK(ce);
+        for (int k = 0; k < b; ++k) {  // the view sum of every item, as pget_vjp forms it
+            RedArgs<T> ra;
+            ra.out = (T*)w.q;
+            ra.n = w.g.n;
+            w.prof->begin(kPRed, st);
+            reduce_views<T, T>((const T*)((const char*)bb->gpart + bb->s_part * k), w.g.n, w.n_groups, w.n_groups0,
+                               w.groups, (T*)w.part2, ra, false, st);
+            w.prof->end(st);
+            CK(cudaMemcpyAsync((char*)gl + e * nn * (i0 + k), w.q, e * nn, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync((char*)gm + e * nn * (i0 + k), (char*)w.q + e * nn, e * nn, cudaMemcpyDeviceToDevice,
+                               st));
+        }
+    }
+    CK(cudaGetLastError());
+    return PGET_OK;
+}
+
 template <typename T>
 static pget_status cg_impl(Workspace& w, const pget_lm_params& p, const void* lam, const void* mu, double nu,
                            const void* rhs, void* x, int32_t* iters, cudaStream_t st) {
@@ -1089,7 +1327,7 @@ template <typename T>
 static pget_status objective_at(Workspace& w, const pget_lm_params& p, void* const pk[2], const void* uvec,
                                 void* U, void* r, double* f, cudaStream_t st) {
     const T* u = (const T*)uvec;
-    CK(op_forward(w, pk, U, w.Jp, nullptr, st));
+    CK(op_objective(w, uvec, pk, U, w.Jp, nullptr, st));
     sub_dot<T>((const T*)w.Jp, (const T*)w.yb, (T*)r, w.M, w.dpart[0], nullptr, st);
     reg_value<T>(u, w.g.n, p.alpha_lambda, p.tv_eps, w.dpart[1], nullptr, st, (const T*)p.geo_mask, p.geo_alpha_lambda, 0.0);
     reg_value<T>(u + w.nn, w.g.n, p.alpha_mu, p.tv_eps, w.dpart[2], nullptr, st, (const T*)p.geo_mask, p.geo_alpha_mu, p.geo_mu_water);
@@ -1392,6 +1630,7 @@ pget_status pget_destroy(pget_ctx* ctx) {
             cudaDeviceSynchronize();
             ctx->slots.clear();
             ctx->pool.clear();
+            ctx->batch.reset();
             ctx->ws.reset();
             if (ctx->scratch) cudaFree(ctx->scratch);
         }
@@ -1457,6 +1696,50 @@ pget_status pget_vjp(pget_ctx* ctx, const pget_geometry* g, int32_t prec, const 
     });
 }
 
+// the batched operators: one workspace, chunks of items per walk launch
+static pget_status batch_call(pget_ctx* ctx, const pget_geometry* g, int32_t prec, int32_t batch, int mode,
+                              const void* lam, const void* mu, const void* dl, const void* dm, const void* r, void* y,
+                              void* gl, void* gm, void* stream) {
+    if (!ctx || !lam || !mu) return fail(PGET_EINVAL, "null argument");
+    if (batch < 0) return fail(PGET_EINVAL, "batch must be >= 0");
+    if (prec == PGET_MIXED) return fail(PGET_EINVAL, "batched operators take PGET_F64, PGET_F32 or PGET_F32_KAHAN");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    Workspace* w;
+    pget_status s = get_workspace(ctx, g, prec, &w);
+    if (s != PGET_OK || batch == 0) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    return w->f64 ? batch_impl<double>(ctx, *w, mode, batch, lam, mu, dl, dm, r, y, gl, gm, st)
+                  : batch_impl<float>(ctx, *w, mode, batch, lam, mu, dl, dm, r, y, gl, gm, st);
+}
+
+pget_status pget_forward_batch(pget_ctx* ctx, const pget_geometry* g, int32_t prec, int32_t batch, const void* lam,
+                               const void* mu, void* y, void* stream) {
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_forward_batch");
+        if (!y) return fail(PGET_EINVAL, "null argument");
+        return batch_call(ctx, g, prec, batch, kFwd, lam, mu, nullptr, nullptr, nullptr, y, nullptr, nullptr, stream);
+    });
+}
+
+pget_status pget_jvp_batch(pget_ctx* ctx, const pget_geometry* g, int32_t prec, int32_t batch, const void* lam,
+                           const void* mu, const void* dlam, const void* dmu, void* dy, void* stream) {
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_jvp_batch");
+        if (!dlam || !dmu || !dy) return fail(PGET_EINVAL, "null argument");
+        return batch_call(ctx, g, prec, batch, kJvp, lam, mu, dlam, dmu, nullptr, dy, nullptr, nullptr, stream);
+    });
+}
+
+pget_status pget_vjp_batch(pget_ctx* ctx, const pget_geometry* g, int32_t prec, int32_t batch, const void* lam,
+                           const void* mu, const void* r, void* glam, void* gmu, void* stream) {
+    return guarded([&]() -> pget_status {
+        PGET_RANGE("pget_vjp_batch");
+        if (!r || !glam || !gmu) return fail(PGET_EINVAL, "null argument");
+        return batch_call(ctx, g, prec, batch, kVjp, lam, mu, nullptr, nullptr, r, nullptr, glam, gmu, stream);
+    });
+}
+
 pget_status pget_operator_status(pget_ctx* ctx, void* stream) {
     return guarded([&]() -> pget_status {
         if (!ctx) return fail(PGET_EINVAL, "null ctx");
@@ -1478,11 +1761,11 @@ pget_status pget_reg_apply(pget_ctx* ctx, int32_t n, int32_t prec, double alpha,
         PGET_RANGE("pget_reg_apply");
         if (!ctx || !u || !v || !out) return fail(PGET_EINVAL, "null argument");
         if (n < 2) return fail(PGET_EINVAL, "n must be >= 2");
-        if (prec != PGET_F64 && prec != PGET_F32 && prec != PGET_F32_KAHAN) return fail(PGET_EINVAL, "unknown precision");
+        if (!known_precision(prec)) return fail(PGET_EINVAL, "unknown precision");
         std::lock_guard<std::mutex> lk(ctx->mu);
         DeviceGuard dg(ctx->device);
         cudaStream_t st = (cudaStream_t)stream;
-        const size_t elt = prec == PGET_F64 ? 8 : 4;
+        const size_t elt = vectors_f64(prec) ? 8 : 4;
         const size_t need = elt * (size_t)n * n + sizeof(double) * (kRedBlocks + 1);
         if (ctx->scratch_bytes < need) {
             CK(cudaStreamSynchronize(st));
@@ -1494,7 +1777,7 @@ pget_status pget_reg_apply(pget_ctx* ctx, int32_t n, int32_t prec, double alpha,
         }
         double* part = (double*)ctx->scratch;
         void* W = (char*)ctx->scratch + sizeof(double) * (kRedBlocks + 1);
-        if (prec == PGET_F64) {
+        if (vectors_f64(prec)) {
             reg_weights<double>((const double*)u, n, eps, (double*)W, nullptr, st);
             reg_apply<double>((const double*)v, (const double*)W, n, alpha, (double*)out, st);
             if (value_host) reg_value<double>((const double*)u, n, alpha, eps, part, nullptr, st);
@@ -1655,7 +1938,7 @@ pget_status pget_project(pget_ctx* ctx, const pget_lm_params* p, int32_t n, void
         DeviceGuard dg(ctx->device);
         cudaStream_t st = (cudaStream_t)stream;
         const size_t nn = (size_t)n * n;
-        if (p->precision == PGET_F64) project_pair<double>((double*)lam, (double*)mu, nn, feas_of(*p), st);
+        if (vectors_f64(p->precision)) project_pair<double>((double*)lam, (double*)mu, nn, feas_of(*p), st);
         else project_pair<float>((float*)lam, (float*)mu, nn, feas_of(*p), st);
         CK(cudaGetLastError());
         return PGET_OK;

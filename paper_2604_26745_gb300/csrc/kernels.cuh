@@ -155,6 +155,12 @@ struct WalkArgs {
     int tx_extra;              // test aid: bytes added to the first chunk's expected copy
                                // size, so that its wait runs out (0 in normal use)
     int* err;                  // error flags (bit 1: adjoint stencil bound, bit 2: chunk copy wait timed out)
+    // batched launches (grid.y = n_items independent items of one geometry): byte strides
+    // between the items' packed layouts (u_img and p_img), sinograms (y_out and r_in), ray
+    // totals (slot_val) and adjoint partial images (gpart); n_items 0 or 1 and strides 0
+    // for one item
+    int n_items;
+    long long s_img, s_sino, s_slot, s_part;
 };
 
 struct WalkPlan {

@@ -254,8 +254,8 @@ static pget_status forward_noalloc(const pget_geometry* gin, int32_t precision, 
     void* img0 = D + o_img0;
     void* img1 = D + o_img1;
     const double kappa = h * 1.4426950408889634;  // h log2(e): attenuation in powers of 2
-    if (f64) pack<double>((const double*)lam, (const double*)mu, n, P, kappa, img0, img1, nullptr, st);
-    else pack<float>((const float*)lam, (const float*)mu, n, P, kappa, img0, img1, nullptr, st);
+    if (f64) pack<double, double>((const double*)lam, (const double*)mu, n, P, kappa, img0, img1, nullptr, st);
+    else pack<float, float>((const float*)lam, (const float*)mu, n, P, kappa, img0, img1, nullptr, st);
     Geometry gplan;  // scalar fields only (its containers stay empty)
     gplan.n = n;
     gplan.max_slots = max_slots;

@@ -18,18 +18,18 @@ namespace pget {
 // ([ix+1][iy+1]); the one-pixel border stays zero (bilinear samples see zero outside).
 // The second component is stored as mu * mu_scale (the ray kernels take h log2(e), so
 // the attenuation sum is directly the exponent of 2).
-template <typename T>
-__global__ void pack_kernel(const T* __restrict__ lam, const T* __restrict__ mu, int n, int P, T mu_scale,
-                            typename Vec2<T>::type* __restrict__ out_n,
-                            typename Vec2<T>::type* __restrict__ out_t, const int* skip) {
-    using T2 = typename Vec2<T>::type;
+template <typename TV, typename TW>
+__global__ void pack_kernel(const TV* __restrict__ lam, const TV* __restrict__ mu, int n, int P, TV mu_scale,
+                            typename Vec2<TW>::type* __restrict__ out_n,
+                            typename Vec2<TW>::type* __restrict__ out_t, const int* skip) {
+    using T2 = typename Vec2<TW>::type;
     if (skip && *skip) return;
     __shared__ T2 tile[32][33];
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         int iy = by + k, ix = bx + threadIdx.x;
         if (iy < n && ix < n) {
-            T2 v = mk2(lam[(size_t)iy * n + ix], mu_scale * mu[(size_t)iy * n + ix]);
+            T2 v = mk2((TW)lam[(size_t)iy * n + ix], (TW)(mu_scale * mu[(size_t)iy * n + ix]));
             out_n[(size_t)(iy + 1) * P + ix + 1] = v;
             tile[k][threadIdx.x] = v;
         }
@@ -41,16 +41,34 @@ __global__ void pack_kernel(const T* __restrict__ lam, const T* __restrict__ mu,
     }
 }
 
-template <typename T>
-void pack(const T* lam, const T* mu, int n, int P, double mu_scale, void* out_n, void* out_t, const int* skip,
+template <typename TV, typename TW>
+void pack(const TV* lam, const TV* mu, int n, int P, double mu_scale, void* out_n, void* out_t, const int* skip,
           cudaStream_t st) {
     dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-    pack_kernel<T><<<grid, block, 0, st>>>(lam, mu, n, P, (T)mu_scale, (typename Vec2<T>::type*)out_n,
-                                           (typename Vec2<T>::type*)out_t, skip);
+    pack_kernel<TV, TW><<<grid, block, 0, st>>>(lam, mu, n, P, (TV)mu_scale, (typename Vec2<TW>::type*)out_n,
+                                                (typename Vec2<TW>::type*)out_t, skip);
     note_launch();
 }
-template void pack<float>(const float*, const float*, int, int, double, void*, void*, const int*, cudaStream_t);
-template void pack<double>(const double*, const double*, int, int, double, void*, void*, const int*, cudaStream_t);
+template void pack<float, float>(const float*, const float*, int, int, double, void*, void*, const int*, cudaStream_t);
+template void pack<double, double>(const double*, const double*, int, int, double, void*, void*, const int*,
+                                   cudaStream_t);
+template void pack<double, float>(const double*, const double*, int, int, double, void*, void*, const int*,
+                                  cudaStream_t);
+
+// dst = src element by element (sinograms between the solver's and the ray kernels' types)
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ src, B* __restrict__ dst, size_t m, const int* skip) {
+    if (skip && *skip) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (B)src[i];
+}
+template <typename A, typename B>
+void convert(const A* src, B* dst, size_t m, const int* skip, cudaStream_t st) {
+    convert_kernel<A, B><<<kRedBlocks, 256, 0, st>>>(src, dst, m, skip);
+    note_launch();
+}
+template void convert<float, double>(const float*, double*, size_t, const int*, cudaStream_t);
+template void convert<double, float>(const double*, float*, size_t, const int*, cudaStream_t);
 
 // ------------------------------------------------------------------------ prior
 // forward differences with a zero-flux border; W = 1/sqrt(|grad u|^2 + eps^2) or 1
@@ -333,8 +351,8 @@ __global__ void __launch_bounds__(256, KAHAN ? 3 : 4)
 
 // Stage 2: out = sum over groups (+ alpha grad^T W grad v + nu v when v given);
 // per-block partial of <dotv, out> when dotv given.
-template <typename T, bool KAHAN>
-__global__ void reduce_groups_kernel(RedArgs<T> a) {
+template <typename T, typename TP, bool KAHAN>
+__global__ void reduce_groups_kernel(RedArgs<T> a, const TP* __restrict__ in2) {
     if (a.skip && *a.skip) return;
     const size_t nn = (size_t)a.n * a.n;
     double acc = 0.0;
@@ -344,7 +362,7 @@ __global__ void reduce_groups_kernel(RedArgs<T> a) {
         const size_t i = e - f * nn;
         Acc<T, KAHAN> s;
         s.init();
-        for (int g = 0; g < a.groups; ++g) s.add(a.in2[(size_t)g * 2 * nn + e]);
+        for (int g = 0; g < a.groups; ++g) s.add((T)in2[(size_t)g * 2 * nn + e]);
         T val = s.val();
         if (a.v) {
             const int iy = (int)(i / a.n), ix = (int)(i - (size_t)iy * a.n);
@@ -366,8 +384,8 @@ __global__ void reduce_groups_kernel(RedArgs<T> a) {
     }
 }
 
-template <typename T>
-void reduce_views(const T* gpart, int n, int n_views, int n0, int groups, T* part2, const RedArgs<T>& ra,
+template <typename T, typename TP>
+void reduce_views(const TP* gpart, int n, int n_views, int n0, int groups, TP* part2, const RedArgs<T>& ra,
                   bool kahan, cudaStream_t st) {
     const int tiles_x = (n + 31) / 32;
     // groups per orientation in proportion to its views, at least one for each present
@@ -376,7 +394,7 @@ void reduce_views(const T* gpart, int n, int n_views, int n0, int groups, T* par
     dim3 block(32, 8);
     const int grid = tiles_x * tiles_x * groups;
     bool vec4 = false;
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<TP, float>::value) {
         vec4 = n % 4 == 0;  // then partial images and their rows start on 16-byte boundaries
         if (vec4 && kahan)
             reduce_views4_kernel<true><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
@@ -384,20 +402,23 @@ void reduce_views(const T* gpart, int n, int n_views, int n0, int groups, T* par
             reduce_views4_kernel<false><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
     }
     if (!vec4 && kahan)
-        reduce_views_kernel<T, true><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
+        reduce_views_kernel<TP, true><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
     else if (!vec4)
-        reduce_views_kernel<T, false><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
+        reduce_views_kernel<TP, false><<<grid, block, 0, st>>>(gpart, n, n_views, n0, groups, g0, part2, ra.skip);
     RedArgs<T> r2 = ra;
-    r2.in2 = part2;
     r2.groups = groups;
     if (kahan)
-        reduce_groups_kernel<T, true><<<kRedBlocks, 256, 0, st>>>(r2);
+        reduce_groups_kernel<T, TP, true><<<kRedBlocks, 256, 0, st>>>(r2, part2);
     else
-        reduce_groups_kernel<T, false><<<kRedBlocks, 256, 0, st>>>(r2);
+        reduce_groups_kernel<T, TP, false><<<kRedBlocks, 256, 0, st>>>(r2, part2);
     note_launch(2);
 }
-template void reduce_views<float>(const float*, int, int, int, int, float*, const RedArgs<float>&, bool, cudaStream_t);
-template void reduce_views<double>(const double*, int, int, int, int, double*, const RedArgs<double>&, bool, cudaStream_t);
+template void reduce_views<float, float>(const float*, int, int, int, int, float*, const RedArgs<float>&, bool,
+                                         cudaStream_t);
+template void reduce_views<double, double>(const double*, int, int, int, int, double*, const RedArgs<double>&, bool,
+                                           cudaStream_t);
+template void reduce_views<double, float>(const float*, int, int, int, int, float*, const RedArgs<double>&, bool,
+                                          cudaStream_t);
 
 // ------------------------------------------------------------------ elementwise
 template <typename T>
@@ -569,11 +590,11 @@ __global__ void cg_step_kernel(T* __restrict__ x, T* __restrict__ res, const T* 
 // (p untouched) when sqrt(s) <= tol |b| or s is not finite; otherwise
 // p = res + (s / rr_prev) p on the block's 32 x 32 tile of both fields, written planar and
 // in the two padded layouts of pack_kernel.  Block 0 records iters, rr and beta.
-template <typename T>
+template <typename T, typename TW>
 __global__ void cg_dir_pack_kernel(T* __restrict__ p, const T* __restrict__ res, const double* __restrict__ part_rr,
-                                   CgState* cg, int n, int P, T mu_scale, typename Vec2<T>::type* __restrict__ out_n,
-                                   typename Vec2<T>::type* __restrict__ out_t) {
-    using T2 = typename Vec2<T>::type;
+                                   CgState* cg, int n, int P, T mu_scale, typename Vec2<TW>::type* __restrict__ out_n,
+                                   typename Vec2<TW>::type* __restrict__ out_t) {
+    using T2 = typename Vec2<TW>::type;
     if (block_stopped(cg)) return;
     const double s = block_partials(part_rr);
     const double rp = cg->rr_prev;
@@ -599,7 +620,7 @@ __global__ void cg_dir_pack_kernel(T* __restrict__ p, const T* __restrict__ res,
             const T pm = res[nn + i] + be * p[nn + i];
             p[i] = pl;
             p[nn + i] = pm;
-            const T2 v = mk2(pl, mu_scale * pm);
+            const T2 v = mk2((TW)pl, (TW)(mu_scale * pm));
             out_n[(size_t)(iy + 1) * P + ix + 1] = v;
             tile[k][threadIdx.x] = v;
         }
@@ -617,22 +638,24 @@ void cg_step(T* x, T* res, const T* p, const T* q, size_t m, const double* part_
     cg_step_kernel<T><<<kRedBlocks, 256, 0, st>>>(x, res, p, q, m, part_pq, part_rr, cg);
     note_launch();
 }
-template <typename T>
+template <typename T, typename TW>
 void cg_dir_pack(T* p, const T* res, const double* part_rr, CgState* cg, int n, int P, double mu_scale, void* out_n,
                  void* out_t, cudaStream_t st) {
     dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-    cg_dir_pack_kernel<T><<<grid, block, 0, st>>>(p, res, part_rr, cg, n, P, (T)mu_scale,
-                                                  (typename Vec2<T>::type*)out_n, (typename Vec2<T>::type*)out_t);
+    cg_dir_pack_kernel<T, TW><<<grid, block, 0, st>>>(p, res, part_rr, cg, n, P, (T)mu_scale,
+                                                      (typename Vec2<TW>::type*)out_n, (typename Vec2<TW>::type*)out_t);
     note_launch();
 }
 template void cg_step<float>(float*, float*, const float*, const float*, size_t, const double*, double*, CgState*,
                              cudaStream_t);
 template void cg_step<double>(double*, double*, const double*, const double*, size_t, const double*, double*,
                               CgState*, cudaStream_t);
-template void cg_dir_pack<float>(float*, const float*, const double*, CgState*, int, int, double, void*, void*,
-                                 cudaStream_t);
-template void cg_dir_pack<double>(double*, const double*, const double*, CgState*, int, int, double, void*, void*,
-                                  cudaStream_t);
+template void cg_dir_pack<float, float>(float*, const float*, const double*, CgState*, int, int, double, void*,
+                                        void*, cudaStream_t);
+template void cg_dir_pack<double, double>(double*, const double*, const double*, CgState*, int, int, double, void*,
+                                          void*, cudaStream_t);
+template void cg_dir_pack<double, float>(double*, const double*, const double*, CgState*, int, int, double, void*,
+                                         void*, cudaStream_t);
 
 template <typename T>
 void cg_init(const T* b, T* x, T* res, T* p, size_t m, double scale_b, double tol, double* part, CgState* cg,

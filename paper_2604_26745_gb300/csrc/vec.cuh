@@ -48,7 +48,6 @@ struct LmParamsDev {
 };
 
 template <typename T> struct RedArgs {
-    const T* in2 = nullptr;      // set by reduce_views
     int groups = 0;
     int n = 0;
     T* out = nullptr;            // [2][n][n]
@@ -68,9 +67,14 @@ template <typename T> struct RedArgs {
     int geo_offset = 0;
 };
 
-template <typename T>
-void pack(const T* lam, const T* mu, int n, int P, double mu_scale, void* out_n, void* out_t, const int* skip,
+// planar (lambda, mu) of the solver's type TV -> the padded interleaved layouts of the ray
+// kernels' type TW
+template <typename TV, typename TW>
+void pack(const TV* lam, const TV* mu, int n, int P, double mu_scale, void* out_n, void* out_t, const int* skip,
           cudaStream_t st);
+// dst[i] = src[i] (sinograms between the solver's and the ray kernels' types)
+template <typename A, typename B>
+void convert(const A* src, B* dst, size_t m, const int* skip, cudaStream_t st);
 template <typename T>
 void reg_weights(const T* u, int n, double eps, T* W, const int* skip, cudaStream_t st);
 template <typename T>
@@ -82,8 +86,10 @@ void reg_value(const T* u, int n, double alpha, double eps, double* part, const 
 template <typename T>
 void dot(const T* a, const T* b, size_t m, double* part, const int* skip, cudaStream_t st);
 void finish_sum(const double* part, double* dst, const int* skip, cudaStream_t st);
-template <typename T>
-void reduce_views(const T* gpart, int n, int n_views, int n0, int groups, T* part2, const RedArgs<T>& ra,
+// adjoint view reduction: partial images of the ray kernels' type TP, result and the fused
+// prior / damping / dot of the solver's type T
+template <typename T, typename TP>
+void reduce_views(const TP* gpart, int n, int n_views, int n0, int groups, TP* part2, const RedArgs<T>& ra,
                   bool kahan, cudaStream_t st);
 template <typename T>
 void sub_dot(const T* a, const T* b, T* out, size_t m, double* part, const int* skip, cudaStream_t st);
@@ -102,7 +108,7 @@ void cg_init(const T* b, T* x, T* res, T* p, size_t m, double scale_b, double to
 template <typename T>
 void cg_step(T* x, T* res, const T* p, const T* q, size_t m, const double* part_pq, double* part_rr, CgState* cg,
              cudaStream_t st);
-template <typename T>
+template <typename T, typename TW>
 void cg_dir_pack(T* p, const T* res, const double* part_rr, CgState* cg, int n, int P, double mu_scale, void* out_n,
                  void* out_t, cudaStream_t st);
 template <typename T>

@@ -147,6 +147,17 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char sm[];
     if (A.stop && *A.stop) return;
+    // batched launches: item blockIdx.y of a batch of independent images (same geometry),
+    // its arrays at the item strides (bytes); 0 strides for a single item
+    const long long item = blockIdx.y;
+    const unsigned char* const u_img0 = (const unsigned char*)A.u_img[0] + item * A.s_img;
+    const unsigned char* const u_img1 = (const unsigned char*)A.u_img[1] + item * A.s_img;
+    const unsigned char* const p_img0 = (const unsigned char*)A.p_img[0] + item * A.s_img;
+    const unsigned char* const p_img1 = (const unsigned char*)A.p_img[1] + item * A.s_img;
+    unsigned char* const y_out = (unsigned char*)A.y_out + item * A.s_sino;
+    const unsigned char* const r_in = (const unsigned char*)A.r_in + item * A.s_sino;
+    unsigned char* const slot_val = A.slot_val ? (unsigned char*)A.slot_val + item * A.s_slot : nullptr;
+    unsigned char* const gpart = (unsigned char*)A.gpart + item * A.s_part;
     const int n = A.n, P = A.P, Ps = A.Ps, Yc = A.Yc, tid = threadIdx.x;
     const int nth = A.nst;  // stencil plane stride (>= blockDim.x)
     const T h = (T)A.h;
@@ -201,8 +212,8 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
     const ViewDev vp = A.views[v];
     const int ns = vp.n_slots;
     const bool active = tid < ns;
-    const T2* ug = (const T2*)A.u_img[vp.transposed];
-    const T2* pg = (MODE == kJvp) ? (const T2*)A.p_img[vp.transposed] : nullptr;
+    const T2* ug = (const T2*)(vp.transposed ? u_img1 : u_img0);
+    const T2* pg = (MODE == kJvp) ? (const T2*)(vp.transposed ? p_img1 : p_img0) : nullptr;
 
     const int2 jr = active ? A.clip[(size_t)v * A.max_slots + tid] : make_int2(0, -1);
     const int jlo = jr.x;
@@ -221,12 +232,12 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
         if (active) {
             const int q0 = A.src_off[vp.bank * A.max_slots + tid];
             const int q1 = A.src_off[vp.bank * A.max_slots + tid + 1];
-            const T* r = (const T*)A.r_in + (size_t)vp.angle * A.n_det;
+            const T* r = (const T*)r_in + (size_t)vp.angle * A.n_det;
             const T* sw = (const T*)A.src_w;
             T acc = T(0);
             for (int e = q0; e < q1; ++e) acc += sw[e] * r[A.src_det[e]];
             rho = acc;
-            Utot = ((const T*)A.slot_val)[(size_t)v * A.max_slots + tid];
+            Utot = ((const T*)slot_val)[(size_t)v * A.max_slots + tid];
         }
     }
     // stencil origin offset: walking down, X moves by -dXs per step; the first sample
@@ -389,7 +400,7 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
             const int r0 = max(row_lo, 0), r1 = min(row_hi + 1, n - 1);
             T2* carry_rd = (ck & 1) ? carry0 : carry1;
             T2* carry_wr = (ck & 1) ? carry1 : carry0;
-            T* gp = (T*)A.gpart + (size_t)g * 2 * n * n;
+            T* gp = (T*)gpart + (size_t)g * 2 * n * n;
             // every thread gathers two neighbouring pixels (Xa, Xa + 1) of a row: their
             // candidate rays overlap, so one pass over the union loads each ray's stencil
             // origin once; a ray outside one pixel's own window holds zeros at that pixel,
@@ -444,10 +455,10 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
         if (active) {
             sval[tid] = val;
             // the adjoint's ray total: with depth factors the c-weighted one
-            if (MODE == kFwd && A.slot_val) ((T*)A.slot_val)[(size_t)v * A.max_slots + tid] = DEPTH ? qc.val() : val;
+            if (MODE == kFwd && slot_val) ((T*)slot_val)[(size_t)v * A.max_slots + tid] = DEPTH ? qc.val() : val;
         }
         __syncthreads();
-        T* y = (T*)A.y_out + (size_t)vp.angle * A.n_det + (size_t)vp.bank * A.nb;
+        T* y = (T*)y_out + (size_t)vp.angle * A.n_det + (size_t)vp.bank * A.nb;
         const T* wk = (const T*)A.w;
         for (int d = tid; d < A.nb; d += blockDim.x) {
             const int* ds = A.det_slot + (size_t)(vp.bank * A.nb + d) * A.n_sub;
@@ -677,7 +688,7 @@ static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_view
     WalkArgs a = a0;
     a.Ps = pl.Ps;
     a.nst = pl.nst;
-    kern<<<n_views, pl.threads, pl.smem, st>>>(a);
+    kern<<<dim3((unsigned)n_views, (unsigned)std::max(1, a.n_items)), pl.threads, pl.smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }

@@ -13,10 +13,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpget.so")
 
 PGET_OK, PGET_EINVAL, PGET_ENOMEM, PGET_EAGAIN, PGET_ECUDA, PGET_ETIMEOUT, PGET_ENUMERIC, PGET_ENOTFOUND, PGET_EINTERNAL = range(9)
-PGET_F64, PGET_F32, PGET_F32_KAHAN = 0, 1, 2
+PGET_F64, PGET_F32, PGET_F32_KAHAN, PGET_MIXED = 0, 1, 2, 3
 PGET_TRACE = 256
 
-_DTYPE = {PGET_F64: torch.float64, PGET_F32: torch.float32, PGET_F32_KAHAN: torch.float32}
+_DTYPE = {PGET_F64: torch.float64, PGET_F32: torch.float32, PGET_F32_KAHAN: torch.float32,
+          PGET_MIXED: torch.float64}
 
 
 class PgetError(RuntimeError):
@@ -96,6 +97,9 @@ _SIGS = {
     "pget_jvp": ([_vp, C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "pget_vjp": ([_vp, C.POINTER(pget_geometry), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "pget_operator_status": ([_vp, _vp], C.c_int),
+    "pget_forward_batch": ([_vp, C.POINTER(pget_geometry), C.c_int32, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
+    "pget_jvp_batch": ([_vp, C.POINTER(pget_geometry), C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
+    "pget_vjp_batch": ([_vp, C.POINTER(pget_geometry), C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp], C.c_int),
     "pget_reg_apply": ([_vp, C.c_int32, C.c_int32, C.c_double, C.c_double, _vp, _vp, _vp,
                         C.POINTER(C.c_double), _vp], C.c_int),
     "pget_cg_solve": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
@@ -180,7 +184,7 @@ def _arr(t, precision, numel: int, device, name: str, host: bool = False):
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if precision is not None:
-        want = 8 if precision == PGET_F64 else 4
+        want = 8 if precision in (PGET_F64, PGET_MIXED) else 4
         if not t.is_floating_point() or t.element_size() != want:
             raise ValueError(f"{name} is {t.dtype}; precision {precision} takes "
                              f"{'float64' if want == 8 else 'float32'}")
@@ -319,6 +323,41 @@ def pget_vjp(ctx: Context, g: pget_geometry, precision: int, lam, mu, r, glam=No
                            _arr(mu, precision, nn, d, "mu"), _arr(r, precision, M, d, "r"),
                            _arr(glam, precision, nn, d, "glam"), _arr(gmu, precision, nn, d, "gmu"),
                            _stream(stream)), ctx.h)
+    return glam, gmu
+
+
+def pget_forward_batch(ctx: Context, g: pget_geometry, precision: int, lam, mu, y=None, stream=None):
+    """y[b] = A(lam[b], mu[b]) for lam, mu [B, n, n] in one call (see pget.h)."""
+    B, nn, M, d = lam.shape[0], g.n * g.n, g.n_angles * g.n_det, ctx.device
+    if y is None:
+        y = torch.empty((B, g.n_angles, g.n_det), dtype=lam.dtype, device=lam.device)
+    _check(load().pget_forward_batch(ctx.h, C.byref(g), precision, B, _arr(lam, precision, B * nn, d, "lam"),
+                                     _arr(mu, precision, B * nn, d, "mu"), _arr(y, precision, B * M, d, "y"),
+                                     _stream(stream)), ctx.h)
+    return y
+
+
+def pget_jvp_batch(ctx: Context, g: pget_geometry, precision: int, lam, mu, dlam, dmu, dy=None, stream=None):
+    """dy[b] = J(lam[b], mu[b]) (dlam[b], dmu[b]) for [B, n, n] inputs in one call."""
+    B, nn, M, d = lam.shape[0], g.n * g.n, g.n_angles * g.n_det, ctx.device
+    if dy is None:
+        dy = torch.empty((B, g.n_angles, g.n_det), dtype=lam.dtype, device=lam.device)
+    _check(load().pget_jvp_batch(ctx.h, C.byref(g), precision, B, _arr(lam, precision, B * nn, d, "lam"),
+                                 _arr(mu, precision, B * nn, d, "mu"), _arr(dlam, precision, B * nn, d, "dlam"),
+                                 _arr(dmu, precision, B * nn, d, "dmu"), _arr(dy, precision, B * M, d, "dy"),
+                                 _stream(stream)), ctx.h)
+    return dy
+
+
+def pget_vjp_batch(ctx: Context, g: pget_geometry, precision: int, lam, mu, r, glam=None, gmu=None, stream=None):
+    """(glam[b], gmu[b]) = J(lam[b], mu[b])^T r[b] for [B, n, n] / [B, n_angles, n_det] inputs."""
+    B, nn, M, d = lam.shape[0], g.n * g.n, g.n_angles * g.n_det, ctx.device
+    glam = torch.empty_like(lam) if glam is None else glam
+    gmu = torch.empty_like(mu) if gmu is None else gmu
+    _check(load().pget_vjp_batch(ctx.h, C.byref(g), precision, B, _arr(lam, precision, B * nn, d, "lam"),
+                                 _arr(mu, precision, B * nn, d, "mu"), _arr(r, precision, B * M, d, "r"),
+                                 _arr(glam, precision, B * nn, d, "glam"), _arr(gmu, precision, B * nn, d, "gmu"),
+                                 _stream(stream)), ctx.h)
     return glam, gmu
 
 

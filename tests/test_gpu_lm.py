@@ -190,3 +190,66 @@ def test_graph_replay_matches_direct_launches(ctx, O, P, torch, monkeypatch):
         outs.append((lam.clone(), mu.clone(), rep["f"]))
     for o in outs[1:]:
         assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1]) and o[2] == outs[0][2]
+
+
+def _single128(P, torch):
+    """The oracle-stored single-request case (128^2, 360 x 182 x 5, Poisson 1e5, 20 LM x
+    CG <= 30): data rebuilt bitwise from the stored counts, the oracle's reconstruction and
+    its measured spreads (tests/golden/make_lm_single128.py)."""
+    import json
+    import os
+    base = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "lm_single128")
+    z = np.load(base + ".npz")
+    with open(base + ".json") as fh:
+        meta = json.load(fh)
+    c = meta["case"]
+    y = z["counts"].astype(np.float64) * float(z["ymax"]) / c["counts"]
+    g = P.geometry(c["n"], c["n_angles"], c["n_det"], n_sub=c["n_sub"], collimator=c["collimator"])
+    ref = np.concatenate([z["lam"].ravel(), z["mu"].ravel()])
+    return c, meta, y, g, ref
+
+
+def _solve_c2(ctx, P, torch, g, c, prec, y):
+    p = P.default_params(max_iters=c["max_iters"], cg_max_iters=c["cg_max_iters"], cg_rel_tol=c["cg_rel_tol"],
+                         precision=prec)
+    yd = torch.tensor(y, dtype=P.dtype_of(prec), device="cuda")
+    lam, mu = P.pget_initial_guess(ctx, g, p, yd)
+    rep = P.pget_lm_solve(ctx, g, p, yd, lam, mu)
+    return np.concatenate([lam.double().cpu().numpy().ravel(), mu.double().cpu().numpy().ravel()]), rep
+
+
+def test_lm_single_request_configuration_fp64_vs_oracle(ctx, P, torch):
+    """The benchmark's configuration in full (20 LM iterations, CG <= 30) in FP64 against the
+    oracle's own reconstruction of the same data.  At this configuration rounding alone moves
+    the result: the oracle's variants (other summation orders, relative 1e-14 changes of the
+    data) lie 1.7e-6 to 7.7e-5 from it, and the GPU's own result moves by 1e-4 to 1e-3
+    under relative 1e-14 changes of the data.  The bar: the same accept/reject trace as the
+    oracle, and a distance within twice the larger of the two measured rounding spreads."""
+    c, meta, y, g, ref = _single128(P, torch)
+    u, rep = _solve_c2(ctx, P, torch, g, c, 0, y)
+    assert rep["acc"] == meta["base"]["accepted"], (rep["acc"], meta["base"]["accepted"])
+    own = []
+    for s in (31, 32):  # the oracle's perturbation seeds
+        sign = np.where(np.random.default_rng(s).random(y.shape) < 0.5, -1.0, 1.0)
+        up, rp = _solve_c2(ctx, P, torch, g, c, 0, y * (1.0 + 1e-14 * sign))
+        assert rp["acc"] == rep["acc"]
+        own.append(rel2(up, u))
+    bar = 2.0 * max(meta["spread_max_rel_l2_u"], max(own))
+    d = rel2(u, ref)
+    assert d <= bar, (d, bar, own)
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_lm_single_request_configuration_float_regression(ctx, P, torch, prec):
+    """The same configuration with the float Jacobian products of CG (PGET_F32_KAHAN, and
+    PGET_MIXED with its double objective).  At iteration 2 the model decrease of the
+    projected CG step is a small difference of terms of ~1e5 (+781 in FP64, negative with
+    float products, whose adjoint is the transpose of their JVP only to ~2e-9): the step is
+    rejected and the trajectory departs, ending ~5.7 % from the oracle with a ~5 % higher
+    objective.  This is reported, not a parity claim; the bars guard against regressions:
+    distance <= 0.1, final objective within 10 % of the oracle's."""
+    c, meta, y, g, ref = _single128(P, torch)
+    u, rep = _solve_c2(ctx, P, torch, g, c, prec, y)
+    assert rel2(u, ref) <= 0.1
+    assert rep["f_final"] <= 1.1 * meta["base"]["f_final"]
+    assert rep["acc"][0] == meta["base"]["accepted"][0] == 1

@@ -9,6 +9,8 @@ Tolerances (relative, max-norm over the output unless stated):
                   128^2 geometry
   PGET_F32        sinogram and JVP 2e-6, gradient 5e-6 (uncompensated float sums of ~200
                   terms; measured at most 4.3e-7)
+  PGET_MIXED  the FP32-Kahan bars: the same ray kernels on double inputs rounded
+                  to float, outputs widened to double
 """
 import numpy as np
 import pytest
@@ -17,7 +19,7 @@ from paper_2604_26745_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: (1e-12, 1e-12), 2: (1e-6, 2e-6), 1: (2e-6, 5e-6)}
+TOL = {0: (1e-12, 1e-12), 2: (1e-6, 2e-6), 1: (2e-6, 5e-6), 3: (1e-6, 2e-6)}
 
 
 def rel(a, b):
@@ -45,7 +47,7 @@ def _inputs(n, n_lat, seed):
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
-@pytest.mark.parametrize("prec", [0, 2, 1])
+@pytest.mark.parametrize("prec", [0, 2, 1, 3])
 def test_forward_jvp_vjp_parity(ctx, O, P, torch, case, prec):
     n, na, nd, S, col, nl = CASES[case]
     lam, mu, dl, dm = _inputs(n, nl, 100 + n)
@@ -148,3 +150,40 @@ def test_invalid_geometry_is_einval(ctx, P, torch):
     with pytest.raises(P.PgetError) as e:
         P.pget_forward(ctx, P.geometry(8, 4, 91, n_sub=0), 2, x, x, torch.zeros((4, 91), device="cuda"))
     assert e.value.status == P.PGET_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_batched_operators_equal_single_item_calls(ctx, P, torch, prec):
+    """pget_forward_batch, pget_jvp_batch and pget_vjp_batch: item b of a batch equals the
+    single-item call on item b, bitwise (one walk launch covers all items' views)."""
+    n, na, nd, S, B = 40, 36, 182, 5, 5
+    g = P.geometry(n, na, nd, n_sub=S)
+    dt = P.dtype_of(prec)
+    rs = np.random.default_rng(11)
+    items = [_inputs(n, 4, 300 + b) for b in range(B)]
+    t = lambda k: torch.tensor(np.stack([it[k] for it in items]), dtype=dt, device="cuda")
+    L, M, DL, DM = t(0), t(1), t(2), t(3)
+    R = torch.tensor(rs.standard_normal((B, na, nd)), dtype=dt, device="cuda")
+    y = P.pget_forward_batch(ctx, g, prec, L, M)
+    dy = P.pget_jvp_batch(ctx, g, prec, L, M, DL, DM)
+    gl, gm = P.pget_vjp_batch(ctx, g, prec, L, M, R)
+    for b in range(B):
+        assert torch.equal(y[b], P.pget_forward(ctx, g, prec, L[b], M[b]))
+        assert torch.equal(dy[b], P.pget_jvp(ctx, g, prec, L[b], M[b], DL[b], DM[b]))
+        sl, sm = P.pget_vjp(ctx, g, prec, L[b], M[b], R[b])
+        assert torch.equal(gl[b], sl) and torch.equal(gm[b], sm)
+
+
+def test_batched_adjoint_in_several_chunks(ctx, P, torch):
+    """At 256 x 256 (360 x 182 x 5) a chunk holds about ten items of adjoint partial
+    images: twelve items run as two launches and still equal the single-item calls."""
+    n, na, nd, S, B = 256, 360, 182, 5, 12
+    g = P.geometry(n, na, nd, n_sub=S)
+    ph = [synth.lattice_phantom(n, 17, radius=5.0, seed=1200 + b) for b in range(B)]
+    L = torch.tensor(np.stack([p.lam for p in ph]), dtype=torch.float32, device="cuda")
+    M = torch.tensor(np.stack([p.mu for p in ph]), dtype=torch.float32, device="cuda")
+    R = torch.tensor(np.random.default_rng(3).standard_normal((B, na, nd)), dtype=torch.float32, device="cuda")
+    gl, gm = P.pget_vjp_batch(ctx, g, 2, L, M, R)
+    for b in (0, 9, 10, B - 1):
+        sl, sm = P.pget_vjp(ctx, g, 2, L[b], M[b], R[b])
+        assert torch.equal(gl[b], sl) and torch.equal(gm[b], sm), b
