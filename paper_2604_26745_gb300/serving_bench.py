@@ -3,7 +3,7 @@ continuous-admission path (pget_submit / pget_poll), against the same requests s
 at a time through the single-request path (pget_initial_guess + pget_lm_solve).
 
   python -m paper_2604_26745_gb300.serving_bench [--requests 64] [--rate 50] [--seed 4242]
-         [--iters 15] [--cg 30] [--inflight 8] [--saturate]
+         [--iters 15] [--cg 30] [--inflight 8] [--saturate] [--rates 50,3]
 
 Requests follow the mixed serving workload: exponential inter-arrival gaps at the given
 rate; per request N in {96, 128, 192, 256}, lattice in {9, 10, 17}, angles in {180, 360},
@@ -12,8 +12,10 @@ FP64 scalars.  Data are generated before timing (GPU FP64 forward + Poisson nois
 
 Both arms are timed warm (workspaces and captured graphs exist, as in a long-running
 server): the single-request arm solves every request once untimed, then once timed; the
-serving arm replays the whole stream once untimed, then once timed.  Prints one JSON
-line: serving recon/s (requests / time from the first arrival to the last completion),
+serving arm replays the whole stream once untimed, then once timed.  --rates serves the same
+requests at each listed arrival rate in turn (the seeded stream draws the same sizes at
+every rate; only the gaps scale), against one single-request arm.  Prints one JSON
+line per rate: serving recon/s (requests / time from the first arrival to the last completion),
 single-request recon/s (requests / sum of the per-request solve times), p50/p99 latency
 (completion - arrival), and the largest relative L2 difference between a serving result
 and the same request solved alone.
@@ -41,6 +43,7 @@ def _args():
     ap.add_argument("--cg", type=int, default=30)
     ap.add_argument("--inflight", type=int, default=8)
     ap.add_argument("--saturate", action="store_true", help="all requests arrive at t = 0")
+    ap.add_argument("--rates", default="", help="comma-separated arrival rates, one serving run each")
     return ap.parse_args()
 
 
@@ -119,28 +122,33 @@ def main():
     a = _args()
     os.environ["PGET_MAX_INFLIGHT"] = str(a.inflight)
     build.build()
-    stream = synth.serving_stream(a.requests, a.rate, a.seed)
+    rates = [float(x) for x in a.rates.split(",") if x] or [a.rate]
+    stream = synth.serving_stream(a.requests, rates[0], a.seed)
     p = P.default_params(max_iters=a.iters, cg_max_iters=a.cg, cg_rel_tol=1e-6, precision=P.PGET_F32_KAHAN)
     with P.Context(0) as ctx:
         reqs = make_requests(ctx, stream)
         times, alone = single_arm(ctx, reqs, p)
-    with P.Context(0) as sctx:
-        span, lat, served = serving_arm(sctx, reqs, p, a.saturate)
-    diff = max(float(torch.linalg.norm(s - r) / torch.linalg.norm(r)) for s, r in zip(served, alone))
-    lat_ms = sorted(x * 1e3 for x in lat)
     single = len(reqs) / sum(times)
-    line = {
-        "metric": "serving recon/s", "value": round(len(reqs) / span, 3), "unit": "recon/s",
-        "single_request_recon_s": round(single, 3), "speedup_vs_single": round(len(reqs) / span / single, 3),
-        "latency_ms": {"p50": round(statistics.median(lat_ms), 1),
-                       "p99": round(lat_ms[min(len(lat_ms) - 1, int(np.ceil(0.99 * len(lat_ms))) - 1)], 1)},
-        "single_request_ms": {"p50": round(statistics.median(times) * 1e3, 1), "max": round(max(times) * 1e3, 1)},
-        "max_rel_l2_diff_vs_alone": diff,
-        "config": {"requests": len(reqs), "rate_hz": None if a.saturate else a.rate, "seed": a.seed,
-                   "lm_iters": a.iters, "cg_max": a.cg, "max_inflight": a.inflight, "precision": "f32-kahan",
-                   "sizes": sorted({rq.n for rq, _, _ in reqs}), "data": "synthetic"},
-    }
-    print(json.dumps(line), flush=True)
+    for rate in rates:
+        st = synth.serving_stream(a.requests, rate, a.seed)  # same sizes and seeds, scaled gaps
+        reqs_r = [(rq, g, y) for (_, g, y), rq in zip(reqs, st)]
+        with P.Context(0) as sctx:
+            span, lat, served = serving_arm(sctx, reqs_r, p, a.saturate)
+        diff = max(float(torch.linalg.norm(s_ - r) / torch.linalg.norm(r)) for s_, r in zip(served, alone))
+        lat_ms = sorted(x * 1e3 for x in lat)
+        line = {
+            "metric": "serving recon/s", "value": round(len(reqs) / span, 3), "unit": "recon/s",
+            "single_request_recon_s": round(single, 3), "speedup_vs_single": round(len(reqs) / span / single, 3),
+            "latency_ms": {"p50": round(statistics.median(lat_ms), 1),
+                           "p99": round(lat_ms[min(len(lat_ms) - 1, int(np.ceil(0.99 * len(lat_ms))) - 1)], 1)},
+            "single_request_ms": {"p50": round(statistics.median(times) * 1e3, 1), "max": round(max(times) * 1e3, 1)},
+            "max_rel_l2_diff_vs_alone": diff,
+            "config": {"requests": len(reqs), "rate_hz": None if a.saturate else rate, "seed": a.seed,
+                       "arrival_span_s": round(max(rq.arrival_s for rq in st), 2),
+                       "lm_iters": a.iters, "cg_max": a.cg, "max_inflight": a.inflight, "precision": "f32-kahan",
+                       "sizes": sorted({rq.n for rq, _, _ in reqs}), "data": "synthetic"},
+        }
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -52,6 +52,60 @@ def test_two_ranks_weak_scaling():
     assert len(ids0) == len(ids1) == 8
 
 
+def _solve_request(k):
+    """A small reconstruction keyed by the request id, as bench.py keys its problems
+    (phantom seed 1100 + k, noise seed 2100 + k), solved by the oracle on the CPU."""
+    from oracle import oracle as O
+    from paper_2604_26745_gb300 import synth
+    g = O.geom(16, 12, 182, n_sub=3)
+    ph = synth.lattice_phantom(16, 3, radius=2.0, seed=1100 + k)
+    y = synth.poisson_noise(O.forward(g, ph.lam, ph.mu), 1e4, 2100 + k)
+    l0, m0 = O.initial_guess(g, y)
+    lam, mu, rep = O.lm(g, O.default_params(max_iters=3, cg_max_iters=5), y, l0, m0)
+    return lam, mu, rep["f_final"]
+
+
+def _worker(rank, world, port, q):
+    import time
+
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ids = bench.rank_request_ids(rank, world, 3)
+    t0 = time.perf_counter()
+    out = {k: _solve_request(k) for k in ids}
+    elapsed = time.perf_counter() - t0
+    t = torch.tensor([elapsed], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    q.put((rank, ids, float(t.item()), {k: (v[0].tobytes(), v[1].tobytes(), v[2]) for k, v in out.items()}))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_reconstruct_their_own_requests():
+    """The data path of the replicas: each rank reconstructs its own request ids with no
+    collective on the data; every result equals the same request solved in one process,
+    bitwise, and together the ranks cover every request once."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][2] == res[1][2]  # the job time: max over ranks
+    ids = res[0][1] + res[1][1]
+    assert sorted(ids) == list(range(6))
+    for _, _, _, out in res:
+        for k, (lb, mb, f) in out.items():
+            lam, mu, f1 = _solve_request(k)
+            assert lb == lam.tobytes() and mb == mu.tobytes() and f == f1
+
+
 def _leaver(rank, world, port, q, how):
     import time
 

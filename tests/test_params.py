@@ -25,7 +25,7 @@ BAD = [
     ("nu_up", 0.5), ("nu_down", 0.0), ("nu_down", 2.0),
     ("eta", NAN), ("rho_lo", 0.9), ("rho_hi", INF),
     ("nu_min", 0.0), ("nu_max", 1e-13), ("nu_min", NAN),
-    ("precision", 3), ("alpha_decay", 0.5), ("alpha_decay_iters", -1),
+    ("precision", 4), ("precision", -1), ("alpha_decay", 0.5), ("alpha_decay_iters", -1),
     ("inner_solver", 2), ("lin_constraint", 2),
 ]
 
@@ -68,7 +68,7 @@ if hyp is not None:
         "lambda_max", "mu_max", "alpha_lambda", "alpha_mu", "tv_eps", "cg_rel_tol", "nu0_scale", "nu_up", "nu_down",
         "eta", "rho_lo", "rho_hi", "nu_min", "nu_max", "alpha_decay")}),
         i=st.fixed_dictionaries({"max_iters": st.integers(-2, 50), "cg_max_iters": st.integers(-2, 50),
-                                 "precision": st.integers(-1, 3), "alpha_decay_iters": st.integers(-2, 5),
+                                 "precision": st.integers(-1, 4), "alpha_decay_iters": st.integers(-2, 5),
                                  "inner_solver": st.integers(-1, 2)}))
     def test_random_parameters_are_refused_or_consistent(f, i):
         p = P.default_params()
@@ -78,7 +78,7 @@ if hyp is not None:
             P.check_params(p)
         except ValueError:
             return
-        assert p.max_iters >= 0 and p.cg_max_iters >= 0 and p.precision in (0, 1, 2) and p.inner_solver in (0, 1)
+        assert p.max_iters >= 0 and p.cg_max_iters >= 0 and p.precision in (0, 1, 2, 3) and p.inner_solver in (0, 1)
         assert p.lambda_max > 0 and p.mu_max > 0 and p.alpha_lambda >= 0 and p.alpha_mu >= 0
         assert math.isfinite(p.tv_eps) and not math.isnan(p.cg_rel_tol)
         assert 0 < p.nu0_scale < INF and p.nu_up >= 1 and 0 < p.nu_down <= 1
