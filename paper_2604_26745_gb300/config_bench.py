@@ -11,9 +11,11 @@ diff256    differentiation: K pairs (lambda, mu) on 256 x 256 (17 x 17 rods r = 
            wrapper (pairs/s, FP32-Kahan and FP64) and the memory the recompute saves.
 stress512  precision stress: K reconstructions on 512 x 512 (17 x 17 rods r = 10, rod
            mu ~ U(0.05, 0.12)), 720 x 182 x 9, Poisson 1e6, 10 LM iterations, CG <= 30,
-           in FP32, FP32-Kahan and FP64: recon/s per precision and, per result, the
-           relative L2 distance of the FP32 and FP32-Kahan sinogram, gradient and final
-           reconstruction from the FP64 GPU path on the same input.
+           box mu <= 0.25, in FP32, FP32-Kahan and FP64: recon/s per precision and, per
+           result, the relative L2 distance of the FP32 and FP32-Kahan sinogram, gradient and
+           final reconstruction from the FP64 GPU path on the same input; for the items the
+           oracle has reconstructed (--oracle, default tests/golden/stress512), the data are
+           the oracle's and every precision's reconstruction is compared with the oracle's.
 
 ops128     the three ray operators alone on the single-request geometry (128 x 128, 360 x
            182 x 5, FP32-Kahan): forward, JVP and adjoint, K launches each after one
@@ -29,6 +31,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import math
 import statistics
 
@@ -158,9 +161,22 @@ def _in_grid_samples(n, na, nd, S) -> int:
     return tot
 
 
-def stress512(k: int) -> dict:
+def _stored_oracle(path: str):
+    """The oracle's stored reconstructions of the first precision-stress items, if present
+    (written by tests/golden/make_stress512.py, which calls only the oracle)."""
+    if not path or not os.path.exists(path + ".npz"):
+        return None
+    z = np.load(path + ".npz")
+    with open(path + ".json") as fh:
+        meta = json.load(fh)
+    return z, meta
+
+
+def stress512(k: int, oracle_path: str = "") -> dict:
     n, na, nd, S = 512, 720, 182, 9
     g = P.geometry(n, na, nd, n_sub=S)
+    stored = _stored_oracle(oracle_path)
+    n_stored = len(stored[1]["items"]) if stored else 0
     precs = (("f32", P.PGET_F32), ("f32_kahan", P.PGET_F32_KAHAN), ("f64", P.PGET_F64))
     res = {name: [] for name, _ in precs}
     ms = {name: [] for name, _ in precs}
@@ -171,7 +187,12 @@ def stress512(k: int) -> dict:
             lam64 = torch.tensor(ph.lam, device="cuda")
             mu64 = torch.tensor(ph.mu, device="cuda")
             yc = P.pget_forward(ctx, g, P.PGET_F64, lam64, mu64)
+            if i < n_stored:  # the oracle's data for this item (its forward model, stored counts)
+                z, meta = stored
+                y_or = z[f"counts{i}"].astype(np.float64) * float(z[f"ymax{i}"]) / meta["case"]["counts"]
             y64 = torch.tensor(synth.poisson_noise(yc.cpu().numpy(), 1e6, 2500 + i), device="cuda")
+            if i < n_stored:
+                y64 = torch.tensor(y_or, device="cuda")
             r64 = (yc - y64).contiguous()
             ops = {}
             for name, prec in precs:
@@ -181,7 +202,7 @@ def stress512(k: int) -> dict:
                 gl, gm = P.pget_vjp(ctx, g, prec, lam, mu, r)
                 ops[name] = (sino, torch.cat([gl.ravel(), gm.ravel()]))
                 p = P.default_params(max_iters=10, cg_max_iters=30, cg_rel_tol=1e-6 if dt == torch.float32 else 1e-10,
-                                     precision=prec)
+                                     mu_max=0.25, precision=prec)
                 y = y64.to(dt)
                 if i == 0:
                     _timed_solve(ctx, g, p, y)  # warm-up per precision
@@ -193,9 +214,17 @@ def stress512(k: int) -> dict:
                 item[name] = {"sinogram": _rel(ops[name][0], ops["f64"][0]),
                               "gradient": _rel(ops[name][1], ops["f64"][1]),
                               "reconstruction": _rel(res[name][-1], res["f64"][-1])}
+            if i < n_stored:  # each GPU reconstruction against the oracle's, same data
+                z, meta = stored
+                u_or = torch.tensor(np.concatenate([z[f"lam{i}"].ravel(), z[f"mu{i}"].ravel()]).astype(np.float64),
+                                    device="cuda")
+                item["vs_oracle"] = {name: _rel(res[name][-1], u_or) for name, _ in precs}
+                item["oracle_rel_err_truth"] = {"lambda": meta["items"][i]["rel_err_truth_lambda"],
+                                                "mu": meta["items"][i]["rel_err_truth_mu"]}
             per.append(item)
     return {"config": "precision stress: 512x512, 17x17 rods r=10, rod mu ~ U(0.05,0.12), 720 x 182 x 9, "
-                      "Poisson 1e6, 10 LM x CG<=30",
+                      "Poisson 1e6, 10 LM x CG<=30, box mu <= 0.25",
+            "oracle_items": n_stored,
             "reconstructions": k,
             "recon_per_s": {name: round(1e3 * len(v) / sum(v), 3) for name, v in ms.items()},
             "rel_l2_vs_f64_gpu": per}
@@ -248,12 +277,18 @@ def main():
     ap.add_argument("--config", required=True, choices=["plain64", "diff256", "stress512", "ops128", "ops512"])
     ap.add_argument("--count", type=int, default=0)
     ap.add_argument("--op", default="all", choices=["all", "forward", "jvp", "vjp"])
+    ap.add_argument("--oracle", default=os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                                     "tests", "golden", "stress512"),
+                    help="stored oracle reconstructions of the first stress512 items (prefix of .npz/.json)")
     a = ap.parse_args()
     build.build()
     if a.config in OPS:
         print(json.dumps(ops(a.count or 20, a.config, a.op)), flush=True)
         return
-    fn, k0 = {"plain64": (plain64, 16), "diff256": (diff256, 32), "stress512": (stress512, 4)}[a.config]
+    if a.config == "stress512":
+        print(json.dumps(stress512(a.count or 4, a.oracle)), flush=True)
+        return
+    fn, k0 = {"plain64": (plain64, 16), "diff256": (diff256, 32)}[a.config]
     print(json.dumps(fn(a.count or k0)), flush=True)
 
 
