@@ -202,6 +202,10 @@ struct Workspace {
     void* d_depth = nullptr;  // [T] (w_j, c_j) depth factors of Eq. (5), element type; null without
     int* d_group_off = nullptr;
     int* d_group_view = nullptr;
+    // launch orders: CTA b of a forward or JVP walk takes view d_view_order[b], CTA b of an
+    // adjoint walk group d_group_order[b], longest rays first (see walk_orders)
+    int* d_view_order = nullptr;
+    int* d_group_order = nullptr;
     void* pk_u[2] = {nullptr, nullptr};
     void* pk_ut[2] = {nullptr, nullptr};
     void* pk_p[2] = {nullptr, nullptr};
@@ -268,6 +272,7 @@ static size_t workspace_bytes(const Geometry& g, int prec, int groups) {
     b += (size_t)groups * 2 * nn * welt;
     b += 4 * kRedBlocks * 8 + sizeof(LmState) + 64;
     b += V * sizeof(ViewDev) + V * 4 + (size_t)g.n_det * g.n_sub * 4 + g.n_sub * 8;
+    b += 4 * (V + 1) * 4;               // view groups and the two launch orders
     b += g.src_off.size() * 4 + g.src_det.size() * 12 + g.clip.size() * 4;
     b += V * (size_t)(g.n + 1) * 8;     // adjoint ray windows (at most n + 1 chunks per view)
     if (g.depth) b += 2 * (size_t)g.T * welt;  // depth factors
@@ -371,6 +376,34 @@ pget_status resolve(const pget_geometry* gin, int prec, Geometry* g, std::string
     return PGET_OK;
 }
 
+// Launch orders of the walks.  A walk CTA's time grows with the length of its view's
+// rays (their samples per image row go as 1/cos of the ray's angle to the canonical
+// axis: up to sqrt(2) times more at 45 degrees), and a launch of more CTAs than fit at
+// once ends with a partial wave.  Launching the longest views first leaves the shortest
+// for that wave (longest-processing-time-first list scheduling); ties keep the view
+// order.  Every view or group still writes its own output, so results do not change.
+void walk_orders(const Geometry& G, const std::vector<int>& goff, const std::vector<int>& gview,
+                 std::vector<int>* vorder, std::vector<int>* gorder) {
+    const int V = (int)G.views.size(), ms = G.max_slots;
+    std::vector<long long> len(V, 0);  // samples of the view's longest ray
+    for (int v = 0; v < V; ++v)
+        for (int i = 0; i < G.views[v].n_slots; ++i) {
+            const long long lo = G.clip[((size_t)v * ms + i) * 2], hi = G.clip[((size_t)v * ms + i) * 2 + 1];
+            len[v] = std::max(len[v], hi - lo + 1);
+        }
+    const int NG = (int)goff.size() - 1;
+    std::vector<long long> glen(NG, 0);
+    for (int g = 0; g < NG; ++g)
+        for (int k = goff[g]; k < goff[g + 1]; ++k) glen[g] += len[gview[k]];
+    auto order = [](const std::vector<long long>& c, std::vector<int>* o) {
+        o->resize(c.size());
+        for (size_t i = 0; i < c.size(); ++i) (*o)[i] = (int)i;
+        std::stable_sort(o->begin(), o->end(), [&](int a, int b) { return c[a] > c[b]; });
+    };
+    order(len, vorder);
+    order(glen, gorder);
+}
+
 size_t serving_bytes(const pget_ctx* ctx);
 bool evict_idle(pget_ctx* ctx);
 
@@ -442,6 +475,8 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     }
     w->n_groups = (int)gtrans.size();
     w->n_groups0 = (int)std::count(gtrans.begin(), gtrans.end(), 0);  // normal-frame groups come first
+    std::vector<int> vorder, gorder;
+    walk_orders(G, goff, gview, &vorder, &gorder);
     const size_t e = w->elt, we = w->welt;  // solver and walk element bytes
     CK(w->alloc(&w->d_views, sizeof(ViewDev) * V));
     CK(cudaMemcpy(w->d_views, G.views.data(), sizeof(ViewDev) * V, cudaMemcpyHostToDevice));
@@ -508,6 +543,10 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     CK(cudaMemcpy(w->d_group_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->d_group_view, sizeof(int) * gview.size()));
     CK(cudaMemcpy(w->d_group_view, gview.data(), sizeof(int) * gview.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_view_order, sizeof(int) * vorder.size()));
+    CK(cudaMemcpy(w->d_view_order, vorder.data(), sizeof(int) * vorder.size(), cudaMemcpyHostToDevice));
+    CK(w->alloc(&w->d_group_order, sizeof(int) * gorder.size()));
+    CK(cudaMemcpy(w->d_group_order, gorder.data(), sizeof(int) * gorder.size(), cudaMemcpyHostToDevice));
     CK(w->alloc(&w->part2, we * (size_t)groups * 2 * w->nn));
     for (int k = 0; k < 4; ++k) CK(w->alloc(&w->dpart[k], sizeof(double) * kRedBlocks));
     CK(w->alloc(&w->lm, sizeof(LmState)));
@@ -577,6 +616,7 @@ WalkArgs base_args(const Workspace& w) {
     a.err = w.err;
     a.tx_extra = w.tx_extra;
     a.wait_ns = w.wait_ns;
+    a.cta_order = w.d_view_order;  // views; the adjoint launches replace it by the group order
     return a;
 }
 
@@ -659,6 +699,7 @@ cudaError_t op_vjp(Workspace& w, void* const pku[2], const void* U, const void* 
     a.win = w.d_win;
     a.group_off = w.d_group_off;
     a.group_view = w.d_group_view;
+    a.cta_order = w.d_group_order;
     a.stop = stop;
     w.prof->begin(kPVjp, st);
     cudaError_t e = launch_walk(kVjp, w.wprec, w.pv, a, w.n_groups, st);
@@ -1262,6 +1303,7 @@ static pget_status batch_impl(pget_ctx* ctx, Workspace& w, int mode, int batch, 
         a.win = w.d_win;
         a.group_off = w.d_group_off;
         a.group_view = w.d_group_view;
+        a.cta_order = w.d_group_order;
         w.prof->begin(kPVjp, st);
         ce = launch_walk(kVjp, w.wprec, w.pv, a, w.n_groups, st);
         w.prof->end(st);

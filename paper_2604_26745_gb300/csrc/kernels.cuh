@@ -148,6 +148,9 @@ struct WalkArgs {
                                //      samples in the chunk; stencil column = slot - first
     const int* group_off;      // VJP: CTA g handles views group_view[group_off[g] .. group_off[g+1])
     const int* group_view;     //      (null: CTA g handles view g)
+    const int* cta_order;      // CTA b takes view (FWD / JVP) or view group (VJP) cta_order[b]:
+                               //      longest rays first, so that the last wave holds the
+                               //      shortest (null: b)
     const void* depth;         // [T] (w_j, c_j) pairs (element type of the path): depth factors
                                //      of Eq. (5); null without tables
     const int* stop;           // optional: skip the launch when *stop != 0

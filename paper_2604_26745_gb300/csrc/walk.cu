@@ -203,7 +203,7 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
 
     // the views of this CTA: one view, or (VJP) a group of views sharing the canonical
     // orientation whose adjoint images are summed into the group's partial image
-    const int g = blockIdx.x;
+    const int g = A.cta_order ? A.cta_order[blockIdx.x] : (int)blockIdx.x;
     const int gb = A.group_off ? A.group_off[g] : g;
     const int ge = A.group_off ? A.group_off[g + 1] : g + 1;
     for (int gi = gb; gi < ge; ++gi) {
