@@ -27,24 +27,29 @@ def sources() -> list:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stale(force: bool) -> bool:
-    if force or not os.path.exists(OUT):
+def _stale(force: bool, out: str = OUT) -> bool:
+    if force or not os.path.exists(out):
         return True
-    t = os.path.getmtime(OUT)
+    t = os.path.getmtime(out)
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "pget.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    if not _stale(force):
-        return OUT
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, out: str = OUT,
+          build_dir: str = BUILD) -> str:
+    """Compile every translation unit and link the library at ``out`` (default: the
+    package's libpget.so).  ``extra`` adds nvcc flags, e.g. ``-DPGET_TUNING`` for a variant
+    that reads the walk plans' tuning variables from the environment; give such a variant
+    its own ``out`` and ``build_dir``."""
+    if not _stale(force, out):
+        return out
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     extra = extra or []
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -57,13 +62,13 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = OUT + f".{os.getpid()}.tmp"
+    tmp = out + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", *objs, "-o", tmp, "-ldl"]  # dlopen: NVTX looks for an attached tool
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

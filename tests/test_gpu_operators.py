@@ -91,39 +91,75 @@ def test_vjp_deterministic(ctx, P, torch):
     assert torch.equal(a1[0], a2[0]) and torch.equal(a1[1], a2[1])
 
 
+# Runs in a child process on a library built with -DPGET_TUNING (the only build that reads
+# the shared-memory budgets of the walk plans from the environment): forward, JVP and
+# adjoint three times each at one budget, saved for the parent to compare.
+_CHUNK_CHILD = r"""
+import sys
+import numpy as np
+import torch
+from paper_2604_26745_gb300 import pget as P, synth
+P.load(sys.argv[1])
+n, na, S = (int(x) for x in sys.argv[3:6])
+ph = synth.lattice_phantom(n, 9, radius=3.0, seed=41)
+g = P.geometry(n, na, 182, n_sub=S)
+t = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
+lam, mu = t(ph.lam), t(ph.mu)
+rs = np.random.default_rng(42)
+dl, dm = t(rs.standard_normal((n, n))), t(0.01 * rs.standard_normal((n, n)))
+r = t(rs.standard_normal((na, 182)))
+out = {}
+with P.Context(0) as c:
+    for k in range(3):
+        gl, gm = P.pget_vjp(c, g, P.PGET_F32_KAHAN, lam, mu, r)
+        y = P.pget_forward(c, g, P.PGET_F32_KAHAN, lam, mu)
+        dy = P.pget_jvp(c, g, P.PGET_F32_KAHAN, lam, mu, dl, dm)
+        for name, v in (("y", y), ("dy", dy), ("gl", gl), ("gm", gm)):
+            out[f"{name}{k}"] = v.cpu().numpy()
+np.savez(sys.argv[2], **out)
+"""
+
+
+@pytest.fixture(scope="module")
+def tuning_lib(tmp_path_factory):
+    from paper_2604_26745_gb300 import build
+    d = tmp_path_factory.mktemp("tuning_build")
+    return build.build(extra=["-DPGET_TUNING"], out=str(d / "libpget_tuning.so"), build_dir=str(d))
+
+
 @pytest.mark.parametrize("geo", [(128, 360, 5), (96, 90, 7)])
-def test_walks_independent_of_chunk_height(P, torch, monkeypatch, geo):
+def test_walks_independent_of_chunk_height(tuning_lib, tmp_path, geo):
     """The chunk height is a tuning choice (shared-memory budget): forward and JVP must be
     bitwise the same at every height (each ray sums in the same order), the adjoint the
     same up to rounding (carried rows split the per-pixel sums differently), and every
     operator bitwise reproducible at a fixed height.  A stencil column written by one
-    thread and cleared by another would break the last two."""
-    n, na, S = geo
-    ph = synth.lattice_phantom(n, 9, radius=3.0, seed=41)
-    g = P.geometry(n, na, 182, n_sub=S)
-    t = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")
-    lam, mu = t(ph.lam), t(ph.mu)
-    rs = np.random.default_rng(42)
-    dl, dm = t(rs.standard_normal((n, n))), t(0.01 * rs.standard_normal((n, n)))
-    r = t(rs.standard_normal((na, 182)))
-    ref = None
+    thread and cleared by another would break the last two.  The budgets reach the plans
+    only in a -DPGET_TUNING build, which the test builds and runs in child processes; an
+    adjoint that stays bitwise equal at every budget means the budget did not take effect,
+    and fails the test."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
     for kb in (72, 40, 100):
-        for k in ("FWD", "JVP", "VJP"):
-            monkeypatch.setenv(f"PGET_SMEM_KB_{k}", str(kb))
-        with P.Context(0) as c:
-            runs = []
-            for _ in range(3):
-                gl, gm = P.pget_vjp(c, g, P.PGET_F32_KAHAN, lam, mu, r)
-                runs.append((P.pget_forward(c, g, P.PGET_F32_KAHAN, lam, mu),
-                             P.pget_jvp(c, g, P.PGET_F32_KAHAN, lam, mu, dl, dm), gl, gm))
-        for rr in runs[1:]:
-            assert all(torch.equal(a, b) for a, b in zip(rr, runs[0])), kb
-        if ref is None:
-            ref = runs[0]
-            continue
-        assert torch.equal(runs[0][0], ref[0]) and torch.equal(runs[0][1], ref[1]), kb
-        for a, b in zip(runs[0][2:], ref[2:]):
-            assert float((a - b).abs().max() / b.abs().max()) <= 1e-6, kb
+        env = dict(os.environ, PGET_SMEM_KB_FWD=str(kb), PGET_SMEM_KB_JVP=str(kb), PGET_SMEM_KB_VJP=str(kb),
+                   PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+        f = tmp_path / f"kb{kb}.npz"
+        subprocess.run([sys.executable, "-c", _CHUNK_CHILD, tuning_lib, str(f), *(str(x) for x in geo)],
+                       env=env, cwd=root, check=True, timeout=600)
+        res[kb] = dict(np.load(f))
+    moved = False
+    for kb, d in res.items():
+        for name in ("y", "dy", "gl", "gm"):
+            assert np.array_equal(d[name + "1"], d[name + "0"]) and np.array_equal(d[name + "2"], d[name + "0"]), \
+                (kb, name)
+        ref = res[72]
+        assert np.array_equal(d["y0"], ref["y0"]) and np.array_equal(d["dy0"], ref["dy0"]), kb
+        for name in ("gl0", "gm0"):
+            assert float(np.abs(d[name] - ref[name]).max() / np.abs(ref[name]).max()) <= 1e-6, (kb, name)
+            moved |= not np.array_equal(d[name], ref[name])
+    assert moved, "the adjoint is bitwise equal at every budget: the chunk height did not change"
 
 
 @pytest.mark.parametrize("prec", [0, 2])
