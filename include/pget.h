@@ -345,6 +345,26 @@ pget_status pget_check_params(const pget_lm_params* p);
 pget_status pget_geometry_info(const pget_geometry* g, int32_t* n_samples, int32_t* n_banks, double* fov_radius,
                                double* det_pitch, int32_t* max_slots);
 
+/* Launch plans of the three ray operators (forward A of Eq. (1), J of Eq. (2) and its
+ * adjoint) for a geometry and precision, as every call on that pair will use them.  Index
+ * 0 forward, 1 JVP, 2 adjoint: image rows staged per chunk, chunks per view, dynamic
+ * shared memory per CTA.  adjoint_phases: the adjoint's accumulation scheme, 0 for per-ray
+ * 4-column stencils gathered per pixel, K > 0 for K phase-coloured row buffers (slot t
+ * writes buffer t mod K; rays of one phase never touch the same pixel, so each buffer is
+ * written without conflicts and a pixel sums its K buffers).  Host only, no context;
+ * PGET_EINVAL for a null argument, an unknown precision or an invalid geometry. */
+typedef struct pget_walk_plan_info {
+    int32_t threads;            /* threads per CTA (one per distinct ray of a view) */
+    int32_t rows_per_chunk[3];
+    int32_t chunks[3];
+    int32_t smem_bytes[3];
+    int32_t adjoint_phases;
+    int32_t phases_needed;      /* phases the slot lattice needs (the plan takes phase
+                                   buffers when at most 4 are needed and they fit; 0: a
+                                   degenerate lattice) */
+} pget_walk_plan_info;
+pget_status pget_walk_plans(const pget_geometry* g, int32_t precision, pget_walk_plan_info* out);
+
 /* Projection onto the constraint set of p (Sec. 2.2): every pixel's pair (lambda, mu)
  * is replaced, in place, by its Euclidean projection onto the box [0, lambda_max] x
  * [0, mu_max], intersected with lambda <= lin_slope mu + lin_offset when p->lin_constraint

@@ -23,6 +23,8 @@ ops128     the three ray operators alone on the single-request geometry (128 x 1
            per second.  --op forward|jvp|vjp|all restricts the launches (also the small,
            named case for kernel profilers).
 ops512     the same on the precision-stress geometry (512 x 512, 720 x 182 x 9).
+ops256     the same on the differentiation geometry (256 x 256, 360 x 182 x 5).
+ops64      the same on the plain-LM geometry (64 x 64, 90 x 91 x 1) in FP64.
 
 Prints one JSON line per configuration.  Timing: CUDA events on the current stream around
 each reconstruction or launch (after one untimed warm-up), data resident in HBM.
@@ -231,11 +233,14 @@ def stress512(k: int, oracle_path: str = "") -> dict:
 
 
 OPS = {"ops128": dict(n=128, n_lat=9, radius=5.0, n_angles=360, n_det=182, n_sub=5),
-       "ops512": dict(n=512, n_lat=17, radius=10.0, n_angles=720, n_det=182, n_sub=9)}
+       "ops512": dict(n=512, n_lat=17, radius=10.0, n_angles=720, n_det=182, n_sub=9),
+       "ops256": dict(n=256, n_lat=17, radius=5.0, n_angles=360, n_det=182, n_sub=5),
+       "ops64": dict(n=64, n_lat=9, radius=3.0, n_angles=90, n_det=91, n_sub=1, precision=0)}
 
 
-def ops(k: int, name: str, op: str = "all", prec: int = P.PGET_F32_KAHAN) -> dict:
+def ops(k: int, name: str, op: str = "all", prec: int | None = None) -> dict:
     c = OPS[name]
+    prec = c.get("precision", P.PGET_F32_KAHAN) if prec is None else prec
     dt = P.dtype_of(prec)
     ph = synth.lattice_phantom(c["n"], c["n_lat"], radius=c["radius"], seed=1)
     g = P.geometry(c["n"], c["n_angles"], c["n_det"], n_sub=c["n_sub"])
@@ -274,7 +279,7 @@ def ops(k: int, name: str, op: str = "all", prec: int = P.PGET_F32_KAHAN) -> dic
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--config", required=True, choices=["plain64", "diff256", "stress512", "ops128", "ops512"])
+    ap.add_argument("--config", required=True, choices=["plain64", "diff256", "stress512", *OPS])
     ap.add_argument("--count", type=int, default=0)
     ap.add_argument("--op", default="all", choices=["all", "forward", "jvp", "vjp"])
     ap.add_argument("--oracle", default=os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),

@@ -407,6 +407,27 @@ void walk_orders(const Geometry& G, const std::vector<int>& goff, const std::vec
 size_t serving_bytes(const pget_ctx* ctx);
 bool evict_idle(pget_ctx* ctx);
 
+// Shared memory per walk CTA: three CTAs of up to 1024 threads share an SM's 227 KB (a
+// build with -DPGET_TUNING reads PGET_SMEM_KB_{FWD,JVP,VJP} to sweep the budgets).
+static size_t walk_budget(const char* env, size_t kb) {
+#ifdef PGET_TUNING
+    const char* v = getenv(env);
+    if (v && atoi(v) > 0) kb = (size_t)atoi(v);
+#else
+    (void)env;
+#endif
+    return kb * 1024;
+}
+
+// The launch plans of the forward, JVP and adjoint walks (host only).
+static void walk_plans(const Geometry& G, int P, bool wf64, WalkPlan* pf, WalkPlan* pj, WalkPlan* pv) {
+    *pf = plan_walk(G, P, kFwd, wf64, walk_budget("PGET_SMEM_KB_FWD", 64));
+    *pj = plan_walk(G, P, kJvp, wf64, walk_budget("PGET_SMEM_KB_JVP", 72));
+    std::vector<int2> rows;
+    ray_rows(G, wf64, &rows);
+    *pv = plan_walk(G, P, kVjp, wf64, walk_budget("PGET_SMEM_KB_VJP", 72), &rows);
+}
+
 // Allocate and initialise a workspace for a resolved geometry (no budget check).
 pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, std::unique_ptr<Workspace>* out) {
     const int V = g.n_angles * g.n_banks;
@@ -427,25 +448,8 @@ pget_status make_workspace(pget_ctx* ctx, Geometry&& g, int prec, int groups, st
     w->M = (size_t)G.n_angles * G.n_det;
     w->nslots = (size_t)V * G.max_slots;
     w->img_elems = (size_t)(G.n + 2) * w->P;
-    // shared memory per CTA: three CTAs of up to 1024 threads share an SM's 227 KB
-    // (a build with -DPGET_TUNING reads PGET_SMEM_KB_{FWD,JVP,VJP} to sweep the budgets)
-    auto budget = [](const char* env, size_t kb) {
-#ifdef PGET_TUNING
-        const char* v = getenv(env);
-        if (v && atoi(v) > 0) kb = (size_t)atoi(v);
-#else
-        (void)env;
-#endif
-        return kb * 1024;
-    };
-    w->pf = plan_walk(G, w->P, kFwd, w->wf64, budget("PGET_SMEM_KB_FWD", 64));
-    w->pj = plan_walk(G, w->P, kJvp, w->wf64, budget("PGET_SMEM_KB_JVP", 72));
-    {
-        std::vector<int2> rows;
-        ray_rows(G, w->wf64, &rows);
-        w->pv = plan_walk(G, w->P, kVjp, w->wf64, budget("PGET_SMEM_KB_VJP", 72), &rows);
-    }
-    if (w->obj64) w->pf64 = plan_walk(G, w->P, kFwd, true, budget("PGET_SMEM_KB_FWD", 64));
+    walk_plans(G, w->P, w->wf64, &w->pf, &w->pj, &w->pv);
+    if (w->obj64) w->pf64 = plan_walk(G, w->P, kFwd, true, walk_budget("PGET_SMEM_KB_FWD", 64));
     // views per adjoint CTA: one (the hardware scheduler balances single-view CTAs across
     // SMs best); a build with -DPGET_TUNING reads PGET_VJP_VIEWS_PER_CTA > 1 to group views
     // of one orientation, which shrinks the partial images but assigns work statically (0
@@ -1965,6 +1969,28 @@ pget_status pget_geometry_info(const pget_geometry* gin, int32_t* n_samples, int
         if (fov_radius) *fov_radius = g.r;
         if (det_pitch) *det_pitch = g.p;
         if (max_slots) *max_slots = g.max_slots;
+        return PGET_OK;
+    });
+}
+
+pget_status pget_walk_plans(const pget_geometry* gin, int32_t precision, pget_walk_plan_info* out) {
+    return guarded([&]() -> pget_status {
+        if (!gin || !out) return fail(PGET_EINVAL, "null argument");
+        if (!known_precision(precision)) return fail(PGET_EINVAL, "unknown precision %d", precision);
+        Geometry g;
+        std::string msg;
+        pget_status s = build_geometry(*gin, &g, &msg);
+        if (s != PGET_OK) return fail(s, "%s", msg.c_str());
+        WalkPlan pl[3];
+        walk_plans(g, ((g.n + 2 + 1) / 2) * 2, walk_precision(precision) == PGET_F64, &pl[0], &pl[1], &pl[2]);
+        out->threads = pl[0].threads;
+        for (int k = 0; k < 3; ++k) {
+            out->rows_per_chunk[k] = pl[k].Yc;
+            out->chunks[k] = pl[k].nchunks;
+            out->smem_bytes[k] = (int32_t)pl[k].smem;
+        }
+        out->adjoint_phases = pl[2].nph;
+        out->phases_needed = adjoint_phases_needed(g);
         return PGET_OK;
     });
 }

@@ -123,13 +123,16 @@ template <> struct Pos<double> {
     __device__ __forceinline__ float yf() const { return (float)Y; }
 };
 
-enum WalkMode { kFwd = 0, kJvp = 1, kVjp = 2 };
+// kVjpP is the adjoint with phase-coloured row buffers; callers ask for kVjp and the
+// launch takes kVjpP when the adjoint's plan has phases (WalkPlan::nph > 0)
+enum WalkMode { kFwd = 0, kJvp = 1, kVjp = 2, kVjpP = 3 };
 
 struct WalkArgs {
     const ViewDev* views;
     int n, T, P, Yc, nchunks, sb_cap;
     int Ps;                    // shared-memory row pitch of a staged chunk (elements)
     int nst;                   // VJP: stride between stencil planes (>= threads)
+    int nph, Pb, phs;          // kVjpP: phases, row pitch and phase stride of the row buffers (elements)
     double h;
     const void* u_img[2];      // padded interleaved (lambda, mu): [0] normal, [1] transposed
     const void* p_img[2];      // JVP: padded interleaved (dlambda, dmu)
@@ -168,6 +171,7 @@ struct WalkArgs {
 
 struct WalkPlan {
     int threads = 0, Yc = 0, nchunks = 0, sb_cap = 0, Ps = 0, nst = 0;
+    int nph = 0, Pb = 0, phs = 0;  // adjoint with phase-coloured row buffers (nph > 0)
     size_t smem = 0;
     std::vector<int2> win;  // VJP: [view][chunk] ray window of each chunk
 };
@@ -179,6 +183,10 @@ void ray_rows(const Geometry& g, bool f64, std::vector<int2>* rows);
 
 // h log2(e): the packed images hold mu in units where the attenuation sum is a power of 2
 inline double attenuation_scale(const Geometry& g) { return g.h * 1.4426950408889634; }
+
+// Phases the adjoint's row buffers need for this geometry's slot lattice (0: a degenerate
+// lattice); see the derivation in walk.cu.
+int adjoint_phases_needed(const Geometry& g);
 
 // Plan (threads, rows per chunk, shared memory) for one walk mode.
 // The adjoint plan needs the ray rows (ray_rows) to size its stencil windows.

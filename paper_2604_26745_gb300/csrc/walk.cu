@@ -26,6 +26,14 @@
 // whose footprint covers it: no atomics, no write conflicts, deterministic order.  Rows
 // shared by consecutive chunks are completed through a carried pixel row; each view
 // writes its own partial image, reduce_views sums them in a fixed order.
+//
+// Phase buffers (kVjpP, for slot lattices that need at most kMaxPhases phases).  The rays
+// of slots t and t + K of a view never touch the same pixel when K slot steps, measured
+// along a pixel row, span more than the columns a ray's cells cover in two rows
+// (adjoint_phases_needed).  Each ray then accumulates straight into the row buffer of its
+// phase t mod K, a dense copy of the chunk's rows that no other ray writes at those pixels,
+// and every pixel sums its K buffers in phase order: no stencil origins, no candidate
+// search, still no atomics and a fixed order.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -33,6 +41,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
+#include <string>
 #include <utility>
 
 #include "kernels.cuh"
@@ -50,6 +59,18 @@ constexpr short kNoRow = -30000;  // stencil origin of a (ray, row) the ray neve
 // always suffice, the double path evaluates positions per sample and keeps one column
 // of slack for rounding at exactly 45-degree views.
 template <typename T> constexpr int stencil_width() { return sizeof(T) == 8 ? 5 : 4; }
+
+// two neighbouring shared-memory elements from a 16-byte aligned address (one vector
+// load for float pairs)
+__device__ __forceinline__ void ld_pair(const float2* p, float2* a, float2* b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    *a = make_float2(v.x, v.y);
+    *b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2* a, double2* b) {
+    *a = p[0];
+    *b = p[1];
+}
 
 // ---- chunk staging: TMA bulk copies (cp.async.bulk) completing on an mbarrier
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -167,16 +188,26 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
     // bulk copies (the next chunk is copied while the current one is walked); the adjoint
     // stages its single buffer with plain loads of all warps between its chunks (measured
     // faster there: its short chunks alternate walk and gather phases)
-    constexpr int NB = MODE == kVjp ? 1 : 2;
-    constexpr bool TMA = MODE != kVjp;
+    constexpr bool VJP = MODE == kVjp || MODE == kVjpP;  // adjoint: stencils, or phase buffers (PH)
+    constexpr bool PH = MODE == kVjpP;
+    constexpr int NB = VJP ? 1 : 2;
+    constexpr bool TMA = !VJP;
     const size_t rbytes = sizeof(T2) * (size_t)(Yc + 1) * Ps;  // one staged image chunk
     size_t off = 0;
     T2* const cu0 = (T2*)sm;  // buffer 0: (lambda, mu) [, (dlambda, dmu)]; buffer 1 follows
     off += NB * rbytes * (MODE == kJvp ? 2 : 1);
     T* sval = (T*)(sm + off);  // forward / JVP: ray totals
-    if constexpr (MODE != kVjp) off += sizeof(T2) * (size_t)nth;  // T2-sized: keeps alignment
-    T2 *ST = nullptr, *carry0 = nullptr, *carry1 = nullptr;
+    if constexpr (!VJP) off += sizeof(T2) * (size_t)nth;  // T2-sized: keeps alignment
+    T2 *ST = nullptr, *carry0 = nullptr, *carry1 = nullptr, *PB = nullptr;
     short* C0 = nullptr;
+    if constexpr (PH) {
+        PB = (T2*)(sm + off);  // [phase][row][column + 2]: 16-byte aligned rows (Pb, phs even)
+        off += sizeof(T2) * (size_t)A.nph * A.phs;
+        carry0 = (T2*)(sm + off);
+        off += sizeof(T2) * (size_t)n;
+        carry1 = (T2*)(sm + off);
+        off += sizeof(T2) * (size_t)n;
+    }
     if constexpr (MODE == kVjp) {
         ST = (T2*)(sm + off);  // [(row * SW + k) * nth + ray]
         off += sizeof(T2) * (size_t)(Yc + 1) * SW * nth;
@@ -203,6 +234,8 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
 
     // the views of this CTA: one view, or (VJP) a group of views sharing the canonical
     // orientation whose adjoint images are summed into the group's partial image
+    // adjoint with phase buffers: the buffer of this thread's ray (slot tid) is tid mod nph
+    const int ph_off = PH ? (tid % A.nph) * A.phs : 0;
     const int g = A.cta_order ? A.cta_order[blockIdx.x] : (int)blockIdx.x;
     const int gb = A.group_off ? A.group_off[g] : g;
     const int ge = A.group_off ? A.group_off[g + 1] : g + 1;
@@ -228,7 +261,7 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
     const T2* dtab = (const T2*)A.depth;
     (void)dtab;
     T rho = T(0), Utot = T(0);
-    if constexpr (MODE == kVjp) {
+    if constexpr (VJP) {
         if (active) {
             const int q0 = A.src_off[vp.bank * A.max_slots + tid];
             const int q1 = A.src_off[vp.bank * A.max_slots + tid + 1];
@@ -302,6 +335,16 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
                 }
             cur_row = INT_MIN;  // the stencil rows of this chunk start empty
         }
+        if constexpr (PH) {
+            __syncthreads();  // the gather of chunk ck - 1 has read every row buffer
+            // rows 0 .. nrows - 1 of every phase start at zero (rows of one phase are
+            // contiguous, 16-byte aligned; the walk's rows are the staged ones)
+            const int per_phase = nrows * A.Pb * (int)sizeof(T2) / 16;
+            for (int k = 0; k < A.nph; ++k) {
+                float4* d = reinterpret_cast<float4*>(PB + (size_t)k * A.phs);
+                for (int e = tid; e < per_phase; e += blockDim.x) d[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
         if constexpr (TMA) {
             if (pend & (1u << b)) {  // after an abort the buffer holds stale rows: results are void
                 if (!mb_wait(&mb[b], (phase >> b) & 1u, wait_ns)) {
@@ -361,30 +404,42 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
                         const T gl = DEPTH ? rho * h * (dw * at) : rho * h * at;
                         const T gm = -rho * h * h * Qh;
                         const int rl = iy0 - row_lo;  // lower row of the cell; upper is rl + 1
-                        if (iy0 != cur_row && in_win) {  // stencil rows start zeroed (chunk top)
-                            if (iy0 + 1 != cur_row) {
-                                c0_hi = ix0 - base;
-                                C0[(rl + 1) * nth + ts] = (short)c0_hi;
-                            } else {
-                                c0_hi = c0_lo;
-                            }
-                            c0_lo = ix0 - base;
-                            C0[rl * nth + ts] = (short)c0_lo;
-                            cur_row = iy0;
-                        }
-                        const int ol = ix0 - c0_lo, oh = ix0 - c0_hi;
-                        // in_win holds by construction of the windows; never write outside them
-                        if ((unsigned)ol <= (unsigned)(SW - 2) && (unsigned)oh <= (unsigned)(SW - 2) && in_win) {
-                            T2* pl = ST + (size_t)(rl * SW + ol) * nth + ts;
-                            T2* ph = ST + (size_t)((rl + 1) * SW + oh) * nth + ts;
+                        if constexpr (PH) {
+                            // the ray's own phase buffer: no other ray of this phase touches
+                            // these cells in this chunk (the plan's phase count guarantees it)
+                            T2* pb = PB + ph_off + rl * A.Pb + ix0 + 2;
                             const T2 g2 = mk2(gl, gm);
-                            const T2 t0 = pl[0], t1 = pl[nth], t2 = ph[0], t3 = ph[nth];
-                            pl[0] = fma2(w00, g2, t0);
-                            pl[nth] = fma2(w10, g2, t1);
-                            ph[0] = fma2(w01, g2, t2);
-                            ph[nth] = fma2(w11, g2, t3);
+                            const T2 t0 = pb[0], t1 = pb[1], t2 = pb[A.Pb], t3 = pb[A.Pb + 1];
+                            pb[0] = fma2(w00, g2, t0);
+                            pb[1] = fma2(w10, g2, t1);
+                            pb[A.Pb] = fma2(w01, g2, t2);
+                            pb[A.Pb + 1] = fma2(w11, g2, t3);
                         } else {
-                            atomicOr(A.err, 2);  // geometry bound violated: report, never write out of range
+                            if (iy0 != cur_row && in_win) {  // stencil rows start zeroed (chunk top)
+                                if (iy0 + 1 != cur_row) {
+                                    c0_hi = ix0 - base;
+                                    C0[(rl + 1) * nth + ts] = (short)c0_hi;
+                                } else {
+                                    c0_hi = c0_lo;
+                                }
+                                c0_lo = ix0 - base;
+                                C0[rl * nth + ts] = (short)c0_lo;
+                                cur_row = iy0;
+                            }
+                            const int ol = ix0 - c0_lo, oh = ix0 - c0_hi;
+                            // in_win holds by construction of the windows; never write outside them
+                            if ((unsigned)ol <= (unsigned)(SW - 2) && (unsigned)oh <= (unsigned)(SW - 2) && in_win) {
+                                T2* pl = ST + (size_t)(rl * SW + ol) * nth + ts;
+                                T2* ph = ST + (size_t)((rl + 1) * SW + oh) * nth + ts;
+                                const T2 g2 = mk2(gl, gm);
+                                const T2 t0 = pl[0], t1 = pl[nth], t2 = ph[0], t3 = ph[nth];
+                                pl[0] = fma2(w00, g2, t0);
+                                pl[nth] = fma2(w10, g2, t1);
+                                ph[0] = fma2(w01, g2, t2);
+                                ph[nth] = fma2(w11, g2, t3);
+                            } else {
+                                atomicOr(A.err, 2);  // geometry bound violated: report, never write out of range
+                            }
                         }
                         q.add(cla);
                     }
@@ -396,34 +451,46 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
         }
         __syncthreads();  // every walk of chunk ck is done: its row buffer is free
         if constexpr (TMA) aborted = *s_abort != 0;
-        if constexpr (MODE == kVjp) {
+        if constexpr (VJP) {
             const int r0 = max(row_lo, 0), r1 = min(row_hi + 1, n - 1);
             T2* carry_rd = (ck & 1) ? carry0 : carry1;
             T2* carry_wr = (ck & 1) ? carry1 : carry0;
             T* gp = (T*)gpart + (size_t)g * 2 * n * n;
-            // every thread gathers two neighbouring pixels (Xa, Xa + 1) of a row: their
-            // candidate rays overlap, so one pass over the union loads each ray's stencil
-            // origin once; a ray outside one pixel's own window holds zeros at that pixel,
-            // and each pixel's sum keeps the ascending order of the rays
+            // every thread gathers two neighbouring pixels (Xa, Xa + 1) of a row.  Stencils:
+            // their candidate rays overlap, so one pass over the union loads each ray's
+            // stencil origin once; a ray outside one pixel's own window holds zeros at that
+            // pixel, and each pixel's sum keeps the ascending order of the rays.  Phase
+            // buffers: the pixel's value in each phase (at most one ray of a phase touches
+            // it), summed in phase order
             const int npair = (n + 1) / 2;
             const int nout2 = (r1 - r0 + 1) * npair;
             for (int e2 = tid; e2 < nout2; e2 += blockDim.x) {
                 const int dy = __float2int_rz(((float)e2 + 0.5f) * inv_np);
                 const int Yr = r0 + dy, Xa = 2 * (e2 - dy * npair);
                 const int rl = Yr - row_lo;
-                const float fa = ((float)Xa - X00f) * dXrf * invR2 + ((float)Yr - Y00f) * dYrf * invR2;
-                const float fb = fa + dXrf * invR2;
-                const int ilo = max(0, (int)ceilf(fminf(fa, fb) - wI - wa));
-                const int ihi = min(wn - 1, (int)floorf(fmaxf(fa, fb) + wI - wa));
                 T2 acca = mk2(T(0), T(0)), accb = mk2(T(0), T(0));
-                const short* c0r = C0 + rl * nth;
-                const T2* str = ST + (size_t)rl * SW * nth;
-                for (int t = ilo; t <= ihi; ++t) {
-                    const int ka = Xa - (int)c0r[t];
-                    const T2 va = (unsigned)ka < (unsigned)SW ? str[ka * nth + t] : mk2(T(0), T(0));
-                    const T2 vb = (unsigned)(ka + 1) < (unsigned)SW ? str[(ka + 1) * nth + t] : mk2(T(0), T(0));
-                    acca = add2(acca, va);
-                    accb = add2(accb, vb);
+                if constexpr (PH) {
+                    const T2* src = PB + rl * A.Pb + Xa + 2;  // even offset: 16-byte aligned pair
+                    for (int k = 0; k < A.nph; ++k) {
+                        T2 va, vb;
+                        ld_pair(src + (size_t)k * A.phs, &va, &vb);
+                        acca = add2(acca, va);
+                        accb = add2(accb, vb);
+                    }
+                } else {
+                    const float fa = ((float)Xa - X00f) * dXrf * invR2 + ((float)Yr - Y00f) * dYrf * invR2;
+                    const float fb = fa + dXrf * invR2;
+                    const int ilo = max(0, (int)ceilf(fminf(fa, fb) - wI - wa));
+                    const int ihi = min(wn - 1, (int)floorf(fmaxf(fa, fb) + wI - wa));
+                    const short* c0r = C0 + rl * nth;
+                    const T2* str = ST + (size_t)rl * SW * nth;
+                    for (int t = ilo; t <= ihi; ++t) {
+                        const int ka = Xa - (int)c0r[t];
+                        const T2 va = (unsigned)ka < (unsigned)SW ? str[ka * nth + t] : mk2(T(0), T(0));
+                        const T2 vb = (unsigned)(ka + 1) < (unsigned)SW ? str[(ka + 1) * nth + t] : mk2(T(0), T(0));
+                        acca = add2(acca, va);
+                        accb = add2(accb, vb);
+                    }
                 }
 #pragma unroll
                 for (int q2 = 0; q2 < 2; ++q2) {
@@ -571,6 +638,55 @@ static size_t walk_smem(int mode, bool f64, int threads, int Yc, int Ps, int nst
     return (b + 15) / 16 * 16;
 }
 
+// Phases of the adjoint's row buffers.  In a view's canonical frame the lines of slots t
+// and t + K lie K sigma_h apart horizontally, sigma_h = |dXr - dYr dXs / dYs| (the slot
+// step projected along the rays onto a row).  The samples whose cells touch one pixel row
+// have Y in [row - 1, row + 1), so their X span is below 2 s (s = |dXs / dYs| <= 1), and
+// the columns they write lie in [floor(x_min), floor(x_max) + 1].  K sigma_h >= 2 s + 2
+// then keeps the columns of two rays of one phase apart in every row: each phase buffer
+// is written by one ray per pixel.  0.05 px of margin covers the rounding of positions.
+// Returns 0 when no view allows it (a zero slot step).
+int adjoint_phases_needed(const Geometry& g) {
+    double need = 1.0;
+    for (const ViewDev& v : g.views) {
+        const double s = std::fabs(v.dXsd / v.dYsd);
+        const double sh = std::fabs(v.dXrd - v.dYrd * v.dXsd / v.dYsd);
+        if (!(sh > 1e-9) || !std::isfinite(s)) return 0;
+        need = std::max(need, (2.0 * s + 2.05) / sh);
+    }
+    return need > 1e6 ? 0 : (int)std::ceil(need);
+}
+
+// stride between phase buffers of (Yc + 1) rows of pitch Pb: even (16-byte aligned
+// buffers) and 8 words past a multiple of the 32 banks, so that the lanes of a warp, which
+// walk rays of consecutive phases, start their rows in different banks
+static int phase_stride(int Yc, int Pb, bool f64) {
+    const int words = f64 ? 4 : 2;
+    int s = (Yc + 1) * Pb;
+    s += s & 1;
+    while ((s * words) % 32 != 8) s += 2;
+    return s;
+}
+
+// shared memory of the adjoint with phase buffers: the staged chunk, nph buffers, the two
+// carried rows, the barrier and the abort flag
+static size_t walk_smem_phases(bool f64, int Yc, int Ps, int nph, int Pb, int n) {
+    const size_t s2 = f64 ? 16 : 8;
+    size_t b = s2 * (size_t)(Yc + 1) * Ps + s2 * (size_t)nph * phase_stride(Yc, Pb, f64) + 2 * s2 * n;
+    b = (b + 7) / 8 * 8 + 8 + 8;
+    return (b + 15) / 16 * 16;
+}
+
+// Most phases the adjoint takes phase buffers with: the gather reads every phase per pixel,
+// so finer slot lattices keep the per-ray stencils.  Measured (adjoint alone, phases vs
+// stencils): 2 phases at 512^2 x 720 x 182 x 9 3.27 vs 4.97 ms, 3 at 256^2 x 360 x 182 x 5
+// 510 vs 547 us, 3 at 64^2 x 90 x 91 x 1 (FP64) 213 vs 260 us, 5 at 128^2 x 360 x 182 x 5
+// 230 vs 229 us.  A -DPGET_TUNING build reads PGET_VJP_DESIGN=stencil|phases to force
+// either (phases up to kMaxPhasesForced).
+constexpr int kMaxPhases = 4;
+constexpr int kMaxPhasesForced = 16;
+
+
 WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, const std::vector<int2>* rows) {
     WalkPlan pl;
     pl.threads = ((g.max_slots + 31) / 32) * 32;
@@ -591,6 +707,35 @@ WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, 
             else hi = mid - 1;
         }
         fits(lo, &nst);
+        // phase buffers instead, when the slot lattice needs few phases and the buffers
+        // leave chunks at least as tall as the stencils do
+        const int K = adjoint_phases_needed(g);
+        int kmax = kMaxPhases;
+#ifdef PGET_TUNING
+        if (const char* d = getenv("PGET_VJP_DESIGN")) kmax = std::string(d) == "stencil" ? 0
+                                                              : std::string(d) == "phases" ? kMaxPhasesForced
+                                                                                           : kmax;
+#endif
+        const bool phases = K > 0 && K <= kmax;
+        if (phases) {
+            const int Pb = (g.n + 4) / 2 * 2;  // columns -1 .. n at index column + 2, even pitch
+            int Ych = 0;
+            for (int Yc = 1; Yc <= g.n + 1; ++Yc) {
+                if (walk_smem_phases(f64, Yc, pl.Ps, K, Pb, g.n) <= budget) Ych = Yc;
+                else break;
+            }
+            if (Ych >= std::max(2, lo)) {
+                pl.Yc = Ych;
+                pl.nchunks = (g.n + 1 + Ych - 1) / Ych;
+                pl.nph = K;
+                pl.Pb = Pb;
+                pl.phs = phase_stride(Ych, Pb, f64);
+                pl.nst = pl.threads;
+                pl.sb_cap = 0;
+                pl.smem = walk_smem_phases(f64, Ych, pl.Ps, K, Pb, g.n);
+                return pl;
+            }
+        }
         pl.Yc = lo;
         pl.nchunks = (g.n + 1 + lo - 1) / lo;
         pl.nst = nst;
@@ -688,6 +833,9 @@ static cudaError_t launch_one(const WalkPlan& pl, const WalkArgs& a0, int n_view
     WalkArgs a = a0;
     a.Ps = pl.Ps;
     a.nst = pl.nst;
+    a.nph = pl.nph;
+    a.Pb = pl.Pb;
+    a.phs = pl.phs;
     kern<<<dim3((unsigned)n_views, (unsigned)std::max(1, a.n_items)), pl.threads, pl.smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
@@ -708,7 +856,8 @@ int walk_occupancy(int mode, int precision, const WalkPlan& pl) {
     switch (mode) {                                       \
         case kFwd: return occ_one<T, K, kFwd>(pl);        \
         case kJvp: return occ_one<T, K, kJvp>(pl);        \
-        default: return occ_one<T, K, kVjp>(pl);          \
+        default: return pl.nph ? occ_one<T, K, kVjpP>(pl) \
+                               : occ_one<T, K, kVjp>(pl); \
     }
     if (precision == PGET_F64) {
         PGET_O(double, false)
@@ -736,7 +885,7 @@ cudaError_t prepare_walk(int mode, int precision, const WalkPlan& pl) {
     switch (mode) {                                                                              \
         case kFwd: return prepare_one<T, K, kFwd>(pl);                                           \
         case kJvp: return prepare_one<T, K, kJvp>(pl);                                           \
-        default: return prepare_one<T, K, kVjp>(pl);                                             \
+        default: return pl.nph ? prepare_one<T, K, kVjpP>(pl) : prepare_one<T, K, kVjp>(pl);     \
     }
     if (precision == PGET_F64) {
         PGET_P(double, false)
@@ -757,8 +906,11 @@ cudaError_t launch_walk(int mode, int precision, const WalkPlan& pl, const WalkA
                                   : launch_one<T, K, kFwd, false>(pl, a, n_views, st);                \
         case kJvp: return a.depth ? launch_one<T, K, kJvp, true>(pl, a, n_views, st)                  \
                                   : launch_one<T, K, kJvp, false>(pl, a, n_views, st);                \
-        default: return a.depth ? launch_one<T, K, kVjp, true>(pl, a, n_views, st)                    \
-                                : launch_one<T, K, kVjp, false>(pl, a, n_views, st);                  \
+        default:                                                                                      \
+            if (pl.nph) return a.depth ? launch_one<T, K, kVjpP, true>(pl, a, n_views, st)           \
+                                       : launch_one<T, K, kVjpP, false>(pl, a, n_views, st);         \
+            return a.depth ? launch_one<T, K, kVjp, true>(pl, a, n_views, st)                         \
+                           : launch_one<T, K, kVjp, false>(pl, a, n_views, st);                       \
     }
     if (precision == PGET_F64) {
         PGET_L(double, false)

@@ -85,6 +85,11 @@ class pget_step_report(C.Structure):
     _fields_ = [("check", pget_check_report), ("checked", C.c_int32), ("took", C.c_int32), ("nu_next", C.c_double)]
 
 
+class pget_walk_plan_info(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("rows_per_chunk", C.c_int32 * 3), ("chunks", C.c_int32 * 3),
+                ("smem_bytes", C.c_int32 * 3), ("adjoint_phases", C.c_int32), ("phases_needed", C.c_int32)]
+
+
 def _fields(st) -> dict:
     return {k: getattr(st, k) for k, _ in st._fields_ if k != "pad"}
 
@@ -120,6 +125,7 @@ _SIGS = {
     "pget_check_params": ([C.POINTER(pget_lm_params)], C.c_int),
     "pget_geometry_info": ([C.POINTER(pget_geometry), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32)], C.c_int),
+    "pget_walk_plans": ([C.POINTER(pget_geometry), C.c_int32, C.POINTER(pget_walk_plan_info)], C.c_int),
     "pget_lm_solve_host": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp,
                             _vp, C.c_int32, C.POINTER(pget_lm_report), _vp], C.c_int),
     "pget_submit": ([_vp, C.POINTER(pget_geometry), C.POINTER(pget_lm_params), _vp, _vp, _vp,
@@ -231,6 +237,20 @@ def geometry_info(g: pget_geometry) -> dict:
     _check(st)
     return {"n_samples": T.value, "n_banks": nb.value, "fov_radius": r.value, "det_pitch": p.value,
             "max_slots": ms.value}
+
+
+def walk_plans(g: pget_geometry, precision: int) -> dict:
+    """Launch plans of the forward, JVP and adjoint walks (host only): threads per CTA,
+    rows per chunk, chunks and shared memory per operator, adjoint phase count."""
+    out = pget_walk_plan_info()
+    st = load().pget_walk_plans(C.byref(g), int(precision), C.byref(out))
+    if st == PGET_EINVAL:
+        raise ValueError("invalid walk plan query: " + load().pget_last_error(None).decode())
+    _check(st)
+    ops = ("forward", "jvp", "vjp")
+    return {"threads": out.threads, "adjoint_phases": out.adjoint_phases, "phases_needed": out.phases_needed,
+            **{o: {"rows_per_chunk": out.rows_per_chunk[k], "chunks": out.chunks[k], "smem_bytes": out.smem_bytes[k]}
+               for k, o in enumerate(ops)}}
 
 
 def check_params(p: pget_lm_params) -> None:

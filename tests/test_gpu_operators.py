@@ -162,6 +162,58 @@ def test_walks_independent_of_chunk_height(tuning_lib, tmp_path, geo):
     assert moved, "the adjoint is bitwise equal at every budget: the chunk height did not change"
 
 
+# Child process on the -DPGET_TUNING build: the adjoint three times at one geometry and
+# precision, with the plan's phase count (PGET_VJP_DESIGN forces phase buffers or stencils).
+_DESIGN_CHILD = r"""
+import sys
+import numpy as np
+import torch
+from paper_2604_26745_gb300 import pget as P, synth
+P.load(sys.argv[1])
+n, na, nd, S, prec = (int(x) for x in sys.argv[3:8])
+ph = synth.lattice_phantom(n, 9 if n >= 64 else 4, radius=3.0, seed=43, jitter=0.7)
+g = P.geometry(n, na, nd, n_sub=S)
+dt = torch.float64 if prec in (0, 3) else torch.float32
+t = lambda x: torch.tensor(x, dtype=dt, device="cuda")
+lam, mu = t(ph.lam), t(ph.mu)
+r = t(np.random.default_rng(44).standard_normal((na, nd)))
+out = {"phases": np.int64(P.walk_plans(g, prec)["adjoint_phases"])}
+with P.Context(0) as c:
+    for k in range(3):
+        gl, gm = P.pget_vjp(c, g, prec, lam, mu, r)
+        out[f"gl{k}"], out[f"gm{k}"] = gl.cpu().numpy(), gm.cpu().numpy()
+np.savez(sys.argv[2], **out)
+"""
+
+
+@pytest.mark.parametrize("geo", [(128, 360, 182, 5, 2), (64, 90, 91, 1, 0), (40, 36, 182, 5, 1),
+                                 (96, 45, 182, 7, 2), (27, 17, 91, 3, 3)])
+def test_adjoint_designs_agree(tuning_lib, tmp_path, geo):
+    """The two accumulation schemes of the adjoint (phase-coloured row buffers and per-ray
+    stencils) give the same gradient up to the order of the per-pixel sums, each bitwise
+    reproducible: FP64 within 1e-12, the float walks within 1e-6 (max-norm relative)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for arm in ("phases", "stencil"):
+        env = dict(os.environ, PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""),
+                   PGET_VJP_DESIGN=arm)
+        f = tmp_path / f"{arm}.npz"
+        subprocess.run([sys.executable, "-c", _DESIGN_CHILD, tuning_lib, str(f), *(str(x) for x in geo)],
+                       env=env, cwd=root, check=True, timeout=600)
+        res[arm] = dict(np.load(f))
+    assert int(res["phases"]["phases"]) > 0 and int(res["stencil"]["phases"]) == 0
+    for d in res.values():
+        for name in ("gl", "gm"):
+            assert np.array_equal(d[name + "1"], d[name + "0"]) and np.array_equal(d[name + "2"], d[name + "0"])
+    tol = 1e-12 if geo[-1] == 0 else 1e-6
+    for name in ("gl0", "gm0"):
+        a, b = res["phases"][name], res["stencil"][name]
+        assert float(np.abs(a - b).max() / np.abs(b).max()) <= tol, name
+
+
 @pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("eps", [1e-3, -1.0])
 def test_prior_parity(ctx, O, P, torch, prec, eps):
