@@ -360,7 +360,7 @@ typedef struct pget_walk_plan_info {
     int32_t smem_bytes[3];
     int32_t adjoint_phases;
     int32_t phases_needed;      /* phases the slot lattice needs (the plan takes phase
-                                   buffers when at most 4 are needed and they fit; 0: a
+                                   buffers when at most 16 are needed and they fit; 0: a
                                    degenerate lattice) */
 } pget_walk_plan_info;
 pget_status pget_walk_plans(const pget_geometry* g, int32_t precision, pget_walk_plan_info* out);

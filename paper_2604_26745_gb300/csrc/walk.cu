@@ -658,33 +658,91 @@ int adjoint_phases_needed(const Geometry& g) {
 }
 
 // stride between phase buffers of (Yc + 1) rows of pitch Pb: even (16-byte aligned
-// buffers) and 8 words past a multiple of the 32 banks, so that the lanes of a warp, which
-// walk rays of consecutive phases, start their rows in different banks
-static int phase_stride(int Yc, int Pb, bool f64) {
+// buffers) and `bank` words past a multiple of the 32 banks (rounded down to what an even
+// stride reaches: a multiple of 2 words per element)
+static int phase_stride(int Yc, int Pb, bool f64, int bank) {
     const int words = f64 ? 4 : 2;
+    const int target = (bank % 32) / (2 * words) * (2 * words);
     int s = (Yc + 1) * Pb;
     s += s & 1;
-    while ((s * words) % 32 != 8) s += 2;
+    while ((s * words) % 32 != target) s += 2;
     return s;
 }
 
 // shared memory of the adjoint with phase buffers: the staged chunk, nph buffers, the two
 // carried rows, the barrier and the abort flag
-static size_t walk_smem_phases(bool f64, int Yc, int Ps, int nph, int Pb, int n) {
+static size_t walk_smem_phases(bool f64, int Yc, int Ps, int nph, int Pb, int n, int bank) {
     const size_t s2 = f64 ? 16 : 8;
-    size_t b = s2 * (size_t)(Yc + 1) * Ps + s2 * (size_t)nph * phase_stride(Yc, Pb, f64) + 2 * s2 * n;
+    size_t b = s2 * (size_t)(Yc + 1) * Ps + s2 * (size_t)nph * phase_stride(Yc, Pb, f64, bank) + 2 * s2 * n;
     b = (b + 7) / 8 * 8 + 8 + 8;
     return (b + 15) / 16 * 16;
 }
 
+// Samples of a few views, in the walk's order, split by chunk: [view][chunk][slot] lists of
+// (column, buffer row), for the bank model below.  Positions as in ray_rows (double).
+using ChunkSamples = std::vector<std::vector<std::vector<int2>>>;
+static std::vector<ChunkSamples> sample_views(const Geometry& g, int Yc, int nviews) {
+    const int V = (int)g.views.size(), n = g.n, ms = g.max_slots;
+    const int nch = (n + 1 + Yc - 1) / Yc;
+    std::vector<ChunkSamples> out;
+    for (int q = 0; q < std::min(V, nviews); ++q) {
+        const int v = (int)(((2LL * q + 1) * V) / (2LL * std::min(V, nviews)));
+        const ViewDev& vp = g.views[v];
+        ChunkSamples cs(nch, std::vector<std::vector<int2>>(vp.n_slots));
+        for (int i = 0; i < vp.n_slots; ++i) {
+            const int jlo = g.clip[((size_t)v * ms + i) * 2], jhi = g.clip[((size_t)v * ms + i) * 2 + 1];
+            const double X0 = vp.X00d + i * vp.dXrd, Y0 = vp.Y00d + i * vp.dYrd;
+            for (int j = jhi; j >= jlo; --j) {
+                const int ix = (int)std::floor(X0 + j * vp.dXsd), iy = (int)std::floor(Y0 + j * vp.dYsd);
+                if (ix < -1 || ix > n - 1 || iy < -1 || iy > n - 1) continue;
+                const int ck = (n - 1 - iy) / Yc;
+                const int row_lo = std::max(-1, n - 1 - ck * Yc - Yc + 1);
+                cs[ck][i].push_back(make_int2(ix, iy - row_lo));
+            }
+        }
+        out.push_back(std::move(cs));
+    }
+    return out;
+}
+
+// Modeled shared-memory wavefronts of the phase buffers' read-modify-writes for one layout:
+// the lanes of a warp walk consecutive slots in step (iteration k of a chunk: each lane's
+// k-th sample in it), a 64-bit (128-bit) access is served per half-warp, and a half-warp
+// takes as many wavefronts as the most distinct elements on one bank.  The layout
+// (phase stride modulo the banks, row pitch) decides how the lanes' rows, columns and
+// phases spread over the banks; measured at 128^2, 256^2 and 512^2 the model ranks the
+// layouts as their adjoint times do.
+static long long phase_layout_cost(const std::vector<ChunkSamples>& vs, int K, int Pb, int phs, bool f64) {
+    const int words = f64 ? 4 : 2;
+    long long total = 0;
+    for (const ChunkSamples& cs : vs)
+        for (const auto& ch : cs)
+            for (size_t w0 = 0; w0 < ch.size(); w0 += 32) {
+                size_t L = 0;
+                for (size_t s = w0; s < std::min(ch.size(), w0 + 32); ++s) L = std::max(L, ch[s].size());
+                for (size_t k = 0; k < L; ++k)
+                    for (size_t h = w0; h < std::min(ch.size(), w0 + 32); h += 16) {
+                        int cnt[32] = {0};
+                        for (size_t s = h; s < std::min(ch.size(), h + 16); ++s) {
+                            if (k >= ch[s].size()) continue;
+                            const long long e = (long long)(s % K) * phs + (long long)ch[s][k].y * Pb + ch[s][k].x + 2;
+                            for (int wd = 0; wd < words; ++wd) ++cnt[(int)((e * words + wd) & 31)];
+                        }
+                        total += *std::max_element(cnt, cnt + 32);
+                    }
+            }
+    return total;
+}
+
 // Most phases the adjoint takes phase buffers with: the gather reads every phase per pixel,
-// so finer slot lattices keep the per-ray stencils.  Measured (adjoint alone, phases vs
-// stencils): 2 phases at 512^2 x 720 x 182 x 9 3.27 vs 4.97 ms, 3 at 256^2 x 360 x 182 x 5
-// 510 vs 547 us, 3 at 64^2 x 90 x 91 x 1 (FP64) 213 vs 260 us, 5 at 128^2 x 360 x 182 x 5
-// 230 vs 229 us.  A -DPGET_TUNING build reads PGET_VJP_DESIGN=stencil|phases to force
-// either (phases up to kMaxPhasesForced).
-constexpr int kMaxPhases = 4;
-constexpr int kMaxPhasesForced = 16;
+// so finer slot lattices keep the per-ray stencils.  Measured (adjoint alone, FP32 + Kahan
+// unless stated, phase buffers in the layout the bank model picks vs stencils), K phases:
+// 512^2 x 720 x 182 x 9 (K 2) 3.14 vs 4.97 ms; 256^2 x 360 x 182 x 5 (3) 496 vs 547 us;
+// 64^2 x 90 x 91 x 1 FP64 (3) 213 vs 259 us; 192^2 x 360 x 182 x 7 (4) 449 vs 559 us;
+// 128^2 x 360 x 182 x 5 (5) 210 vs 229 us; 96^2 x 360 x 182 x 5 (6) 150 vs 180 us;
+// 128^2 x 360 x 182 x 7 (6) 263 vs 348 us; 128^2 x 360 x 182 x 9 (8) 284 vs 454 us.  A
+// -DPGET_TUNING build keeps the stencils when PGET_VJP_DESIGN=stencil.
+constexpr int kMaxPhases = 16;
 
 
 WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, const std::vector<int2>* rows) {
@@ -712,27 +770,58 @@ WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, 
         const int K = adjoint_phases_needed(g);
         int kmax = kMaxPhases;
 #ifdef PGET_TUNING
-        if (const char* d = getenv("PGET_VJP_DESIGN")) kmax = std::string(d) == "stencil" ? 0
-                                                              : std::string(d) == "phases" ? kMaxPhasesForced
-                                                                                           : kmax;
+        if (const char* d = getenv("PGET_VJP_DESIGN"))
+            if (std::string(d) == "stencil") kmax = 0;
 #endif
         const bool phases = K > 0 && K <= kmax;
         if (phases) {
-            const int Pb = (g.n + 4) / 2 * 2;  // columns -1 .. n at index column + 2, even pitch
-            int Ych = 0;
-            for (int Yc = 1; Yc <= g.n + 1; ++Yc) {
-                if (walk_smem_phases(f64, Yc, pl.Ps, K, Pb, g.n) <= budget) Ych = Yc;
-                else break;
-            }
-            if (Ych >= std::max(2, lo)) {
-                pl.Yc = Ych;
-                pl.nchunks = (g.n + 1 + Ych - 1) / Ych;
+            // the tallest chunk the buffers allow; among the layouts that keep it, the one the
+            // bank model rates best (pitch pads 0, 2, 4 elements; phase strides at every bank
+            // offset an even stride reaches), ties to the smaller pad and offset
+            const int Pb0 = (g.n + 4) / 2 * 2;  // columns -1 .. n at index column + 2, even pitch
+            const int step = f64 ? 8 : 4;
+            int pads[3] = {0, 2, 4}, npad = 3, banks0 = 0, banks1 = 32 - step;
+#ifdef PGET_TUNING
+            if (const char* e = getenv("PGET_PHASE_PITCH_PAD")) pads[0] = std::max(0, atoi(e)) / 2 * 2, npad = 1;
+            if (const char* e = getenv("PGET_PHASE_BANK")) banks0 = banks1 = std::max(0, atoi(e)) % 32 / step * step;
+#endif
+            auto fit = [&](int Pb, int bank) {
+                int Y = 0;
+                for (int Yc = 1; Yc <= g.n + 1; ++Yc) {
+                    if (walk_smem_phases(f64, Yc, pl.Ps, K, Pb, g.n, bank) <= budget) Y = Yc;
+                    else break;
+                }
+                return Y;
+            };
+            int Ymax = 0;
+            for (int a = 0; a < npad; ++a)
+                for (int bk = banks0; bk <= banks1; bk += step) Ymax = std::max(Ymax, fit(Pb0 + pads[a], bk));
+            if (Ymax >= std::max(2, lo)) {
+                // a few views spread over the angles (fewer on large grids: the model's cost
+                // grows with the samples per view)
+                const std::vector<ChunkSamples> vs = sample_views(g, Ymax, g.n <= 128 ? 6 : g.n <= 256 ? 4 : 2);
+                long long best = -1;
+                int bPb = Pb0, bbank = 0;
+                for (int a = 0; a < npad; ++a)
+                    for (int bk = banks0; bk <= banks1; bk += step) {
+                        const int Pb = Pb0 + pads[a];
+                        if (fit(Pb, bk) != Ymax) continue;
+                        const long long c = phase_layout_cost(vs, K, Pb, phase_stride(Ymax, Pb, f64, bk), f64);
+                        if (best < 0 || c < best) best = c, bPb = Pb, bbank = bk;
+                    }
+#ifdef PGET_TUNING
+                if (getenv("PGET_PLAN_VERBOSE"))
+                    fprintf(stderr, "adjoint phases %d: rows %d, pitch %d (pad %d), bank %d, modeled %lld\n", K, Ymax,
+                            bPb, bPb - Pb0, bbank, best);
+#endif
+                pl.Yc = Ymax;
+                pl.nchunks = (g.n + 1 + Ymax - 1) / Ymax;
                 pl.nph = K;
-                pl.Pb = Pb;
-                pl.phs = phase_stride(Ych, Pb, f64);
+                pl.Pb = bPb;
+                pl.phs = phase_stride(Ymax, bPb, f64, bbank);
                 pl.nst = pl.threads;
                 pl.sb_cap = 0;
-                pl.smem = walk_smem_phases(f64, Ych, pl.Ps, K, Pb, g.n);
+                pl.smem = walk_smem_phases(f64, Ymax, pl.Ps, K, bPb, g.n, bbank);
                 return pl;
             }
         }

@@ -126,7 +126,7 @@ def test_plans_fit_their_budgets(geo, prec):
         assert 1 <= q["rows_per_chunk"] <= n + 1
         assert q["chunks"] == -(-(n + 1) // q["rows_per_chunk"])
         assert 0 < q["smem_bytes"] <= kb * 1024 or q["rows_per_chunk"] == 1
-    assert pl["adjoint_phases"] in (0, pl["phases_needed"]) and pl["adjoint_phases"] <= 4
+    assert pl["adjoint_phases"] in (0, pl["phases_needed"]) and pl["adjoint_phases"] <= 16
 
 
 def test_walk_plans_refuses_bad_input():
