@@ -71,6 +71,8 @@ __device__ __forceinline__ void ld_pair(const double2* p, double2* a, double2* b
     *a = p[0];
     *b = p[1];
 }
+__device__ __forceinline__ void zero_pair(float2* p) { *reinterpret_cast<float4*>(p) = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void zero_pair(double2* p) { p[0] = p[1] = make_double2(0.0, 0.0); }
 
 // ---- chunk staging: TMA bulk copies (cp.async.bulk) completing on an mbarrier
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -336,13 +338,14 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
             cur_row = INT_MIN;  // the stencil rows of this chunk start empty
         }
         if constexpr (PH) {
-            __syncthreads();  // the gather of chunk ck - 1 has read every row buffer
-            // rows 0 .. nrows - 1 of every phase start at zero (rows of one phase are
-            // contiguous, 16-byte aligned; the walk's rows are the staged ones)
-            const int per_phase = nrows * A.Pb * (int)sizeof(T2) / 16;
-            for (int k = 0; k < A.nph; ++k) {
-                float4* d = reinterpret_cast<float4*>(PB + (size_t)k * A.phs);
-                for (int e = tid; e < per_phase; e += blockDim.x) d[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            // the view's first chunk finds the buffers zeroed here (the previous view ended
+            // with a barrier); every later chunk finds them zeroed by the gather before it
+            if (ck == 0) {
+                const int per_phase = (Yc + 1) * A.Pb * (int)sizeof(T2) / 16;
+                for (int k = 0; k < A.nph; ++k) {
+                    float4* d = reinterpret_cast<float4*>(PB + (size_t)k * A.phs);
+                    for (int e = tid; e < per_phase; e += blockDim.x) d[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
         }
         if constexpr (TMA) {
@@ -354,7 +357,7 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
                 phase ^= 1u << b;
                 pend &= ~(1u << b);
             }
-        } else {
+        } else if (!PH || ck == 0) {  // the phase-buffer adjoint stages later chunks after each gather
             stage_rows(cu0, ug, P, Ps, n, vp.flipped, row_lo, nrows);
             __syncthreads();
         }
@@ -470,10 +473,12 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
                 const int rl = Yr - row_lo;
                 T2 acca = mk2(T(0), T(0)), accb = mk2(T(0), T(0));
                 if constexpr (PH) {
-                    const T2* src = PB + rl * A.Pb + Xa + 2;  // even offset: 16-byte aligned pair
+                    // read and clear: the next chunk's walk finds the entries at zero
+                    T2* src = PB + rl * A.Pb + Xa + 2;  // even offset: 16-byte aligned pair
                     for (int k = 0; k < A.nph; ++k) {
                         T2 va, vb;
                         ld_pair(src + (size_t)k * A.phs, &va, &vb);
+                        zero_pair(src + (size_t)k * A.phs);
                         acca = add2(acca, va);
                         accb = add2(accb, vb);
                     }
@@ -513,6 +518,26 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
                         }
                     }
                 }
+            }
+            if constexpr (PH) {
+                // entries the walk wrote that no pixel pair read: columns -1 and n of every
+                // buffer row, and image row n (first chunk); then the next chunk's rows
+                const int K = A.nph;
+                for (int e = tid; e < K * nrows * 2; e += blockDim.x) {
+                    const int k = e / (nrows * 2), rem = e - k * (nrows * 2);
+                    PB[(size_t)k * A.phs + (rem >> 1) * A.Pb + ((rem & 1) ? n + 2 : 1)] = mk2(T(0), T(0));
+                }
+                if (row_hi + 1 == n)
+                    for (int e = tid; e < K * (n + 2); e += blockDim.x) {
+                        const int k = e / (n + 2), c = e - k * (n + 2);
+                        PB[(size_t)k * A.phs + (n - row_lo) * A.Pb + 1 + c] = mk2(T(0), T(0));
+                    }
+                if (ck + 1 < A.nchunks) {
+                    int nh, nl, nr;
+                    chunk_rows(n, Yc, ck + 1, &nh, &nl, &nr);
+                    stage_rows(cu0, ug, P, Ps, n, vp.flipped, nl, nr);
+                }
+                __syncthreads();  // buffers back at zero, the next chunk staged
             }
         }
     }
