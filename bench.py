@@ -38,12 +38,12 @@ METRIC = "recon/s"
 PRECISIONS_CHECKED = (("f32_kahan", 2), ("mixed", 3), ("f64", 0))
 SUB = (16, 16)
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
-# adjoint walk on this workload, valid only for the kernel code it was taken on:
-# reported while the device code of csrc/walk.cu (the part before its host section) and
-# csrc/kernels.cuh, without comments, blank lines and includes, hash to these values; null
-# otherwise.
-TRAFFIC = {"walk_vjp": {"bytes": 3042048 + 32939264,
+# DRAM bytes (read + write) and shared-memory wavefronts (all, and those from bank
+# conflicts) per launch of the dominant kernel from one ncu capture of the adjoint walk on
+# this workload, valid only for the kernel code it was taken on: reported while the device
+# code of csrc/walk.cu (the part before its host section) and csrc/kernels.cuh, without
+# comments, blank lines and includes, hash to these values; null otherwise.
+TRAFFIC = {"walk_vjp": {"bytes": 3042048 + 32939264, "smem_wavefronts": 41697874, "smem_conflicts": 14932898,
                         "walk.cu": "e338283873703600083a2a35bc14336785cca341edddc507976ef449c990b0c2",
                         "kernels.cuh": "96cb443f5a2135cf26f2465870fa9ed91417abbaf763465a89b14aeb64a58982"}}
 
@@ -70,7 +70,7 @@ def captured_traffic(kernel: str):
         return None
     if _device_code_hash(os.path.join(csrc, "kernels.cuh")) != t["kernels.cuh"]:
         return None
-    return t["bytes"]
+    return t
 
 
 def workload_config(world: int) -> dict:
@@ -441,7 +441,16 @@ def main():
     dk = dom if dom in bytes_per_sample else max((k for k in kern if k in bytes_per_sample),
                                                  key=lambda k: kern[k]["total_ms"])
     achieved = kern[dk]["achieved_gbs"]
-    traffic = captured_traffic(dk)
+    cap = captured_traffic(dk)
+    traffic = cap["bytes"] if cap else None
+    smem_pipe = None
+    if cap and "smem_wavefronts" in cap:
+        wb = 128 * cap["smem_wavefronts"]
+        got = wb / (kern[dk]["avg_us"] * 1e-6) / 1e9
+        smem_pipe = {"wavefront_bytes": wb, "conflict_wavefronts": cap["smem_conflicts"],
+                     "achieved_gbs": round(got, 1), "frac": round(got / smem_peak, 4),
+                     "note": "ncu shared-memory wavefronts x 128 B per launch (bank conflicts included) over the "
+                             "live launch time, against the same peak: the traffic the pipe actually serves"}
     hbm = None
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -455,7 +464,7 @@ def main():
         pass
     roof = {"kernel": dk, "bound": "smem", "achieved": round(achieved, 1), "peak": round(smem_peak, 1),
             "unit": "GB/s", "frac": round(achieved / smem_peak, 4), "traffic": traffic,
-            "traffic_unit": "DRAM bytes read + written per launch (ncu)", "hbm": hbm,
+            "traffic_unit": "DRAM bytes read + written per launch (ncu)", "hbm": hbm, "smem_pipe": smem_pipe,
             "peak_source": f"derived: {n_sm} SMs x 128 B/clk shared-memory bandwidth x median sampled SM clock",
             "timing": "average launch time from CUDA events on the launching stream, in an untimed pass "
                       "over the same steps (the headline pass runs without events)",
