@@ -822,9 +822,10 @@ WalkPlan plan_walk(const Geometry& g, int P, int mode, bool f64, size_t budget, 
             for (int a = 0; a < npad; ++a)
                 for (int bk = banks0; bk <= banks1; bk += step) Ymax = std::max(Ymax, fit(Pb0 + pads[a], bk));
             if (Ymax >= std::max(2, lo)) {
-                // a few views spread over the angles (fewer on large grids: the model's cost
-                // grows with the samples per view)
-                const std::vector<ChunkSamples> vs = sample_views(g, Ymax, g.n <= 128 ? 6 : g.n <= 256 ? 4 : 2);
+                // views spread over the angles: 16 up to 128^2 (with 6 the model missed the best
+                // layout there by 1 %), fewer on large grids, whose plans would otherwise take
+                // seconds (the model's cost grows with the samples per view)
+                const std::vector<ChunkSamples> vs = sample_views(g, Ymax, g.n <= 128 ? 16 : g.n <= 256 ? 4 : 2);
                 long long best = -1;
                 int bPb = Pb0, bbank = 0;
                 for (int a = 0; a < npad; ++a)
