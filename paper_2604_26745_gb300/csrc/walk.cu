@@ -586,8 +586,13 @@ static int smem_pitch(int P, bool f64) {
         return P + (k > 0 ? (k + 1) / 2 * 2 : 0);
     }
 #endif
-    (void)f64;
-    return P + 4;  // measured best of skews 0..14 at 128 x 128 (forward and JVP)
+    // measured best of skews 0..14 at 128 x 128 (forward and JVP): P + 4.  From 256 x 256
+    // up (float) a pitch on a multiple of 16 elements measured faster: at 256^2 x 360 x
+    // 182 x 5 the JVP 200 -> 171 us and the adjoint 430 -> 424 us, at 512^2 x 720 x 182 x 9
+    // the JVP 1.25 -> 1.21 ms, the adjoint 3.10 -> 3.07 ms, the forward 730 -> 722 us; at
+    // 192^2 and 128^2 it was slower (adjoint 355 -> 370 us, forward 60 -> 68 us)
+    if (!f64 && P >= 258) return (P + 2 + 15) / 16 * 16;
+    return P + 4;
 }
 
 // stencil plane stride: consecutive planes start 8 words apart modulo the banks, so
