@@ -477,8 +477,8 @@ __global__ void __maxnreg__(MAXT <= kWalkThreads ? 72 : 64) walk_kernel(WalkArgs
                     T2* src = PB + rl * A.Pb + Xa + 2;  // even offset: 16-byte aligned pair
                     // up to four phases loaded before any is cleared, so that the loads
                     // overlap; summed in phase order.  Only in the float 72-register
-                    // instantiation: measured 206 -> 196 us at 128^2 x 360 x 182 x 5 and
-                    // 488 -> 429 us at 256^2, but 3.10 -> 3.34 ms in the 64-register one
+                    // instantiation: measured 206 -> 196-201 us at 128^2 x 360 x 182 x 5 and
+                    // 488 -> 430 us at 256^2, but 3.10 -> 3.34 ms in the 64-register one
                     // (512^2 x 720 x 182 x 9), and spills in double
                     constexpr int G = (sizeof(T) == 4 && MAXT <= kWalkThreads) ? 4 : 1;
                     for (int k0 = 0; k0 < A.nph; k0 += G) {
